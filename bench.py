@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the NLPR fusion ADMM on GB300 (prints one JSON line on rank 0).
+
+A step is one pass of the whole hot path over one synthetic problem: guide weights
+(eq. wts), `iters` ADMM iterations (Sec. IV) and the output Z = X E.  The default workload
+is HS+MS fusion at 256 x 256 x 93 bands, subspace L_s = 20, 5x5 patches, 7x7 search window,
+BF16 weights, FP32 iterates, 100 iterations.
+
+Metric: megapixel-band-iterations per second, (H W / 1e6) L_s iters / seconds, summed over
+ranks (each rank solves its own independent problem: weak scaling, no data-path collective).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import pathlib
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import numpy as np  # noqa: E402
+
+METRIC = "ADMM throughput (megapixel*band*iter/s)"
+UNIT = "Mpx*band*iter/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hsms_256")
+    ap.add_argument("--iters", type=int, default=None, help="override the workload's iteration count")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except Exception:
+        return {}
+
+
+def _workload(name, rank, iters_override):
+    from paper_2210_04184_gb300 import synth
+    spec = synth.WORKLOADS[name]
+    p, meta = synth.workload(name, seed=synth.SEED_BASE + spec["cfg"] + 7919 * rank)
+    if iters_override:
+        p.iters = iters_override
+    return p, meta
+
+
+def _config(p, meta, name, n_gpus):
+    return {
+        "workload": name,
+        "H": p.H, "W": p.W, "bands": p.L_l, "L_h": p.L_h, "L_s": p.L_s, "ratio": p.d,
+        "patch": f"{2 * p.K + 1}x{2 * p.K + 1}", "search": f"{2 * p.S + 1}x{2 * p.S + 1}",
+        "offsets": (2 * p.S + 1) ** 2 - 1, "iters": p.iters, "weights": meta["wdtype"],
+        "global_batch": n_gpus, "parallelism": f"independent problems x{n_gpus}",
+        "l2": "latent state per problem exceeds L2 (no flush needed)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def latent_bytes(p, esz, wsz):
+    """Algorithmic bytes of one latent-pass launch: Sigma read + write, omega, X, planes."""
+    n = p.H * p.W
+    nW = (2 * p.S + 1) ** 2 - 1
+    nP = (2 * p.K + 1) ** 2
+    return (2 * nW * nP * p.L_s * n * esz + nW * n * wsz + p.L_s * n * esz
+            + 2 * (2 * p.S + 1) * p.L_s * n * esz)
+
+
+def cpu_baseline(p, target_s=15.0):
+    """The FP64 oracle timed on the host cores on a bounded crop of the same workload
+    (same bands, subspace, patch and window; a 48 x 48 image; weights plus n iterations,
+    n sized from a one-iteration probe so the sample takes about target_s seconds)."""
+    from oracle import nlpr
+    from paper_2210_04184_gb300 import synth
+    crop = 48
+    q = synth.make_problem(H=crop, W=crop, L_l=p.L_l, L_h=p.L_h, L_s=p.L_s, d=p.d,
+                           blur_size=p.blur.shape[0], blur_sigma=1.7, K=p.K, S=p.S, lam1=p.lam1,
+                           lam2=p.lam2, rho=p.rho, h=p.h, seed=1, kind="hsms")
+    Yl, Yh = nlpr.to_hwl(q.Yl), nlpr.to_hwl(q.Yh)
+
+    def run(n):
+        t0 = time.perf_counter()
+        om = nlpr.weights(Yh, q.K, q.S, q.h)
+        nlpr.admm(Yl, Yh, q.blur, q.d, q.R, q.E, q.K, q.S, q.lam1, q.lam2, q.rho, om, n, fast=True)
+        return time.perf_counter() - t0
+
+    run(1)                      # first touch of the oracle's arrays
+    probe = run(1)
+    n = int(max(1, min(100, target_s / max(probe, 1e-3))))
+    dt = run(n)
+    value = crop * crop / 1e6 * q.L_s * n / dt
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{crop}x{crop} crop, {q.L_l} bands, L_s={q.L_s}, K={q.K}, S={q.S}, "
+                      f"weights + {n} iterations, FP64 NumPy + C/OpenMP loops, {dt:.1f}s"}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    p, meta = _workload(a.workload, 0, a.iters)
+    samples = []
+    cb = None
+    for i in range(a.warmup + a.steps):
+        cb = cpu_baseline(p, target_s=8.0 if i >= a.warmup else 2.0)
+        if i >= a.warmup:
+            samples.append(cb["value"])
+    value = statistics.median(samples)
+    cb["value"] = value
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": _config(p, meta, a.workload, a.gpus), "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2210_04184_gb300 import build as _build
+    from paper_2210_04184_gb300.fuse import Fusion, FUSE_OPT_PROFILE, FUSE_K_ALL, FUSE_K_LATENT
+    _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    p, meta = _workload(a.workload, rank, a.iters)
+    td = torch.float64 if meta["dtype"] == "f64" else torch.float32
+    esz = 8 if meta["dtype"] == "f64" else 4
+    wsz = {"bf16": 2, "f32": 4, "f64": 8}[meta["wdtype"]]
+    f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
+    yl = torch.tensor(p.Yl, dtype=td, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=td, device="cuda")
+    Z = torch.empty((p.L_l, p.H, p.W), dtype=td, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream
+    fuse_set_stream(f.ctx, stream.cuda_stream)
+
+    def step():
+        fuse_weights(f.ctx, yh.data_ptr())
+        fuse_solve(f.ctx, yl.data_ptr(), yh.data_ptr(), p.iters, 0, None, Z.data_ptr())
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    f.set_option(FUSE_OPT_PROFILE, 1)
+    f.profile(FUSE_K_LATENT, reset=True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    lat_ms, lat_n = f.profile(FUSE_K_LATENT)
+    _, launches = f.profile(FUSE_K_ALL)
+    f.set_option(FUSE_OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = p.H * p.W / 1e6 * p.L_s * p.iters * a.steps * world
+    value = units / (ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned inputs, Z read back each step)
+    e2e = None
+    if not a.no_e2e:
+        from paper_2210_04184_gb300.fuse import fuse_run_host
+        nd = np.float64 if td == torch.float64 else np.float32
+        hyl = torch.from_numpy(np.ascontiguousarray(p.Yl, dtype=nd)).pin_memory()
+        hyh = torch.from_numpy(np.ascontiguousarray(p.Yh, dtype=nd)).pin_memory()
+        hz = torch.empty((p.L_l, p.H, p.W), dtype=td).pin_memory()
+        f.set_option(FUSE_OPT_PROFILE, 0)
+        for _ in range(max(1, a.warmup)):
+            fuse_run_host(f.ctx, hyl.data_ptr(), hyh.data_ptr(), None, p.iters, None, hz.data_ptr())
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            fuse_run_host(f.ctx, hyl.data_ptr(), hyh.data_ptr(), None, p.iters, None, hz.data_ptr())
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": units / dt, "unit": UNIT,
+               "h2d_bytes_per_step": hyl.numel() * hyl.element_size() + hyh.numel() * hyh.element_size(),
+               "d2h_bytes_per_step": hz.numel() * hz.element_size()}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    per_launch_ms = lat_ms / max(lat_n, 1)
+    lb = latent_bytes(p, esz, wsz)
+    achieved = lb / (per_launch_ms / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": meta["dtype"], "data": "synthetic",
+        "config": _config(p, meta, a.workload, world),
+        "iters_per_s": p.iters * a.steps * world / (ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "latent_kernel",
+                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms,
+                     "launches": lat_n, "peak_source": peak_src},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not a.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(out), flush=True)
+    f.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(a.gpus if a.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/* fuse.h — C-ABI of the GB300 NLPR multiband-fusion solver (libfuse.so).
+ *
+ * The library solves
+ *     min_X  1/2 ||Y_l - S B X E||^2 + lambda1/2 ||Y_h - X E R||^2 + lambda2 phi(X)
+ * (Sec. I-A eq. mainoptim) with the nonlocal patch regulariser
+ *     phi(X) = sum_i sum_{tau in W} omega_{i tau} ||P_{i tau}(X)||_1        (Sec. II-B eq. reg1)
+ * by the ADMM of Sec. IV on the splitting P1 = B X, P2 = X, Q_{tau k} = D_{tau k} X
+ * (eq. fusionoptim).  Every iteration is: FFT solve of the X system (eqs.
+ * x_linear_system_main, inv), the per-pixel P1/P2 closed forms (eqs. Qh_update,
+ * Qm_update), soft thresholding of the latent variables (eq. Qj_main) and the dual
+ * updates (eqs. dualvar1_main..dualvar3_main).  The guide weights omega come once from
+ * patch distances on the high-resolution guide (eq. wts).
+ *
+ * Conventions (all entry points):
+ *   - Images are planar, band-major, contiguous: band c of an H x W image with L bands
+ *     starts at element c*H*W, pixel (i1, i2) is element i1*W + i2 (i1 = row).
+ *   - Device pointers must be CUDA device memory of the current device; host pointers
+ *     are ordinary (preferably pinned) host memory.  Element type is the context's
+ *     dtype (FUSE_F32 -> float, FUSE_F64 -> double) unless stated otherwise.
+ *   - Work is issued asynchronously on the context's stream unless stated otherwise.
+ *   - Indices are circular (periodic boundary conditions, Sec. II-B).
+ *   - The search window is W = [-S, S]^2 without (0, 0), ordered row-major
+ *     (tau1 outer); the patch is P = [-K, K]^2, row-major.  |W| = (2S+1)^2 - 1.
+ *   - The soft threshold is mu = lambda2 * omega / rho (eq. Qj_main).
+ *   - Every call returns a fuse_status; no C++ exception crosses this boundary.  An
+ *     error is recorded in the context (sticky until fuse_reset_error) and its text is
+ *     available from fuse_last_error.  Calls on a context holding an error return
+ *     FUSE_ESTATE without doing work.
+ *   - The caller owns every buffer it passes; the library owns everything it allocates
+ *     inside a context and frees it in fuse_destroy.
+ */
+#ifndef FUSE_H
+#define FUSE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fuse_status {
+    FUSE_OK = 0,
+    FUSE_EINVAL = 1,        /* bad argument (null pointer, size, parameter range) */
+    FUSE_ENOMEM = 2,        /* device or host allocation failed */
+    FUSE_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    FUSE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    FUSE_ENONFINITE = 5,    /* a non-finite value was detected in a monitored quantity */
+    FUSE_ESTATE = 6,        /* call not valid in the context's state (sticky error, no weights) */
+    FUSE_EUNSUPPORTED = 7   /* valid request this build does not support (e.g. FFT size) */
+} fuse_status;
+
+typedef enum fuse_dtype {
+    FUSE_F32 = 0,
+    FUSE_F64 = 1,
+    FUSE_BF16 = 2           /* weights only */
+} fuse_dtype;
+
+/* Sizes of one problem (Sec. I-A): the image is H x W (n_h = H*W pixels, H = p,
+ * W = q rows/columns of the periodic domain); Y_l has L_l bands on the (H/ratio) x
+ * (W/ratio) lattice, Y_h has L_h bands, X has L_s bands (Z = X E, E is L_s x L_l);
+ * the guide passed to fuse_weights has L_guide bands. */
+typedef struct fuse_geometry {
+    int H, W;
+    int L_l, L_h, L_s;
+    int L_guide;
+} fuse_geometry;
+
+typedef struct fuse_ctx fuse_ctx;
+
+/* Options for fuse_set_option. */
+enum {
+    FUSE_OPT_PROFILE = 1,   /* value 1: time every latent-pass launch with CUDA events */
+    FUSE_OPT_GRAPH = 2      /* value 1 (default): replay iterations from a captured CUDA graph */
+};
+
+/* Kernel groups for fuse_profile. */
+enum {
+    FUSE_K_ALL = 0,         /* launch count of every kernel issued by the library */
+    FUSE_K_LATENT = 1       /* the fused latent pass (eqs. Qj_main, dualvar3_main, D^T sum) */
+};
+
+/* Bytes of device memory fuse_init would allocate for this problem (state, weights,
+ * FFT buffers and constants).  No device work.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED. */
+fuse_status fuse_workspace_bytes(const fuse_geometry* g, int K, int S, int ratio,
+                                 fuse_dtype dtype, fuse_dtype wdtype, size_t* bytes);
+
+/* Create a solver context (Sec. IV set-up).
+ *   g        problem sizes; H and W divisible by `ratio`, H and W factor into 2, 3, 5,
+ *            2(K+S)+1 <= min(H, W), W a multiple of 4 (FUSE_F32) or 2 (FUSE_F64).
+ *   blur     host, bh x bw row-major (bh, bw odd, bh <= H, bw <= W): the kernel b of B,
+ *            centred: blur[a*bw + c] = b(a - bh/2, c - bw/2); B X(i) = sum_j b(j) X(i - j)
+ *            with circular indices (Sec. I-A).
+ *   ratio    decimation factor d of S: S keeps pixels with i1 = i2 = 0 (mod d).
+ *   R        host, L_l x L_h row-major (spectral response, Y_h = Z R).
+ *   E        host, L_s x L_l row-major (subspace basis, Z = X E); NULL means E = I
+ *            (then L_s must equal L_l).
+ *   K, S     patch half-size (|P| = (2K+1)^2, 0 <= K <= 3) and search half-size (S >= 1).
+ *   lambda1, lambda2, rho, h   parameters of eqs. mainoptim, wts (lambda1, rho, h > 0,
+ *            lambda2 >= 0).
+ *   dtype    FUSE_F32 or FUSE_F64: arithmetic and storage type of the iterates.
+ *   wdtype   storage type of omega: FUSE_BF16 or FUSE_F32 with FUSE_F32, FUSE_F64 with
+ *            FUSE_F64.
+ *   stream   cudaStream_t (as void*) on which all later work is issued; NULL = legacy
+ *            default stream.
+ * Host arrays are copied; the caller keeps ownership.  On success *out receives the
+ * context (free with fuse_destroy).  The per-frequency factor of eq. inv and the
+ * L_s x L_s inverses of eqs. Qh_update and Qm_update are computed here in FP64 on the
+ * host.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED, FUSE_ENOMEM, FUSE_ECUDA. */
+fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur, int bh, int bw,
+                      int ratio, const double* R, const double* E, int K, int S,
+                      double lambda1, double lambda2, double rho, double h,
+                      fuse_dtype dtype, fuse_dtype wdtype, void* stream);
+
+/* Free every resource of the context (synchronises its stream first).  NULL is a no-op. */
+fuse_status fuse_destroy(fuse_ctx* ctx);
+
+/* Change the stream used by later calls. */
+fuse_status fuse_set_stream(fuse_ctx* ctx, void* stream);
+
+/* Guide weights omega_{i tau} = exp(-||P_{i tau}(G)||_2^2 / h^2) (Sec. II-B eq. wts) for every
+ * pixel i and tau in W, from the device guide G [L_guide][H][W] (dtype).  Stored in the
+ * context as [|W|][H][W] of wdtype.  Must precede fuse_solve.  Errors: FUSE_EINVAL, FUSE_ECUDA. */
+fuse_status fuse_weights(fuse_ctx* ctx, const void* guide_dev);
+
+/* Replace the stored weights with w_dev [|W|][H][W] of the context's wdtype (device). */
+fuse_status fuse_set_weights(fuse_ctx* ctx, const void* w_dev);
+
+/* Copy the stored weights into w_dev [|W|][H][W] of the context's wdtype (device). */
+fuse_status fuse_get_weights(fuse_ctx* ctx, void* w_dev);
+
+/* Run `iters` ADMM iterations (Sec. IV; order X, P1, P2, Q, duals).
+ *   Yl_dev   [L_l][H/ratio][W/ratio] (device, dtype)   low-resolution image Y_l
+ *   Yh_dev   [L_h][H][W] (device, dtype)               high-resolution image Y_h
+ *   iters    >= 0
+ *   warm     0: start from zero P1, P2, Q, Lambda1, Lambda2, Sigma (all zero);
+ *            1: continue from the state left by the previous fuse_solve/fuse_set_state.
+ *   X_out    nullable, [L_s][H][W] (device, dtype): X after the last iteration
+ *            (zero when iters == 0 from a zero start).
+ *   Z_out    nullable, [L_l][H][W] (device, dtype): Z = X E.
+ * Asynchronous on the context stream.  Errors: FUSE_EINVAL, FUSE_ESTATE (no weights), FUSE_ECUDA. */
+fuse_status fuse_solve(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters, int warm,
+                       void* X_out, void* Z_out);
+
+/* End-to-end call on HOST buffers: copies Y_l, Y_h (and the guide; NULL = use Y_h) to the
+ * device, computes the weights, runs fuse_solve from a zero start and copies X and/or Z back
+ * (each nullable).  Synchronous: returns after the results are in host memory.  Device
+ * staging buffers are allocated on first use and kept by the context. */
+fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_host,
+                          const void* guide_host, int iters, void* X_host, void* Z_host);
+
+/* Objective terms at the current X (after a fuse_solve): out[0] = 1/2||Y_l - S B X E||^2,
+ * out[1] = lambda1/2 ||Y_h - X E R||^2, out[2] = lambda2 phi(X) (eq. mainoptim; eq. reg1),
+ * out[3] = ||X||_F^2.  Y_l, Y_h as in fuse_solve.  Synchronous; sums in FP64.
+ * Errors: FUSE_ESTATE (no solve yet), FUSE_ENONFINITE (a term is not finite). */
+fuse_status fuse_objective(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, double out[4]);
+
+/* Size in bytes of the resumable ADMM state (Lambda1, U1 = P1 + Lambda1, Lambda2,
+ * U2 = P2 + Lambda2, Sigma, the adjoint partial sums and X). */
+fuse_status fuse_state_bytes(fuse_ctx* ctx, size_t* bytes);
+
+/* Copy the state to / from a buffer of fuse_state_bytes bytes (host or device; uses
+ * cudaMemcpyAsync with cudaMemcpyDefault, synchronous on return).  fuse_set_state makes
+ * the next warm fuse_solve continue bit-identically from the saved iteration. */
+fuse_status fuse_get_state(fuse_ctx* ctx, void* dst);
+fuse_status fuse_set_state(fuse_ctx* ctx, const void* src);
+
+/* Options (FUSE_OPT_*). */
+fuse_status fuse_set_option(fuse_ctx* ctx, int option, long long value);
+
+/* Profile counters since the last reset: kernel group `which` (FUSE_K_*): total device time
+ * in ms (only with FUSE_OPT_PROFILE, else 0) and launch count.  Synchronises the stream.
+ * reset != 0 clears the counters after reading. */
+fuse_status fuse_profile(fuse_ctx* ctx, int which, double* ms, long long* launches, int reset);
+
+/* Last error text of the context ("" if none); valid until the next call on ctx. */
+const char* fuse_last_error(const fuse_ctx* ctx);
+
+/* Clear the sticky error of the context. */
+fuse_status fuse_reset_error(fuse_ctx* ctx);
+
+/* Static name of a status code. */
+const char* fuse_status_string(fuse_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUSE_H */

@@ -1,0 +1,62 @@
+// Shared device helpers of the NLPR fusion kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace fuse {
+
+// Circular index for a value within one period of [0, n): a in [-n, 2n).
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+// Circular index for any a.
+__device__ __forceinline__ int wrapn(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+template <typename T> struct cplx { T x, y; };
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+
+// 16-byte vector of T (4 floats or 2 doubles) for 128-bit global accesses.
+template <typename T, int N> struct alignas(sizeof(T) * N) vecT { T v[N]; };
+
+// Weight storage type -> arithmetic type.
+__device__ __forceinline__ float wload(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float wload(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double wload(const double* p) { return __ldg(p); }
+
+__device__ __forceinline__ void wstore(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void wstore(float* p, float v) { *p = v; }
+__device__ __forceinline__ void wstore(double* p, double v) { *p = v; }
+
+__device__ __forceinline__ float texp(float x) { return expf(x); }
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+
+// Streaming (evict-first) 16-byte load/store of the latent state.
+__device__ __forceinline__ vecT<float, 4> ld_stream(const vecT<float, 4>* p) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    return {{v.x, v.y, v.z, v.w}};
+}
+__device__ __forceinline__ void st_stream(vecT<float, 4>* p, const vecT<float, 4>& a) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+}
+__device__ __forceinline__ vecT<double, 2> ld_stream(const vecT<double, 2>* p) {
+    double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    return {{v.x, v.y}};
+}
+__device__ __forceinline__ void st_stream(vecT<double, 2>* p, const vecT<double, 2>& a) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(a.v[0], a.v[1]));
+}
+
+}  // namespace fuse

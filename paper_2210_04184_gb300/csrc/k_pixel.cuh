@@ -1,0 +1,79 @@
+// Per-pixel closed forms of Sec. IV (one thread per pixel, all L_s bands):
+//   P2 = (X - Lambda2 + lambda1/rho Y_h R^T E^T) F                       (eq. Qm_update)
+//   P1 = S^T S (rho B X + S^T Y_l E^T - rho Lambda1)(E E^T + rho I)^{-1}
+//        + (I - S^T S)(B X - Lambda1)                                   (eq. Qh_update)
+//   Lambda1 <- Lambda1 - (B X - P1),  Lambda2 <- Lambda2 - (X - P2)      (eqs. dualvar1_main, 2)
+// and writes U1 = P1 + Lambda1, U2 = P2 + Lambda2 for the next right-hand side.
+// S^T S is the 0/1 mask of pixels with i1 = i2 = 0 (mod d); S^T Y_l E^T at those pixels is
+// D9a[c][i1/d][i2/d]; lambda1/rho Y_h R^T E^T is D9b[c][i1][i2].  The per-pixel band vector
+// is staged in shared memory [L_s][blockDim]; the L_s x L_s matrices are read uniformly.
+#pragma once
+#include "common.cuh"
+
+namespace fuse {
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ Lam1, T* __restrict__ U1,
+             T* __restrict__ Lam2, T* __restrict__ U2, const T* __restrict__ D9a, const T* __restrict__ D9b,
+             const T* __restrict__ M1, const T* __restrict__ F, int H, int W, int Ls, int d, T rho) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* a = reinterpret_cast<T*>(smem_raw);     // [Ls][blockDim]
+    const int tid = threadIdx.x, nb = blockDim.x;
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * nb + tid;
+    if (p >= n) return;
+    // P2 and Lambda2
+    for (int j = 0; j < Ls; ++j) a[j * nb + tid] = X[j * n + p] - Lam2[j * n + p] + D9b[j * n + p];
+    for (int c = 0; c < Ls; ++c) {
+        T acc = T(0);
+        for (int j = 0; j < Ls; ++j) acc += a[j * nb + tid] * __ldg(F + j * Ls + c);
+        const T w2 = X[c * n + p] - Lam2[c * n + p];
+        const T l2 = acc - w2;
+        Lam2[c * n + p] = l2;
+        U2[c * n + p] = acc + l2;
+    }
+    // P1 and Lambda1
+    const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+    if ((y % d) == 0 && (x % d) == 0) {
+        const size_t nl = (size_t)(H / d) * (W / d);
+        const size_t pl = (size_t)(y / d) * (W / d) + x / d;
+        for (int j = 0; j < Ls; ++j)
+            a[j * nb + tid] = rho * (BX[j * n + p] - Lam1[j * n + p]) + D9a[j * nl + pl];
+        for (int c = 0; c < Ls; ++c) {
+            T acc = T(0);
+            for (int j = 0; j < Ls; ++j) acc += a[j * nb + tid] * __ldg(M1 + j * Ls + c);
+            const T w1 = BX[c * n + p] - Lam1[c * n + p];
+            const T l1 = acc - w1;
+            Lam1[c * n + p] = l1;
+            U1[c * n + p] = acc + l1;
+        }
+    } else {
+        for (int c = 0; c < Ls; ++c) {
+            const T w1 = BX[c * n + p] - Lam1[c * n + p];   // P1 = w1, Lambda1 = 0
+            Lam1[c * n + p] = T(0);
+            U1[c * n + p] = w1;
+        }
+    }
+}
+
+// out[c][p] = sum_l in[l][p] M[l][c] for every pixel p (band mixing: S^T Y_l E^T,
+// lambda1/rho Y_h R^T E^T, Z = X E).  M is Lin x Lout row-major.
+template <typename T>
+__global__ void __launch_bounds__(128)
+band_mix_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ M, size_t npix,
+                int Lin, int Lout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* a = reinterpret_cast<T*>(smem_raw);     // [Lin][blockDim]
+    const int tid = threadIdx.x, nb = blockDim.x;
+    const size_t p = (size_t)blockIdx.x * nb + tid;
+    if (p >= npix) return;
+    for (int l = 0; l < Lin; ++l) a[l * nb + tid] = in[l * npix + p];
+    for (int c = 0; c < Lout; ++c) {
+        T acc = T(0);
+        for (int l = 0; l < Lin; ++l) acc += a[l * nb + tid] * __ldg(M + (size_t)l * Lout + c);
+        out[(size_t)c * npix + p] = acc;
+    }
+}
+
+}  // namespace fuse

@@ -1,0 +1,311 @@
+"""Python binding of the C-ABI in include/fuse.h (ctypes; argument marshalling only).
+
+One Python function per C entry point, with the same name.  Device buffers are passed as
+integer device addresses (e.g. torch.Tensor.data_ptr()), streams as integer cudaStream_t
+handles (torch.cuda.current_stream().cuda_stream).  Every step of the solve runs inside
+libfuse.so; if the library is missing this module raises instead of computing anything.
+
+`Fusion` wraps a context for torch tensors: it checks device, dtype and contiguity and
+forwards pointers and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+LIB_PATH = pathlib.Path(__file__).resolve().parent / "_build" / "libfuse.so"
+
+FUSE_OK, FUSE_EINVAL, FUSE_ENOMEM, FUSE_ECUDA = 0, 1, 2, 3
+FUSE_ETIMEOUT, FUSE_ENONFINITE, FUSE_ESTATE, FUSE_EUNSUPPORTED = 4, 5, 6, 7
+FUSE_F32, FUSE_F64, FUSE_BF16 = 0, 1, 2
+FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
+FUSE_K_ALL, FUSE_K_LATENT = 0, 1
+
+DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
+
+
+class fuse_geometry(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("L_l", ctypes.c_int),
+                ("L_h", ctypes.c_int), ("L_s", ctypes.c_int), ("L_guide", ctypes.c_int)]
+
+
+class FuseError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_ST = ctypes.c_int
+
+
+def load(path: str | pathlib.Path | None = None):
+    """Load libfuse.so (built by paper_2210_04184_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = pathlib.Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"{p} is missing: the CUDA library must be built (build.build()) "
+                           "before the solver can run")
+    lib = ctypes.CDLL(str(p))
+    sig = {
+        "fuse_workspace_bytes": (_ST, [ctypes.POINTER(fuse_geometry), _I, _I, _I, _I, _I,
+                                       ctypes.POINTER(ctypes.c_size_t)]),
+        "fuse_init": (_ST, [ctypes.POINTER(_VP), ctypes.POINTER(fuse_geometry), _D, _I, _I, _I, _D, _D,
+                            _I, _I, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                            _I, _I, _VP]),
+        "fuse_destroy": (_ST, [_VP]),
+        "fuse_set_stream": (_ST, [_VP, _VP]),
+        "fuse_weights": (_ST, [_VP, _VP]),
+        "fuse_set_weights": (_ST, [_VP, _VP]),
+        "fuse_get_weights": (_ST, [_VP, _VP]),
+        "fuse_solve": (_ST, [_VP, _VP, _VP, _I, _I, _VP, _VP]),
+        "fuse_run_host": (_ST, [_VP, _VP, _VP, _VP, _I, _VP, _VP]),
+        "fuse_objective": (_ST, [_VP, _VP, _VP, _D]),
+        "fuse_state_bytes": (_ST, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+        "fuse_get_state": (_ST, [_VP, _VP]),
+        "fuse_set_state": (_ST, [_VP, _VP]),
+        "fuse_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
+        "fuse_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
+        "fuse_last_error": (ctypes.c_char_p, [_VP]),
+        "fuse_reset_error": (_ST, [_VP]),
+        "fuse_status_string": (ctypes.c_char_p, [_I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["FUSE_OK", "FUSE_EINVAL", "FUSE_ENOMEM", "FUSE_ECUDA", "FUSE_ETIMEOUT",
+             "FUSE_ENONFINITE", "FUSE_ESTATE", "FUSE_EUNSUPPORTED"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(st: int, ctx=None):
+    if st != FUSE_OK:
+        msg = ""
+        if ctx is not None and _lib is not None:
+            raw = _lib.fuse_last_error(ctx)
+            msg = raw.decode() if raw else ""
+        raise FuseError(st, msg)
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data_as(_D), a          # keep `a` alive alongside the pointer
+
+
+# ----- one function per entry point --------------------------------------------------------
+
+def fuse_workspace_bytes(geom: fuse_geometry, K: int, S: int, ratio: int, dtype: int, wdtype: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().fuse_workspace_bytes(ctypes.byref(geom), K, S, ratio, dtype, wdtype, ctypes.byref(out)))
+    return out.value
+
+
+def fuse_init(geom: fuse_geometry, blur: np.ndarray, ratio: int, R: np.ndarray, E: np.ndarray | None,
+              K: int, S: int, lambda1: float, lambda2: float, rho: float, h: float,
+              dtype: int, wdtype: int, stream: int = 0):
+    blur = np.ascontiguousarray(blur, dtype=np.float64)
+    pb, kb = _dptr(blur)
+    pr, kr = _dptr(R)
+    pe, ke = _dptr(E) if E is not None else (None, None)
+    ctx = _VP()
+    st = load().fuse_init(ctypes.byref(ctx), ctypes.byref(geom), pb, blur.shape[0], blur.shape[1], ratio,
+                          pr, pe, K, S, lambda1, lambda2, rho, h, dtype, wdtype, _VP(stream or None))
+    _check(st)
+    return ctx
+
+
+def fuse_destroy(ctx):
+    _check(load().fuse_destroy(ctx))
+
+
+def fuse_set_stream(ctx, stream: int):
+    _check(load().fuse_set_stream(ctx, _VP(stream or None)), ctx)
+
+
+def fuse_weights(ctx, guide_dev: int):
+    _check(load().fuse_weights(ctx, _VP(guide_dev)), ctx)
+
+
+def fuse_set_weights(ctx, w_dev: int):
+    _check(load().fuse_set_weights(ctx, _VP(w_dev)), ctx)
+
+
+def fuse_get_weights(ctx, w_dev: int):
+    _check(load().fuse_get_weights(ctx, _VP(w_dev)), ctx)
+
+
+def fuse_solve(ctx, Yl_dev: int, Yh_dev: int, iters: int, warm: int, X_out: int | None, Z_out: int | None):
+    _check(load().fuse_solve(ctx, _VP(Yl_dev), _VP(Yh_dev), iters, warm, _VP(X_out or None),
+                             _VP(Z_out or None)), ctx)
+
+
+def fuse_run_host(ctx, Yl_host: int, Yh_host: int, guide_host: int | None, iters: int,
+                  X_host: int | None, Z_host: int | None):
+    _check(load().fuse_run_host(ctx, _VP(Yl_host), _VP(Yh_host), _VP(guide_host or None), iters,
+                                _VP(X_host or None), _VP(Z_host or None)), ctx)
+
+
+def fuse_objective(ctx, Yl_dev: int, Yh_dev: int) -> np.ndarray:
+    out = np.zeros(4)
+    _check(load().fuse_objective(ctx, _VP(Yl_dev), _VP(Yh_dev), out.ctypes.data_as(_D)), ctx)
+    return out
+
+
+def fuse_state_bytes(ctx) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().fuse_state_bytes(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def fuse_get_state(ctx, dst: int):
+    _check(load().fuse_get_state(ctx, _VP(dst)), ctx)
+
+
+def fuse_set_state(ctx, src: int):
+    _check(load().fuse_set_state(ctx, _VP(src)), ctx)
+
+
+def fuse_set_option(ctx, option: int, value: int):
+    _check(load().fuse_set_option(ctx, option, value), ctx)
+
+
+def fuse_profile(ctx, which: int, reset: bool = False) -> tuple[float, int]:
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(load().fuse_profile(ctx, which, ctypes.byref(ms), ctypes.byref(n), int(reset)), ctx)
+    return ms.value, n.value
+
+
+def fuse_last_error(ctx) -> str:
+    raw = load().fuse_last_error(ctx)
+    return raw.decode() if raw else ""
+
+
+def fuse_reset_error(ctx):
+    _check(load().fuse_reset_error(ctx))
+
+
+def fuse_status_string(status: int) -> str:
+    return load().fuse_status_string(status).decode()
+
+
+# ----- torch convenience wrapper (marshalling only) ----------------------------------------
+
+class Fusion:
+    """One solver context bound to the current CUDA device and stream.
+
+    Arrays: images planar (L, H, W); blur (bh, bw); R (L_l, L_h); E (L_s, L_l) or None."""
+
+    def __init__(self, *, H, W, L_l, L_h, L_s, blur, ratio, R, E, K, S, lam1, lam2, rho, h,
+                 dtype="f32", wdtype="bf16", L_guide=None, stream=None):
+        import torch
+        self.torch = torch
+        self.geom = fuse_geometry(H, W, L_l, L_h, L_s, L_guide or L_h)
+        self.H, self.W, self.L_l, self.L_h, self.L_s, self.ratio = H, W, L_l, L_h, L_s, ratio
+        self.K, self.S = K, S
+        self.nW = (2 * S + 1) ** 2 - 1
+        self.dtype = dtype
+        self.wdtype = wdtype
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.wtdtype = {"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}[wdtype]
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.ctx = fuse_init(self.geom, blur, ratio, R, E, K, S, lam1, lam2, rho, h,
+                             DTYPES[dtype], DTYPES[wdtype], s)
+
+    @classmethod
+    def from_problem(cls, p, dtype="f32", wdtype="bf16", **kw):
+        return cls(H=p.H, W=p.W, L_l=p.L_l, L_h=p.L_h, L_s=p.L_s, blur=p.blur, ratio=p.d, R=p.R, E=p.E,
+                   K=p.K, S=p.S, lam1=p.lam1, lam2=p.lam2, rho=p.rho, h=p.h, dtype=dtype, wdtype=wdtype, **kw)
+
+    def _t(self, a, shape=None, dtype=None):
+        t = self.torch
+        dtype = dtype or self.tdtype
+        if not isinstance(a, t.Tensor):
+            a = t.as_tensor(np.asarray(a), dtype=dtype, device="cuda")
+        if a.device.type != "cuda" or a.dtype != dtype or not a.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA tensor of {dtype}")
+        if shape is not None and tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+        return a
+
+    def _sync_stream(self):
+        fuse_set_stream(self.ctx, self.torch.cuda.current_stream().cuda_stream)
+
+    def weights(self, guide):
+        g = self._t(guide, (self.geom.L_guide, self.H, self.W))
+        self._sync_stream()
+        fuse_weights(self.ctx, g.data_ptr())
+        return g
+
+    def set_weights(self, w):
+        w = self._t(w, (self.nW, self.H, self.W), self.wtdtype)
+        self._sync_stream()
+        fuse_set_weights(self.ctx, w.data_ptr())
+
+    def get_weights(self):
+        w = self.torch.empty((self.nW, self.H, self.W), dtype=self.wtdtype, device="cuda")
+        self._sync_stream()
+        fuse_get_weights(self.ctx, w.data_ptr())
+        return w
+
+    def solve(self, Yl, Yh, iters, warm=False, want_X=True, want_Z=False):
+        d = self.ratio
+        yl = self._t(Yl, (self.L_l, self.H // d, self.W // d))
+        yh = self._t(Yh, (self.L_h, self.H, self.W))
+        X = self.torch.empty((self.L_s, self.H, self.W), dtype=self.tdtype, device="cuda") if want_X else None
+        Z = self.torch.empty((self.L_l, self.H, self.W), dtype=self.tdtype, device="cuda") if want_Z else None
+        self._sync_stream()
+        fuse_solve(self.ctx, yl.data_ptr(), yh.data_ptr(), iters, int(warm),
+                   X.data_ptr() if X is not None else None, Z.data_ptr() if Z is not None else None)
+        self._keep = (yl, yh)
+        return X, Z
+
+    def objective(self, Yl, Yh):
+        d = self.ratio
+        yl = self._t(Yl, (self.L_l, self.H // d, self.W // d))
+        yh = self._t(Yh, (self.L_h, self.H, self.W))
+        self._sync_stream()
+        return fuse_objective(self.ctx, yl.data_ptr(), yh.data_ptr())
+
+    def get_state(self):
+        nb = fuse_state_bytes(self.ctx)
+        buf = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+        self._sync_stream()
+        fuse_get_state(self.ctx, buf.data_ptr())
+        return buf
+
+    def set_state(self, buf):
+        self._sync_stream()
+        fuse_set_state(self.ctx, buf.data_ptr())
+
+    def profile(self, which=FUSE_K_LATENT, reset=False):
+        return fuse_profile(self.ctx, which, reset)
+
+    def set_option(self, option, value):
+        fuse_set_option(self.ctx, option, value)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fuse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

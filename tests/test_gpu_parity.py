@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle, element by element.
+
+Tolerances: FP32 iterates within 1e-5 relative Frobenius error of the FP64 oracle at the same
+iteration count; FP64 within 1e-11.  Sizes span several latent row tiles, two 32x32 stencil
+tiles and mixed-radix FFT lengths with ragged tails."""
+import numpy as np
+import pytest
+
+from paper_2210_04184_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import nlpr  # noqa: E402
+from paper_2210_04184_gb300 import build as _build  # noqa: E402
+from paper_2210_04184_gb300.fuse import Fusion, FUSE_OPT_GRAPH  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_solve(p, iters, dtype="f32", wdtype="f32", omega=None, want_state=False, graph=True):
+    f = Fusion.from_problem(p, dtype=dtype, wdtype=wdtype)
+    if not graph:
+        f.set_option(FUSE_OPT_GRAPH, 0)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    yl = torch.tensor(p.Yl, dtype=td, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=td, device="cuda")
+    if omega is None:
+        f.weights(yh)
+    else:
+        f.set_weights(torch.tensor(omega, dtype=f.wtdtype, device="cuda"))
+    X, Z = f.solve(yl, yh, iters, want_Z=True)
+    torch.cuda.synchronize()
+    out = dict(X=X.double().cpu().numpy(), Z=Z.double().cpu().numpy(), f=f, yl=yl, yh=yh)
+    if want_state:
+        out["state"] = f.get_state().cpu().numpy()
+    return out
+
+
+def oracle_solve(p, iters, omega=None):
+    om = omega if omega is not None else nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    X, st, su = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S,
+                          p.lam1, p.lam2, p.rho, om, iters, fast=True)
+    return nlpr.to_lhw(X), st, om
+
+
+def small(**kw):
+    base = dict(H=40, W=40, L_l=6, L_h=2, L_s=3, d=4, blur_size=5, blur_sigma=1.0, K=1, S=2,
+                lam1=1.0, lam2=1e-2, rho=5e-2, h=0.3, seed=11)
+    base.update(kw)
+    return synth.make_problem(**base)
+
+
+# ------------------------------------------------------------------------------ weights
+
+
+@pytest.mark.parametrize("K,S,H,W", [(1, 2, 40, 40), (2, 3, 36, 64), (0, 1, 24, 20)])
+def test_weights_f32_match_oracle(K, S, H, W):
+    p = small(K=K, S=S, H=H, W=W)
+    f = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+    f.weights(torch.tensor(p.Yh, dtype=torch.float32, device="cuda"))
+    w = f.get_weights().double().cpu().numpy()
+    ref = nlpr.weights(nlpr.to_hwl(p.Yh), K, S, p.h)
+    assert w.shape == ref.shape
+    assert np.abs(w - ref).max() <= 2e-6
+
+
+def test_weights_f64_match_oracle():
+    p = small(K=2, S=3, H=36, W=64)
+    f = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    f.weights(torch.tensor(p.Yh, dtype=torch.float64, device="cuda"))
+    w = f.get_weights().cpu().numpy()
+    ref = nlpr.weights(nlpr.to_hwl(p.Yh), 2, 3, p.h)
+    assert np.abs(w - ref).max() <= 1e-13
+
+
+def test_weights_bf16_rounding():
+    # Both sides round to bf16 (round to nearest even).  The values agree exactly except where
+    # the FP32 and FP64 weights straddle a rounding boundary; there they differ by one bf16 step
+    # and the FP64 value lies within FP32 error of the midpoint.
+    p = small(K=2, S=3, H=48, W=64)
+    f = Fusion.from_problem(p, dtype="f32", wdtype="bf16")
+    f.weights(torch.tensor(p.Yh, dtype=torch.float32, device="cuda"))
+    w = f.get_weights().double().cpu().numpy()
+    ref64 = nlpr.weights(nlpr.to_hwl(p.Yh), 2, 3, p.h)
+    ref = nlpr.round_bf16(ref64)
+    diff = w != ref
+    assert diff.mean() < 1e-3
+    if diff.any():
+        step = np.abs(w[diff] - ref[diff])
+        ulp = np.ldexp(1.0, np.frexp(ref64[diff])[1] - 8)
+        assert np.all(step <= ulp * 1.0001)
+        mid = (w[diff] + ref[diff]) / 2
+        assert np.all(np.abs(ref64[diff] - mid) <= 1e-6 * np.abs(mid))
+
+
+# ------------------------------------------------------------------------------ solve parity
+
+
+@pytest.mark.parametrize("iters", [1, 2, 3])
+def test_first_iterations_state_parity(iters):
+    # Element-by-element state after 1, 2, 3 iterations (X update, P1/P2, duals, latent pass).
+    p = small()
+    g = gpu_solve(p, iters, want_state=True)
+    Xo, st, _ = oracle_solve(p, iters)
+    n = p.H * p.W
+    Ls = p.L_s
+    s = g["state"].view(np.float32).astype(np.float64)
+    img = n * Ls
+    lam1, u1, lam2, u2, xs = (s[i * img:(i + 1) * img].reshape(Ls, p.H, p.W) for i in range(5))
+    scale = max(np.abs(Xo).max(), 1e-3)
+    assert np.abs(g["X"] - Xo).max() <= 2e-6 * max(scale, np.abs(nlpr.to_lhw(st.P2)).max())
+    assert np.abs(lam1 - nlpr.to_lhw(st.Lam1)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P1)).max()
+    assert np.abs(u1 - nlpr.to_lhw(st.P1 + st.Lam1)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P1)).max()
+    assert np.abs(lam2 - nlpr.to_lhw(st.Lam2)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P2)).max()
+    assert np.abs(u2 - nlpr.to_lhw(st.P2 + st.Lam2)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P2)).max()
+    # latent state, stored re-indexed by source pixel: Sig'_{tau k}(m) = Sigma_{tau k}(m + k)
+    nW, nP = len(nlpr.search_offsets(p.S)), len(nlpr.patch_offsets(p.K))
+    sig = s[5 * img:5 * img + nW * nP * img].reshape(nW, nP, Ls, p.H, p.W)
+    for t in range(nW):
+        for kk, k in enumerate(nlpr.patch_offsets(p.K)):
+            ref = nlpr.to_lhw(np.roll(st.Sig[t, kk], shift=(-k[0], -k[1]), axis=(0, 1)))
+            assert np.abs(sig[t, kk] - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+CASES = {
+    # several latent row tiles with a ragged last tile, odd L_s (padded FFT pair), radix 4*2*5
+    "40x40_K1S2": dict(H=40, W=40, L_l=6, L_h=2, L_s=3, K=1, S=2, iters=30),
+    # 5x5 patches, 7x7 window, 9x9 blur, several tiles, radix 4*4*3 and 4*4*4
+    "48x64_K2S3": dict(H=48, W=64, L_l=8, L_h=3, L_s=4, K=2, S=3, blur_size=9, blur_sigma=1.7, iters=30),
+    # radix-5 and radix-3 lengths, K = 0 (pixel differences)
+    "60x20_K0S1": dict(H=60, W=20, L_l=5, L_h=2, L_s=2, K=0, S=1, iters=25),
+    # lambda2 = 0 (the latent pass still runs: Sigma stays 0, G = D X)
+    "32x32_lam0": dict(H=32, W=32, L_l=4, L_h=2, L_s=2, K=1, S=1, lam2=0.0, iters=20),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp32_parity(name):
+    kw = dict(CASES[name])
+    iters = kw.pop("iters")
+    p = small(**kw)
+    g = gpu_solve(p, iters)
+    Xo, _, _ = oracle_solve(p, iters)
+    assert rel(g["X"], Xo) <= 1e-5
+    Zo = np.einsum("chw,cl->lhw", Xo, p.E)
+    assert rel(g["Z"], Zo) <= 1e-5
+
+
+def test_fp64_parity():
+    p = small(H=40, W=36, L_l=5, L_h=2, L_s=3, K=1, S=2)
+    g = gpu_solve(p, 25, dtype="f64", wdtype="f64")
+    Xo, _, _ = oracle_solve(p, 25)
+    assert rel(g["X"], Xo) <= 1e-11
+
+
+def test_identity_subspace_and_ratio2():
+    p = synth.make_problem(H=24, W=24, L_l=3, L_h=2, L_s=3, d=2, blur_size=3, blur_sigma=0.8, K=1, S=1,
+                           lam1=0.7, lam2=2e-2, rho=0.1, h=0.4, seed=5, E_identity=True)
+    g = gpu_solve(p, 20)
+    Xo, _, _ = oracle_solve(p, 20)
+    assert rel(g["X"], Xo) <= 1e-5
+
+
+def test_bf16_weights_parity_with_shared_weights():
+    # The oracle's FP64 weights rounded to bf16 are loaded into both sides.
+    p = small(H=64, W=64, L_l=10, L_h=4, L_s=5, K=2, S=3, blur_size=9, blur_sigma=1.7)
+    om = nlpr.round_bf16(nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h))
+    g = gpu_solve(p, 40, wdtype="bf16", omega=om)
+    Xo, _, _ = oracle_solve(p, 40, omega=om)
+    assert rel(g["X"], Xo) <= 1e-5
+
+
+def test_iters_zero_returns_zero():
+    p = small()
+    g = gpu_solve(p, 0)
+    assert not np.any(g["X"])
+
+
+def test_graph_and_direct_launch_bitwise_equal():
+    p = small()
+    a = gpu_solve(p, 12, graph=True)["X"]
+    b = gpu_solve(p, 12, graph=False)["X"]
+    assert np.array_equal(a, b)
+
+
+def test_run_to_run_deterministic():
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4)
+    a = gpu_solve(p, 10)["X"]
+    b = gpu_solve(p, 10)["X"]
+    assert np.array_equal(a, b)
