@@ -200,6 +200,11 @@ WORKLOADS = {
     "hspan_512": dict(H=512, W=512, L_l=128, L_h=1, L_s=20, d=4, blur_size=11, blur_sigma=2.0,
                       snr_l=30.0, snr_h=30.0, K=2, S=5, iters=200, kind="hspan",
                       dtype="f32", wdtype="bf16", cfg=2),
+    # The HS+MS workload at 128 x 128 (same bands, windows and iterations): latent state 1.6 GB,
+    # above L2 but small enough for detailed profiler captures.
+    "hsms_128": dict(H=128, W=128, L_l=93, L_h=4, L_s=20, d=4, blur_size=9, blur_sigma=1.7,
+                     snr_l=35.0, snr_h=35.0, K=2, S=3, iters=100, kind="hsms",
+                     dtype="f32", wdtype="bf16", cfg=1),
     # Unrolled forward of the differentiable form: Z 256x256x31, MS 3 bands, sigma 1.5,
     # patch 3x3, search 3x3 (S=1), 20 iterations, L_s = 8.
     "unrolled_256": dict(H=256, W=256, L_l=31, L_h=3, L_s=8, d=4, blur_size=9, blur_sigma=1.5,
