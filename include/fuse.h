@@ -69,8 +69,12 @@ typedef struct fuse_ctx fuse_ctx;
 
 /* Options for fuse_set_option. */
 enum {
-    FUSE_OPT_PROFILE = 1,   /* value 1: time every latent-pass launch with CUDA events */
-    FUSE_OPT_GRAPH = 2      /* value 1 (default): replay iterations from a captured CUDA graph */
+    FUSE_OPT_PROFILE = 1,        /* 1: time every latent-pass launch with CUDA events (no graph) */
+    FUSE_OPT_GRAPH = 2,          /* 1 (default): replay iterations from a captured CUDA graph */
+    FUSE_OPT_LATENT_IMPL = 3,    /* latent pass: 1 (default) bulk-copy ring, 0 register-staged loads */
+    FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 256) */
+    FUSE_OPT_LATENT_STAGES = 5,  /* ring slots of the bulk-copy latent pass, 2..32 (default 8) */
+    FUSE_OPT_WAIT_LIMIT = 6      /* polls before a device barrier wait gives up (default 2^22) */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -164,13 +168,24 @@ fuse_status fuse_state_bytes(fuse_ctx* ctx, size_t* bytes);
 fuse_status fuse_get_state(fuse_ctx* ctx, void* dst);
 fuse_status fuse_set_state(fuse_ctx* ctx, const void* src);
 
-/* Options (FUSE_OPT_*). */
+/* Options (FUSE_OPT_*).  Launch options that do not fit the problem return FUSE_EINVAL and
+ * leave the previous setting in place. */
 fuse_status fuse_set_option(fuse_ctx* ctx, int option, long long value);
+
+/* Wait for all work issued on the context's stream and report device-side failures:
+ * FUSE_ETIMEOUT if a bounded barrier wait inside a kernel gave up since the last check
+ * (the results of that work are then invalid), FUSE_ECUDA on an execution error. */
+fuse_status fuse_sync(fuse_ctx* ctx);
 
 /* Profile counters since the last reset: kernel group `which` (FUSE_K_*): total device time
  * in ms (only with FUSE_OPT_PROFILE, else 0) and launch count.  Synchronises the stream.
  * reset != 0 clears the counters after reading. */
 fuse_status fuse_profile(fuse_ctx* ctx, int which, double* ms, long long* launches, int reset);
+
+/* Device self-check.  which = 1: a kernel waits (bounded) on a barrier that nothing completes;
+ * returns FUSE_OK when the wait gave up and its timeout was reported to the host as designed,
+ * leaving the context usable.  Synchronous. */
+fuse_status fuse_selftest(fuse_ctx* ctx, int which);
 
 /* Last error text of the context ("" if none); valid until the next call on ctx. */
 const char* fuse_last_error(const fuse_ctx* ctx);

@@ -74,6 +74,12 @@ struct fuse_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int fault_alloc = -1, alloc_count = 0;
+    // latent pass variant: 0 = register-staged loads, 1 = bulk-copy (TMA) ring
+    int lat_impl = 1, lat_target = 256, lat_stages = 8;
+    int lt_Ty = 1, lt_ncons = 0;
+    size_t lt_smem = 0;
+    int* d_err = nullptr;
+    unsigned wait_limit = 1u << 22;
 };
 
 namespace {
@@ -251,6 +257,24 @@ Sizes sizes_of(const fuse_geometry* g, int K, int S, int ratio, size_t esz, size
     return z;
 }
 
+// Launch shape of the bulk-copy latent pass: about `target` consumer threads per block (full
+// rows), `stages` ring slots; false if it does not fit in shared memory.
+bool latent_tma_shape(fuse_ctx* c) {
+    const int tpr = c->W / c->vec;
+    int Ty = c->lat_target / tpr;
+    if (Ty < 1) Ty = 1;
+    if (Ty > c->H) Ty = c->H;
+    while (Ty > 1 && ((tpr * Ty + 31) / 32) * 32 + 32 > 288) --Ty;
+    const int ncons = ((tpr * Ty + 31) / 32) * 32;
+    if (ncons + 32 > 288) return false;
+    const size_t smem = (size_t)(c->lat_stages + 2 * c->S + 1) * Ty * c->W * c->esz + 2 * (size_t)c->lat_stages * 8;
+    if (smem > (size_t)kMaxSmem || c->lat_stages < 1) return false;
+    c->lt_Ty = Ty;
+    c->lt_ncons = ncons;
+    c->lt_smem = smem;
+    return true;
+}
+
 // ---------------------------------------------------------------------------------------
 // typed launch sequence
 // ---------------------------------------------------------------------------------------
@@ -271,11 +295,17 @@ struct Impl {
     template <typename WT>
     static fuse_status set_attrs_w(fuse_ctx* c) {
         CK(c, cudaFuncSetAttribute(weights_kernel<T, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->w_smem));
+        constexpr int V = 16 / sizeof(T);
+        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
         switch (c->K) {
-            case 0: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 0, 16 / sizeof(T)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->lat_smem)); break;
-            case 1: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 1, 16 / sizeof(T)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->lat_smem)); break;
-            case 2: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 2, 16 / sizeof(T)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->lat_smem)); break;
-            default: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 3, 16 / sizeof(T)>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->lat_smem)); break;
+            case 0: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 0, V>, A, (int)c->lat_smem));
+                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 0, V>, A, kMaxSmem)); break;
+            case 1: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 1, V>, A, (int)c->lat_smem));
+                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 1, V>, A, kMaxSmem)); break;
+            case 2: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 2, V>, A, (int)c->lat_smem));
+                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 2, V>, A, kMaxSmem)); break;
+            default: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 3, V>, A, (int)c->lat_smem));
+                     CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 3, V>, A, kMaxSmem)); break;
         }
         return FUSE_OK;
     }
@@ -310,8 +340,26 @@ struct Impl {
             (T)(c->lam2 / c->rho));
     }
 
+    template <typename WT, int K>
+    static void launch_latent_tma(fuse_ctx* c, cudaStream_t s) {
+        constexpr int VEC = 16 / sizeof(T);
+        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)(2 * c->S + 1), (unsigned)c->Ls);
+        latent_tma_kernel<T, WT, K, VEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(
+            (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lt_Ty,
+            c->lt_ncons, c->lat_stages, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit);
+    }
+
     template <typename WT>
     static void latent(fuse_ctx* c, cudaStream_t s) {
+        if (c->lat_impl == 1) {
+            switch (c->K) {
+                case 0: launch_latent_tma<WT, 0>(c, s); break;
+                case 1: launch_latent_tma<WT, 1>(c, s); break;
+                case 2: launch_latent_tma<WT, 2>(c, s); break;
+                default: launch_latent_tma<WT, 3>(c, s); break;
+            }
+            return;
+        }
         switch (c->K) {
             case 0: launch_latent<WT, 0>(c, s); break;
             case 1: launch_latent<WT, 1>(c, s); break;
@@ -708,7 +756,7 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     c->plane_bytes = z.planes;
     void** imgs[] = {&c->X, &c->BX, &c->C, &c->Lam1, &c->U1, &c->Lam2, &c->U2, &c->D9b};
     for (void** p : imgs)
-        if ((st = dalloc(c, p, z.img)) != FUSE_OK) { fuse_status s2 = c->sticky; (void)s2; return bail(st); }
+        if ((st = dalloc(c, p, z.img)) != FUSE_OK) return bail(st);
     if ((st = dalloc(c, &c->Y, z.cimg)) != FUSE_OK) return bail(st);
     if ((st = dalloc(c, &c->Sig, z.sig)) != FUSE_OK) return bail(st);
     if ((st = dalloc(c, &c->planes, z.planes)) != FUSE_OK) return bail(st);
@@ -726,6 +774,13 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     if ((st = upload_any(c, &c->twW, twiddles(W))) != FUSE_OK) return bail(st);
     if ((st = upload<double>(c, (void**)&c->objE, Em)) != FUSE_OK) return bail(st);
     if ((st = upload<double>(c, (void**)&c->objER, ER)) != FUSE_OK) return bail(st);
+    if ((st = dalloc(c, (void**)&c->d_err, sizeof(int))) != FUSE_OK) return bail(st);
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return bail(FUSE_ECUDA); }
+    if (!latent_tma_shape(c)) {
+        c->lat_target = 128;
+        c->lat_stages = 4;
+        if (!latent_tma_shape(c)) c->lat_impl = 0;
+    }
     const size_t nb = (c->n + 255) / 256;
     c->npartial = nb * 3 + nb * (size_t)c->nW;
     if ((st = dalloc(c, (void**)&c->partial, c->npartial * sizeof(double))) != FUSE_OK) return bail(st);
@@ -821,8 +876,7 @@ fuse_status fuse_run_host(fuse_ctx* c, const void* Yl_h, const void* Yh_h, const
     if (st != FUSE_OK) return st;
     if (X_h) CK(c, cudaMemcpyAsync(X_h, c->sX, bx, cudaMemcpyDeviceToHost, c->stream));
     if (Z_h) CK(c, cudaMemcpyAsync(Z_h, c->sZ, bz, cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    return FUSE_OK;
+    return fuse_sync(c);
 }
 
 fuse_status fuse_objective(fuse_ctx* c, const void* Yl, const void* Yh, double out[4]) {
@@ -878,6 +932,29 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
     switch (option) {
         case FUSE_OPT_PROFILE: c->profile = value != 0; return FUSE_OK;
         case FUSE_OPT_GRAPH: c->use_graph = value != 0; return FUSE_OK;
+        case FUSE_OPT_LATENT_IMPL:
+        case FUSE_OPT_LATENT_THREADS:
+        case FUSE_OPT_LATENT_STAGES: {
+            const int old_impl = c->lat_impl, old_t = c->lat_target, old_d = c->lat_stages;
+            if (option == FUSE_OPT_LATENT_IMPL) c->lat_impl = value ? 1 : 0;
+            if (option == FUSE_OPT_LATENT_THREADS) c->lat_target = (int)value;
+            if (option == FUSE_OPT_LATENT_STAGES) c->lat_stages = (int)value;
+            if (c->lat_target < 32 || c->lat_target > 256 || c->lat_stages < 2 || c->lat_stages > 32 ||
+                !latent_tma_shape(c)) {
+                c->lat_impl = old_impl; c->lat_target = old_t; c->lat_stages = old_d;
+                latent_tma_shape(c);
+                return fail(c, FUSE_EINVAL, "latent launch option out of range");
+            }
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
+        }
+        case FUSE_OPT_WAIT_LIMIT:
+            if (value < 1) return fail(c, FUSE_EINVAL, "wait limit must be positive");
+            c->wait_limit = (unsigned)value;
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
         default: return fail(c, FUSE_EINVAL, "unknown option");
     }
 }
@@ -902,6 +979,36 @@ fuse_status fuse_profile(fuse_ctx* c, int which, double* ms, long long* launches
         return fail(c, FUSE_EINVAL, "unknown kernel group");
     }
     if (reset) { c->latent_ms = 0.0; c->launches_latent = 0; c->launches_all = 0; }
+    return FUSE_OK;
+}
+
+fuse_status fuse_sync(fuse_ctx* c) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    CK(c, cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    CK(c, cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        return fail(c, FUSE_ETIMEOUT, "a bounded device-side barrier wait gave up");
+    }
+    return FUSE_OK;
+}
+
+fuse_status fuse_selftest(fuse_ctx* c, int which) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (which != 1) return fail(c, FUSE_EINVAL, "unknown self-test");
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    wait_selftest_kernel<<<1, 32, 0, c->stream>>>(c->d_err, 1000u, 2);
+    c->launches_all++;
+    CKL(c, "wait_selftest_kernel");
+    CK(c, cudaStreamSynchronize(c->stream));
+    int flag = 0;
+    CK(c, cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    if (flag != 2) return fail(c, FUSE_ECUDA, "bounded wait did not report its timeout");
     return FUSE_OK;
 }
 

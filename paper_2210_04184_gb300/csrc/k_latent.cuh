@@ -122,3 +122,174 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
 }
 
 }  // namespace fuse
+
+// ---------------------------------------------------------------------------------------
+// Pipelined form of the same pass: the latent state is streamed through a shared-memory ring
+// by bulk asynchronous copies (cp.async.bulk, 1D TMA), issued by one producer warp, so the
+// number of bytes in flight no longer depends on registers.  One chunk = the block's rows of
+// one (tau, k) plane of Sig' (Ty*W contiguous elements).  Consumers wait on the chunk's
+// `full` barrier, update their VEC elements, store them back with streaming 16-byte stores
+// and release the slot through its `empty` barrier (one arrival per consumer warp).
+// Every barrier wait is bounded (`limit` polls); a timeout sets bit 1 of *err and the kernel
+// still finishes in bounded time.
+#include "tma.cuh"
+
+namespace fuse {
+
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(288)
+latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restrict__ Sig,
+                  T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, int ncons, int D, T coef,
+                  int* __restrict__ err, unsigned limit) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    constexpr int PS = 2 * K + 1;
+    constexpr int NP = PS * PS;
+    const int side = 2 * S + 1;
+    const int tile = Ty * W;
+    T* ring = reinterpret_cast<T*>(smem_tma);                 // [D][Ty][W]
+    T* Hs = ring + (size_t)D * tile;                          // [(2S+1)][Ty][W]
+    uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)side * tile);
+    uint64_t* empty = full + D;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x;
+    const int tpr = W / VEC;
+    const int y0 = blockIdx.x * Ty;
+    const int rows = min(Ty, H - y0);
+    const int t1 = (int)blockIdx.y - S;
+    const int c = blockIdx.z;
+    const size_t n = (size_t)H * W;
+    const int centre = (side * side) / 2;
+    const int nt2 = t1 == 0 ? side - 1 : side;
+    const int nq = nt2 * NP;
+    const unsigned bytes = (unsigned)(rows * W * (int)sizeof(T));
+
+    // consumer geometry (threads >= tpr*Ty own no pixels)
+    const int r = tid / tpr;
+    const int x0 = (tid - r * tpr) * VEC;
+    const int y = y0 + r;
+    const bool owner = tid < tpr * Ty;
+    const bool active = owner && r < rows;
+    T A[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) A[j] = T(0);
+
+    if (tid == 0) {
+        for (int s = 0; s < D; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], (unsigned)(ncons / 32));
+        }
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (tid >= ncons) {
+        // ---------------- producer warp: one lane issues the bulk copies ----------------
+        if (tid == ncons) {
+            const uint64_t pol = l2_evict_first_policy();
+            int issued = 0;
+            for (int q = 0; q < nq; ++q) {
+                if (s_abort) break;                 // never re-arm a barrier after a timeout
+                const int slot = q % D;
+                if (q >= D && !mbar_wait(&empty[slot], (unsigned)((q / D - 1) & 1), limit, err, 1)) {
+                    s_abort = 1;
+                    break;
+                }
+                const int j = q / NP, kidx = q - j * NP;
+                const int t2 = (t1 == 0 && j >= S) ? j - S + 1 : j - S;
+                const int cell = (t1 + S) * side + (t2 + S);
+                const int tidx = cell > centre ? cell - 1 : cell;
+                const T* src = Sig + ((size_t)(tidx * NP + kidx) * Ls + c) * n + (size_t)y0 * W;
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                tma_load_1d(ring + (size_t)slot * tile, src, bytes, &full[slot], pol);
+                issued = q + 1;
+            }
+            // drain: no bulk copy of this block may still be in flight when it exits; copies of
+            // valid memory always land, so the bound here is generous whatever `limit` is
+            const unsigned dlim = limit > (1u << 20) ? limit : (1u << 20);
+            for (int q = issued > D ? issued - D : 0; q < issued; ++q)
+                if (!mbar_wait(&full[q % D], (unsigned)((q / D) & 1), dlim, err, 1)) break;
+        }
+    } else {
+        // ---------------- consumers ----------------
+        const int lane = tid & 31;
+        const T* Xc = X + (size_t)c * n;
+        T Xm[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) Xm[j] = active ? Xc[(size_t)y * W + x0 + j] : T(0);
+        int slot = 0;
+        unsigned par = 0;
+        for (int t2 = -S; t2 <= S; ++t2) {
+            T Hacc[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
+            if (t1 != 0 || t2 != 0) {
+                const int cell = (t1 + S) * side + (t2 + S);
+                const int tidx = cell > centre ? cell - 1 : cell;
+                T delta[VEC];
+                const int ys = wrap1(y - t1, H);
+#pragma unroll
+                for (int j = 0; j < VEC; ++j)
+                    delta[j] = active ? Xm[j] - Xc[(size_t)ys * W + wrap1(x0 + j - t2, W)] : T(0);
+                const WT* om = omega + (size_t)tidx * n;
+                T* gp = Sig + ((size_t)tidx * NP * Ls + c) * n + (size_t)y * W + x0;
+                const size_t kstride = (size_t)Ls * n;
+#pragma unroll
+                for (int k1 = -K; k1 <= K; ++k1) {
+                    T mu[VEC + 2 * K];
+                    const int yw = wrap1(y + k1, H);
+#pragma unroll
+                    for (int j = 0; j < VEC + 2 * K; ++j)
+                        mu[j] = active ? coef * (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W)) : T(0);
+#pragma unroll
+                    for (int k2 = 0; k2 < PS; ++k2) {
+                        const unsigned lim = s_abort ? 64u : limit;
+                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (active) {
+                            vecT<T, VEC> s = *reinterpret_cast<const vecT<T, VEC>*>(
+                                ring + (size_t)slot * tile + (size_t)r * W + x0);
+#pragma unroll
+                            for (int j = 0; j < VEC; ++j) {
+                                const T u = s.v[j] - delta[j];
+                                const T m = mu[j + k2];
+                                const T s2 = tmin(tmax(u, -m), m);
+                                Hacc[j] += T(2) * s2 - u;
+                                s.v[j] = s2;
+                            }
+                            st_stream(reinterpret_cast<vecT<T, VEC>*>(gp), s);
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        gp += kstride;
+                        if (++slot == D) { slot = 0; par ^= 1u; }
+                    }
+                }
+            }
+            if (owner) {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    A[j] += Hacc[j];
+                    Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    T V[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) V[j] = T(0);
+    for (int t2 = -S; t2 <= S; ++t2) {
+        const T* row = Hs + ((size_t)(t2 + S) * Ty + r) * W;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) V[j] += row[wrap1(x0 + j + t2, W)];
+    }
+    vecT<T, VEC> va, vv;
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) { va.v[j] = A[j]; vv.v[j] = V[j]; }
+    *reinterpret_cast<vecT<T, VEC>*>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + (size_t)y * W + x0) = va;
+    *reinterpret_cast<vecT<T, VEC>*>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + (size_t)y * W + x0) = vv;
+}
+
+}  // namespace fuse

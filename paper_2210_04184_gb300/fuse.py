@@ -21,6 +21,7 @@ FUSE_OK, FUSE_EINVAL, FUSE_ENOMEM, FUSE_ECUDA = 0, 1, 2, 3
 FUSE_ETIMEOUT, FUSE_ENONFINITE, FUSE_ESTATE, FUSE_EUNSUPPORTED = 4, 5, 6, 7
 FUSE_F32, FUSE_F64, FUSE_BF16 = 0, 1, 2
 FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
+FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -73,6 +74,8 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_set_state": (_ST, [_VP, _VP]),
         "fuse_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
         "fuse_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
+        "fuse_sync": (_ST, [_VP]),
+        "fuse_selftest": (_ST, [_VP, _I]),
         "fuse_last_error": (ctypes.c_char_p, [_VP]),
         "fuse_reset_error": (_ST, [_VP]),
         "fuse_status_string": (ctypes.c_char_p, [_I]),
@@ -191,6 +194,14 @@ def fuse_profile(ctx, which: int, reset: bool = False) -> tuple[float, int]:
     return ms.value, n.value
 
 
+def fuse_sync(ctx):
+    _check(load().fuse_sync(ctx), ctx)
+
+
+def fuse_selftest(ctx, which: int):
+    _check(load().fuse_selftest(ctx, which), ctx)
+
+
 def fuse_last_error(ctx) -> str:
     raw = load().fuse_last_error(ctx)
     return raw.decode() if raw else ""
@@ -298,6 +309,9 @@ class Fusion:
 
     def set_option(self, option, value):
         fuse_set_option(self.ctx, option, value)
+
+    def sync(self):
+        fuse_sync(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -14,7 +14,8 @@ torch = pytest.importorskip("torch")
 
 from oracle import nlpr  # noqa: E402
 from paper_2210_04184_gb300 import build as _build  # noqa: E402
-from paper_2210_04184_gb300.fuse import Fusion, FUSE_OPT_GRAPH  # noqa: E402
+from paper_2210_04184_gb300.fuse import (Fusion, FUSE_OPT_GRAPH, FUSE_OPT_LATENT_IMPL,  # noqa: E402
+                                         FUSE_OPT_LATENT_STAGES, FUSE_OPT_LATENT_THREADS)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -26,10 +27,12 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def gpu_solve(p, iters, dtype="f32", wdtype="f32", omega=None, want_state=False, graph=True):
+def gpu_solve(p, iters, dtype="f32", wdtype="f32", omega=None, want_state=False, graph=True, opts=()):
     f = Fusion.from_problem(p, dtype=dtype, wdtype=wdtype)
     if not graph:
         f.set_option(FUSE_OPT_GRAPH, 0)
+    for o, v in opts:
+        f.set_option(o, v)
     td = torch.float64 if dtype == "f64" else torch.float32
     yl = torch.tensor(p.Yl, dtype=td, device="cuda")
     yh = torch.tensor(p.Yh, dtype=td, device="cuda")
@@ -38,7 +41,7 @@ def gpu_solve(p, iters, dtype="f32", wdtype="f32", omega=None, want_state=False,
     else:
         f.set_weights(torch.tensor(omega, dtype=f.wtdtype, device="cuda"))
     X, Z = f.solve(yl, yh, iters, want_Z=True)
-    torch.cuda.synchronize()
+    f.sync()
     out = dict(X=X.double().cpu().numpy(), Z=Z.double().cpu().numpy(), f=f, yl=yl, yh=yh)
     if want_state:
         out["state"] = f.get_state().cpu().numpy()
@@ -145,21 +148,23 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("impl", [1, 0])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_fp32_parity(name):
+def test_fp32_parity(name, impl):
     kw = dict(CASES[name])
     iters = kw.pop("iters")
     p = small(**kw)
-    g = gpu_solve(p, iters)
+    g = gpu_solve(p, iters, opts=[(FUSE_OPT_LATENT_IMPL, impl)])
     Xo, _, _ = oracle_solve(p, iters)
     assert rel(g["X"], Xo) <= 1e-5
     Zo = np.einsum("chw,cl->lhw", Xo, p.E)
     assert rel(g["Z"], Zo) <= 1e-5
 
 
-def test_fp64_parity():
+@pytest.mark.parametrize("impl", [1, 0])
+def test_fp64_parity(impl):
     p = small(H=40, W=36, L_l=5, L_h=2, L_s=3, K=1, S=2)
-    g = gpu_solve(p, 25, dtype="f64", wdtype="f64")
+    g = gpu_solve(p, 25, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_LATENT_IMPL, impl)])
     Xo, _, _ = oracle_solve(p, 25)
     assert rel(g["X"], Xo) <= 1e-11
 
@@ -199,3 +204,63 @@ def test_run_to_run_deterministic():
     a = gpu_solve(p, 10)["X"]
     b = gpu_solve(p, 10)["X"]
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("threads,stages", [(32, 2), (64, 3), (256, 4), (128, 16), (256, 8)])
+def test_latent_ring_shapes_bitwise_equal(threads, stages):
+    # The pipelined latent pass gives bit-identical results for every block / ring shape and
+    # matches the register-staged form (same arithmetic per element, same summation order).
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=9, blur_sigma=1.7)
+    ref = gpu_solve(p, 6, opts=[(FUSE_OPT_LATENT_IMPL, 0)])["X"]
+    got = gpu_solve(p, 6, opts=[(FUSE_OPT_LATENT_IMPL, 1), (FUSE_OPT_LATENT_THREADS, threads),
+                                (FUSE_OPT_LATENT_STAGES, stages)])["X"]
+    assert np.array_equal(got, ref)
+
+
+def test_objective_matches_oracle():
+    # fuse_objective: 1/2||Y_l - SBXE||^2, lambda1/2||Y_h - XER||^2, lambda2 phi(X), ||X||^2 at the
+    # final X, against the oracle's terms evaluated at the oracle's X (FP32 iterates: 1e-5).
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=9, blur_sigma=1.7)
+    g = gpu_solve(p, 15)
+    obj = g["f"].objective(g["yl"], g["yh"])
+    Xo, _, om = oracle_solve(p, 15)
+    X = nlpr.to_hwl(Xo)
+    Yl, Yh = nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh)
+    r1 = nlpr.mat(Yl) - nlpr.mat(nlpr.decimate(nlpr.blur(X, p.blur), p.d)) @ p.E
+    r2 = nlpr.mat(Yh) - nlpr.mat(X) @ p.E @ p.R
+    ref = [0.5 * (r1 ** 2).sum(), 0.5 * p.lam1 * (r2 ** 2).sum(), p.lam2 * nlpr.nlpr(X, om, p.K, p.S),
+           (X ** 2).sum()]
+    for a, b in zip(obj, ref):
+        assert abs(a - b) <= 2e-5 * abs(b)
+    total = sum(obj[:3])
+    assert abs(total - nlpr.objective(X, Yl, Yh, p.blur, p.d, p.R, p.E, om, p.K, p.S, p.lam1, p.lam2)) <= 2e-5 * total
+
+
+def test_checkpoint_resume_bitwise():
+    # fuse_get_state / fuse_set_state: stopping after 5 iterations and resuming for 7 more gives
+    # the same bits as 12 uninterrupted iterations.
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4)
+    full = gpu_solve(p, 12)["X"]
+    a = gpu_solve(p, 5)
+    f = a["f"]
+    st = f.get_state()
+    f2 = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+    f2.weights(a["yh"])
+    f2.set_state(st)
+    X, _ = f2.solve(a["yl"], a["yh"], 7, warm=True)
+    f2.sync()
+    assert np.array_equal(X.double().cpu().numpy(), full)
+
+
+def test_run_host_matches_device_path():
+    from paper_2210_04184_gb300.fuse import fuse_run_host
+    p = small()
+    g = gpu_solve(p, 10)
+    f = g["f"]
+    Yl = np.ascontiguousarray(p.Yl, dtype=np.float32)
+    Yh = np.ascontiguousarray(p.Yh, dtype=np.float32)
+    X = np.zeros((p.L_s, p.H, p.W), dtype=np.float32)
+    Z = np.zeros((p.L_l, p.H, p.W), dtype=np.float32)
+    fuse_run_host(f.ctx, Yl.ctypes.data, Yh.ctypes.data, None, 10, X.ctypes.data, Z.ctypes.data)
+    assert np.array_equal(X.astype(np.float64), g["X"])
+    assert np.array_equal(Z.astype(np.float64), g["Z"])
