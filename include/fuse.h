@@ -182,6 +182,26 @@ fuse_status fuse_sync(fuse_ctx* ctx);
  * reset != 0 clears the counters after reading. */
 fuse_status fuse_profile(fuse_ctx* ctx, int which, double* ms, long long* launches, int reset);
 
+/* The regulariser value phi(X) = sum_i sum_{tau in W} omega_{i tau} ||P_{i tau}(X)||_1 written
+ * to phi_dev[0] (device, one double), without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate device memory
+ * (for example while their stream is being captured into a CUDA graph, or inside a host
+ * application that owns a fixed GPU memory budget) and so cannot create a fuse_ctx.
+ *   X_dev      [L_s][H][W] of dtype (FUSE_F32 or FUSE_F64), device
+ *   omega_dev  [|W|][H][W] of wdtype (FUSE_F32/FUSE_BF16 with FUSE_F32, FUSE_F64 with FUSE_F64),
+ *              as produced by fuse_weights / read by fuse_get_weights
+ *   stream     cudaStream_t (as void*), NULL = legacy default stream; asynchronous.
+ * Scratch: per-block partial sums in one file-scope device array of 2^18 doubles (2 MiB),
+ * held on every GPU that loads the library until the process exits.  The problem must need
+ * at most that many partials: ceil(H*W/256) * |W| <= 262144, else FUSE_EUNSUPPORTED (and
+ * no work is issued).  Every call shares the array and overwrites the slots it uses before
+ * reading them; calls whose execution overlaps on the GPU (different streams, or graphs
+ * replayed concurrently) race on it.  The first call on each device looks up the array's
+ * device address (once, with that device current); make that first call before any stream
+ * capture.  Calls no allocating routine.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED, FUSE_ECUDA. */
+fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev, int H, int W, int L_s, int K,
+                            int S, fuse_dtype dtype, fuse_dtype wdtype, double* phi_dev, void* stream);
+
 /* Device self-check.  which = 1: a kernel waits (bounded) on a barrier that nothing completes;
  * returns FUSE_OK when the wait gave up and its timeout was reported to the host as designed,
  * leaving the context usable.  Synchronous. */

@@ -1,0 +1,125 @@
+// fuse_phi_static: the regulariser value phi(X) of eq. reg1 without any allocation.
+//
+// Who needs it: code that must not call cudaMalloc, for example a caller recording work
+// into another component's CUDA graph (device allocation is not allowed while a stream is
+// being captured), or a host application that gives the GPU a fixed memory budget and owns
+// every allocation itself.  Such a caller cannot create a fuse_ctx (fuse_init allocates), so
+// this entry point takes plain device pointers and keeps its only scratch - the per-block
+// partial sums - in a file-scope device array of fixed size, resident on every GPU that loads
+// the library until the process exits.
+#include "fuse.h"
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "k_objective.cuh"
+
+namespace {
+
+constexpr int kPhiStaticPartials = 1 << 18;      // 2 MiB of doubles
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_phi_scratch[kPhiStaticPartials];
+
+// Per-device address of g_phi_scratch (host code only sees a host-side stand-in for the
+// symbol, so the device address is looked up once per device with that device current).
+double* g_scratch_ptr[kMaxDevices] = {};
+std::once_flag g_scratch_once[kMaxDevices];
+cudaError_t g_scratch_status[kMaxDevices] = {};
+
+double* scratch_for(int dev, cudaError_t* status) {
+    std::call_once(g_scratch_once[dev], [dev] {
+        void* p = nullptr;
+        g_scratch_status[dev] = cudaGetSymbolAddress(&p, g_phi_scratch);
+        g_scratch_ptr[dev] = g_scratch_status[dev] == cudaSuccess ? static_cast<double*>(p) : nullptr;
+    });
+    *status = g_scratch_status[dev];
+    return g_scratch_ptr[dev];
+}
+
+// The regulariser kernel of fuse_objective with its partial sums written to the static array:
+// part[blockIdx.y * gridDim.x + blockIdx.x] = sum over the block's pixels i of
+// omega_tau(i) sum_{k, c} |D_{tau k} X(i, c)|, tau = blockIdx.y (eq. regfilt1).
+template <typename T, typename WT>
+__global__ void __launch_bounds__(256) phi_static_partial_kernel(const T* __restrict__ X,
+                                                                const WT* __restrict__ omega, int H, int W,
+                                                                int Ls, int K, int S, double* __restrict__ part) {
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int side = 2 * S + 1;
+    const int tidx = blockIdx.y;
+    const int cell = tidx >= (side * side) / 2 ? tidx + 1 : tidx;
+    const int t1 = cell / side - S, t2 = cell % side - S;
+    double v[1] = {0.0};
+    if (p < n) {
+        const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+        double acc = 0.0;
+        for (int c = 0; c < Ls; ++c) {
+            const T* Xc = X + (size_t)c * n;
+            T sc = T(0);
+            for (int k1 = -K; k1 <= K; ++k1)
+                for (int k2 = -K; k2 <= K; ++k2) {
+                    const T a = Xc[(size_t)fuse::wrapn(y - k1, H) * W + fuse::wrapn(x - k2, W)];
+                    const T b = Xc[(size_t)fuse::wrapn(y - t1 - k1, H) * W + fuse::wrapn(x - t2 - k2, W)];
+                    sc += a > b ? a - b : b - a;
+                }
+            acc += (double)sc;
+        }
+        v[0] = (double)fuse::wload(omega + (size_t)tidx * n + p) * acc;
+    }
+    fuse::block_sum<1>(v, part + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Sums the partial sums in a fixed order (deterministic) into out[0].
+__global__ void __launch_bounds__(256) phi_static_reduce_kernel(const double* __restrict__ part, int count,
+                                                               double* __restrict__ out) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v[0] += part[i];
+    fuse::block_sum<1>(v, out);
+}
+
+}  // namespace
+
+extern "C" fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev, int H, int W, int L_s, int K,
+                                       int S, fuse_dtype dtype, fuse_dtype wdtype, double* phi_dev,
+                                       void* stream) {
+    if (!X_dev || !omega_dev || !phi_dev) return FUSE_EINVAL;
+    if (H < 1 || W < 1 || L_s < 1 || K < 0 || S < 1) return FUSE_EINVAL;
+    if (2 * (K + S) + 1 > H || 2 * (K + S) + 1 > W) return FUSE_EINVAL;
+    const bool f64 = dtype == FUSE_F64;
+    if (dtype != FUSE_F32 && dtype != FUSE_F64) return FUSE_EINVAL;
+    if (f64 && wdtype != FUSE_F64) return FUSE_EUNSUPPORTED;
+    if (!f64 && wdtype != FUSE_F32 && wdtype != FUSE_BF16) return FUSE_EUNSUPPORTED;
+    const size_t n = (size_t)H * W;
+    const int nW = (2 * S + 1) * (2 * S + 1) - 1;
+    const size_t nb = (n + 255) / 256;
+    if (nb * (size_t)nW > (size_t)kPhiStaticPartials) return FUSE_EUNSUPPORTED;   // beyond the array
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return FUSE_ECUDA;
+    }
+    cudaError_t e = cudaSuccess;
+    double* part = scratch_for(dev, &e);
+    if (!part) return FUSE_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dim3 grid((unsigned)nb, (unsigned)nW);
+    // every partial slot in [0, nb*nW) is written before the reduction reads it
+    if (f64) {
+        phi_static_partial_kernel<double, double><<<grid, 256, 0, s>>>(
+            static_cast<const double*>(X_dev), static_cast<const double*>(omega_dev), H, W, L_s, K, S, part);
+    } else if (wdtype == FUSE_BF16) {
+        phi_static_partial_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>(
+            static_cast<const float*>(X_dev), static_cast<const __nv_bfloat16*>(omega_dev), H, W, L_s, K, S, part);
+    } else {
+        phi_static_partial_kernel<float, float><<<grid, 256, 0, s>>>(
+            static_cast<const float*>(X_dev), static_cast<const float*>(omega_dev), H, W, L_s, K, S, part);
+    }
+    if (cudaGetLastError() != cudaSuccess) return FUSE_ECUDA;
+    phi_static_reduce_kernel<<<1, 256, 0, s>>>(part, (int)(nb * nW), phi_dev);
+    if (cudaGetLastError() != cudaSuccess) return FUSE_ECUDA;
+    return FUSE_OK;
+}

@@ -76,6 +76,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
         "fuse_sync": (_ST, [_VP]),
         "fuse_selftest": (_ST, [_VP, _I]),
+        "fuse_phi_static": (_ST, [_VP, _VP, _I, _I, _I, _I, _I, _I, _I, _VP, _VP]),
         "fuse_last_error": (ctypes.c_char_p, [_VP]),
         "fuse_reset_error": (_ST, [_VP]),
         "fuse_status_string": (ctypes.c_char_p, [_I]),
@@ -200,6 +201,12 @@ def fuse_sync(ctx):
 
 def fuse_selftest(ctx, which: int):
     _check(load().fuse_selftest(ctx, which), ctx)
+
+
+def fuse_phi_static(X_dev: int, omega_dev: int, H: int, W: int, L_s: int, K: int, S: int,
+                    dtype: int, wdtype: int, phi_dev: int, stream: int = 0):
+    _check(load().fuse_phi_static(_VP(X_dev), _VP(omega_dev), H, W, L_s, K, S, dtype, wdtype,
+                                  _VP(phi_dev), _VP(stream or None)))
 
 
 def fuse_last_error(ctx) -> str:
