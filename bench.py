@@ -69,6 +69,7 @@ def _config(p, meta, name, n_gpus):
         "offsets": (2 * p.S + 1) ** 2 - 1, "iters": p.iters, "weights": meta["wdtype"],
         "global_batch": n_gpus, "parallelism": f"independent problems x{n_gpus}",
         "l2": "latent state per problem exceeds L2 (no flush needed)",
+        "latent_state": "half window (one offset of each +-tau pair)",
     }
 
 
@@ -125,13 +126,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def latent_bytes(p, esz, wsz):
-    """Algorithmic bytes of one latent-pass launch: Sigma read + write, omega, X, planes."""
+def latent_bytes(p, esz, wsz, half=True):
+    """Algorithmic bytes of one latent-pass launch: state read + write over the kept offsets
+    (half of the window in half-window mode), their weights, X, and the adjoint planes."""
     n = p.H * p.W
     nW = (2 * p.S + 1) ** 2 - 1
+    nK = nW // 2 if half else nW
+    rows = p.S + 1 if half else 2 * p.S + 1
     nP = (2 * p.K + 1) ** 2
-    return (2 * nW * nP * p.L_s * n * esz + nW * n * wsz + p.L_s * n * esz
-            + 2 * (2 * p.S + 1) * p.L_s * n * esz)
+    return (2 * nK * nP * p.L_s * n * esz + nK * n * wsz + p.L_s * n * esz
+            + 2 * rows * p.L_s * n * esz)
 
 
 def cpu_baseline(p, target_s=15.0):

@@ -74,7 +74,10 @@ enum {
     FUSE_OPT_LATENT_IMPL = 3,    /* latent pass: 1 (default) bulk-copy ring, 0 register-staged loads */
     FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 256) */
     FUSE_OPT_LATENT_STAGES = 5,  /* ring slots of the bulk-copy latent pass, 2..32 (default 8) */
-    FUSE_OPT_WAIT_LIMIT = 6      /* polls before a device barrier wait gives up (default 2^22) */
+    FUSE_OPT_WAIT_LIMIT = 6,     /* polls before a device barrier wait gives up (default 2^22) */
+    FUSE_OPT_HALF_WINDOW = 7     /* 1 (default): keep the latent state for one offset of each
+                                    +-tau pair (exact by the window symmetry, half the state);
+                                    0: full window.  Switching reallocates the state and clears it. */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -83,8 +86,8 @@ enum {
     FUSE_K_LATENT = 1       /* the fused latent pass (eqs. Qj_main, dualvar3_main, D^T sum) */
 };
 
-/* Bytes of device memory fuse_init would allocate for this problem (state, weights,
- * FFT buffers and constants).  No device work.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED. */
+/* Bytes of device memory fuse_init would allocate for this problem (state in the default
+ * half-window mode, weights, FFT buffers and constants).  No device work.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED. */
 fuse_status fuse_workspace_bytes(const fuse_geometry* g, int K, int S, int ratio,
                                  fuse_dtype dtype, fuse_dtype wdtype, size_t* bytes);
 
@@ -159,7 +162,9 @@ fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_hos
 fuse_status fuse_objective(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, double out[4]);
 
 /* Size in bytes of the resumable ADMM state (Lambda1, U1 = P1 + Lambda1, Lambda2,
- * U2 = P2 + Lambda2, Sigma, the adjoint partial sums and X). */
+ * U2 = P2 + Lambda2, X, Sigma, the adjoint partial sums), in that order; Sigma is stored as
+ * Sig'[tau][k][c][m] = Sigma_{tau k}(m + k) over the kept offsets (all of W, or W+ in
+ * half-window mode, row-major). */
 fuse_status fuse_state_bytes(fuse_ctx* ctx, size_t* bytes);
 
 /* Copy the state to / from a buffer of fuse_state_bytes bytes (host or device; uses

@@ -59,4 +59,30 @@ __device__ __forceinline__ void st_stream(vecT<double, 2>* p, const vecT<double,
     __stcs(reinterpret_cast<double2*>(p), make_double2(a.v[0], a.v[1]));
 }
 
+// Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1.
+// Full mode: tau1 in [-S, S], all tau2 (skipping (0,0)); state index = row-major index in W.
+// Half mode (one offset of each +-tau pair, W+ = {tau1 > 0} U {tau1 = 0, tau2 > 0}): tau1 in
+// [0, S]; state index = row-major index in W+.  Weight index is always the full-W index.
+struct TauMap {
+    int S;
+    int half;
+    __device__ __forceinline__ int t1_of_block(int by) const { return half ? by : by - S; }
+    __device__ __forceinline__ int nt2(int t1) const {
+        return t1 == 0 ? (half ? S : 2 * S) : 2 * S + 1;
+    }
+    __device__ __forceinline__ int t2_of(int t1, int j) const {
+        if (t1 != 0) return j - S;
+        return half ? j + 1 : (j >= S ? j - S + 1 : j - S);
+    }
+    __device__ __forceinline__ int w_index(int t1, int t2) const {
+        const int side = 2 * S + 1;
+        const int cell = (t1 + S) * side + (t2 + S);
+        return cell > (side * side) / 2 ? cell - 1 : cell;
+    }
+    __device__ __forceinline__ int s_index(int t1, int t2) const {
+        if (!half) return w_index(t1, t2);
+        return t1 == 0 ? t2 - 1 : S + (t1 - 1) * (2 * S + 1) + (t2 + S);
+    }
+};
+
 }  // namespace fuse

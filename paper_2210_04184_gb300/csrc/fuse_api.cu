@@ -80,6 +80,8 @@ struct fuse_ctx {
     size_t lt_smem = 0;
     int* d_err = nullptr;
     unsigned wait_limit = 1u << 22;
+    // half-window latent state (one offset of each +-tau pair); 0 = full window
+    int half = 1;
 };
 
 namespace {
@@ -244,13 +246,13 @@ struct Sizes {
     size_t img, cimg, sig, planes, omega, d9a;
 };
 
-Sizes sizes_of(const fuse_geometry* g, int K, int S, int ratio, size_t esz, size_t wsz) {
+Sizes sizes_of(const fuse_geometry* g, int K, int S, int ratio, size_t esz, size_t wsz, int half = 1) {
     Sizes z;
     const size_t n = (size_t)g->H * g->W;
     const size_t nW = (size_t)(2 * S + 1) * (2 * S + 1) - 1, nP = (size_t)(2 * K + 1) * (2 * K + 1);
     z.img = n * g->L_s * esz;
     z.cimg = n * ((g->L_s + 1) / 2) * 2 * esz;
-    z.sig = nW * nP * g->L_s * n * esz;
+    z.sig = (half ? nW / 2 : nW) * nP * g->L_s * n * esz;
     z.planes = (size_t)g->L_s * 2 * (2 * S + 1) * n * esz;
     z.omega = nW * n * wsz;
     z.d9a = (size_t)g->L_s * (n / ((size_t)ratio * ratio)) * esz;
@@ -334,19 +336,21 @@ struct Impl {
     template <typename WT, int K>
     static void launch_latent(fuse_ctx* c, cudaStream_t s) {
         constexpr int VEC = 16 / sizeof(T);
-        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)(2 * c->S + 1), (unsigned)c->Ls);
+        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
+        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), rowsW, (unsigned)c->Ls);
         latent_kernel<T, WT, K, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
             (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lat_Ty,
-            (T)(c->lam2 / c->rho));
+            (T)(c->lam2 / c->rho), c->half);
     }
 
     template <typename WT, int K>
     static void launch_latent_tma(fuse_ctx* c, cudaStream_t s) {
         constexpr int VEC = 16 / sizeof(T);
-        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)(2 * c->S + 1), (unsigned)c->Ls);
+        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
+        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), rowsW, (unsigned)c->Ls);
         latent_tma_kernel<T, WT, K, VEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(
             (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lt_Ty,
-            c->lt_ncons, c->lat_stages, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit);
+            c->lt_ncons, c->lat_stages, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit, c->half);
     }
 
     template <typename WT>
@@ -377,7 +381,7 @@ struct Impl {
         dim3 sblock(ST_TX, ST_BY);
         stencil_kernel<T, 1><<<sgrid, sblock, c->st_smem, s>>>(
             (const T*)c->U1, (T*)c->C, (const T*)c->tapsT, c->bh, c->bw, c->H, c->W, (const T*)c->U2,
-            (const T*)c->planes, c->S);
+            (const T*)c->planes, c->S, c->half);
         dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
         fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
             (const T*)c->C, (cplx<T>*)c->Y, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
@@ -387,7 +391,7 @@ struct Impl {
         fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
             (const cplx<T>*)c->Y, (T*)c->X, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
         stencil_kernel<T, 0><<<sgrid, sblock, c->st_smem, s>>>(
-            (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S);
+            (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S, 0);
         const unsigned pblocks = (unsigned)((n + c->px_threads - 1) / c->px_threads);
         pixel_kernel<T><<<pblocks, c->px_threads, c->px_smem, s>>>(
             (const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2, (const T*)c->D9a,
@@ -428,7 +432,7 @@ fuse_status Impl<T>::objective(fuse_ctx* c, const void* Yl, const void* Yh, doub
     const size_t n = c->n;
     dim3 sgrid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
     stencil_kernel<T, 0><<<sgrid, dim3(ST_TX, ST_BY), c->st_smem, c->stream>>>(
-        (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S);
+        (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S, 0);
     const unsigned nb = (unsigned)((n + 255) / 256);
     obj_data_kernel<T><<<nb, 256, 0, c->stream>>>((const T*)c->X, (const T*)c->BX, (const T*)Yl, (const T*)Yh,
                                                    c->objE, c->objER, c->H, c->W, c->d, c->Ls, c->Ll, c->Lh,
@@ -556,7 +560,8 @@ void release(fuse_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (auto& e : c->ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
-    for (void* p : c->allocs) cudaFree(p);
+    for (void* p : c->allocs)
+        if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->allocs.clear();
 }
@@ -945,6 +950,24 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
                 latent_tma_shape(c);
                 return fail(c, FUSE_EINVAL, "latent launch option out of range");
             }
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
+        }
+        case FUSE_OPT_HALF_WINDOW: {
+            const int h = value ? 1 : 0;
+            if (h == c->half) return FUSE_OK;
+            const size_t nWs = h ? (size_t)c->nW / 2 : (size_t)c->nW;
+            const size_t bytes = nWs * c->nP * c->Ls * c->n * c->esz;
+            for (auto& p : c->allocs)
+                if (p == c->Sig) { CK(c, cudaStreamSynchronize(c->stream)); cudaFree(p); p = nullptr; }
+            c->Sig = nullptr;
+            fuse_status s2 = dalloc(c, &c->Sig, bytes);
+            if (s2 != FUSE_OK) return s2;
+            c->sig_bytes = bytes;
+            c->half = h;
+            c->have_state = false;
+            c->have_x = false;
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
             return FUSE_OK;

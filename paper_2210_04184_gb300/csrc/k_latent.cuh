@@ -20,7 +20,14 @@
 // so that R(j) = sum_{tau1} [A_{tau1}(j) - V_{tau1}(j + (tau1, 0))], summed in fixed order by
 // the right-hand-side kernel (deterministic, no atomics).
 //
-// Layouts: X [L_s][H][W]; omega [|W|][H][W]; Sig' [|W|][|P|][L_s][H][W];
+// Half-window mode (half = 1): with M Y(i) = -Y(i + tau), D_{-tau,k} = M D_{tau,k}, and the weights
+// satisfy omega_{i,-tau} = omega_{i+tau,tau}; the soft threshold is odd, so from zero state
+// Sigma_{-tau,k} = M Sigma_{tau,k} at every iteration and, M being orthogonal,
+// D_{-tau,k}^T (Q + Sigma)_{-tau,k} = D_{tau,k}^T (Q + Sigma)_{tau,k}.  Only the offsets of
+// W+ = {tau1 > 0} U {tau1 = 0, tau2 > 0} are kept and their adjoint sum is counted twice by the
+// right-hand-side kernel: the full-window iterates up to summation order, with half the state.
+//
+// Layouts: X [L_s][H][W]; omega [|W|][H][W]; Sig' [|W| or |W|/2][|P|][L_s][H][W];
 // planes [L_s][2(2S+1)][H][W].  Threads: (W/VEC) x Ty, each owning VEC consecutive pixels.
 #pragma once
 #include "common.cuh"
@@ -30,7 +37,7 @@ namespace fuse {
 template <typename T, typename WT, int K, int VEC>
 __global__ void __launch_bounds__(256)
 latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restrict__ Sig,
-              T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, T coef) {
+              T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, T coef, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Hs = reinterpret_cast<T*>(smem_raw);           // [(2S+1)][Ty][W]
     constexpr int PS = 2 * K + 1;
@@ -40,12 +47,13 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
     const int r = tid / tpr;
     const int x0 = (tid - r * tpr) * VEC;
     const int y = blockIdx.x * Ty + r;
-    const int t1 = (int)blockIdx.y - S;
+    const TauMap tm{S, half};
+    const int t1 = tm.t1_of_block(blockIdx.y);
+    const int nt2 = tm.nt2(t1);
     const int c = blockIdx.z;
     const bool active = y < H;
     const size_t n = (size_t)H * W;
     const int side = 2 * S + 1;
-    const int centre = (side * side) / 2;
     const T* Xc = X + (size_t)c * n;
     const size_t kstride = (size_t)Ls * n;
 
@@ -54,20 +62,19 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
 #pragma unroll
     for (int j = 0; j < VEC; ++j) { Xm[j] = active ? Xc[(size_t)y * W + x0 + j] : T(0); A[j] = T(0); }
 
-    for (int t2 = -S; t2 <= S; ++t2) {
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
         T Hacc[VEC];
 #pragma unroll
         for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
-        if (active && (t1 != 0 || t2 != 0)) {
-            const int cell = (t1 + S) * side + (t2 + S);
-            const int tidx = cell > centre ? cell - 1 : cell;
+        if (active) {
             const int ys = wrap1(y - t1, H);
             T delta[VEC];
 #pragma unroll
             for (int j = 0; j < VEC; ++j) delta[j] = Xm[j] - Xc[(size_t)ys * W + wrap1(x0 + j - t2, W)];
-            const WT* om = omega + (size_t)tidx * n;
+            const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
             vecT<T, VEC>* sp = reinterpret_cast<vecT<T, VEC>*>(
-                Sig + ((size_t)tidx * NP * Ls + c) * n + (size_t)y * W + x0);
+                Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0);
             const size_t vstride = kstride / VEC;
 #pragma unroll
             for (int k1 = -K; k1 <= K; ++k1) {
@@ -107,7 +114,8 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
     T V[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) V[j] = T(0);
-    for (int t2 = -S; t2 <= S; ++t2) {
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
         const T* row = Hs + ((size_t)(t2 + S) * Ty + r) * W;
 #pragma unroll
         for (int j = 0; j < VEC; ++j) V[j] += row[wrap1(x0 + j + t2, W)];
@@ -140,7 +148,7 @@ template <typename T, typename WT, int K, int VEC>
 __global__ void __launch_bounds__(288)
 latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restrict__ Sig,
                   T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, int ncons, int D, T coef,
-                  int* __restrict__ err, unsigned limit) {
+                  int* __restrict__ err, unsigned limit, int half) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     constexpr int PS = 2 * K + 1;
     constexpr int NP = PS * PS;
@@ -156,11 +164,11 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
     const int tpr = W / VEC;
     const int y0 = blockIdx.x * Ty;
     const int rows = min(Ty, H - y0);
-    const int t1 = (int)blockIdx.y - S;
+    const TauMap tm{S, half};
+    const int t1 = tm.t1_of_block(blockIdx.y);
     const int c = blockIdx.z;
     const size_t n = (size_t)H * W;
-    const int centre = (side * side) / 2;
-    const int nt2 = t1 == 0 ? side - 1 : side;
+    const int nt2 = tm.nt2(t1);
     const int nq = nt2 * NP;
     const unsigned bytes = (unsigned)(rows * W * (int)sizeof(T));
 
@@ -197,10 +205,8 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
                     break;
                 }
                 const int j = q / NP, kidx = q - j * NP;
-                const int t2 = (t1 == 0 && j >= S) ? j - S + 1 : j - S;
-                const int cell = (t1 + S) * side + (t2 + S);
-                const int tidx = cell > centre ? cell - 1 : cell;
-                const T* src = Sig + ((size_t)(tidx * NP + kidx) * Ls + c) * n + (size_t)y0 * W;
+                const int t2 = tm.t2_of(t1, j);
+                const T* src = Sig + ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + c) * n + (size_t)y0 * W;
                 mbar_arrive_expect_tx(&full[slot], bytes);
                 tma_load_1d(ring + (size_t)slot * tile, src, bytes, &full[slot], pol);
                 issued = q + 1;
@@ -220,20 +226,19 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
         for (int j = 0; j < VEC; ++j) Xm[j] = active ? Xc[(size_t)y * W + x0 + j] : T(0);
         int slot = 0;
         unsigned par = 0;
-        for (int t2 = -S; t2 <= S; ++t2) {
+        for (int jt = 0; jt < nt2; ++jt) {
+            const int t2 = tm.t2_of(t1, jt);
             T Hacc[VEC];
 #pragma unroll
             for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
-            if (t1 != 0 || t2 != 0) {
-                const int cell = (t1 + S) * side + (t2 + S);
-                const int tidx = cell > centre ? cell - 1 : cell;
+            {
                 T delta[VEC];
                 const int ys = wrap1(y - t1, H);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
                     delta[j] = active ? Xm[j] - Xc[(size_t)ys * W + wrap1(x0 + j - t2, W)] : T(0);
-                const WT* om = omega + (size_t)tidx * n;
-                T* gp = Sig + ((size_t)tidx * NP * Ls + c) * n + (size_t)y * W + x0;
+                const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
+                T* gp = Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0;
                 const size_t kstride = (size_t)Ls * n;
 #pragma unroll
                 for (int k1 = -K; k1 <= K; ++k1) {
@@ -280,7 +285,8 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
     T V[VEC];
 #pragma unroll
     for (int j = 0; j < VEC; ++j) V[j] = T(0);
-    for (int t2 = -S; t2 <= S; ++t2) {
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
         const T* row = Hs + ((size_t)(t2 + S) * Ty + r) * W;
 #pragma unroll
         for (int j = 0; j < VEC; ++j) V[j] += row[wrap1(x0 + j + t2, W)];

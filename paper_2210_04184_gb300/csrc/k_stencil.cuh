@@ -3,6 +3,7 @@
 //
 // MODE 0: out = stencil(in)                                        -> B X
 // MODE 1: out = stencil(U1) + U2 + R,  R(j) = sum_{tau1} [A_{tau1}(j) - V_{tau1}(j + (tau1,0))]
+//         (half-window mode: tau1 >= 0 only and R doubled, see k_latent.cuh)
 //         the right-hand side C = B^T(P1 + Lambda1) + P2 + Lambda2 + sum D^T(Q + Sigma)
 //         (Sec. IV-A, after eq. x_linear_system_main), with R from the latent pass planes.
 // Tiles of 32 x 32 pixels of one band; the halo is loaded with circular wrap.
@@ -16,7 +17,7 @@ constexpr int ST_TX = 32, ST_TY = 32, ST_BY = 8;
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ taps, int bh, int bw,
-               int H, int W, const T* __restrict__ U2, const T* __restrict__ planes, int S) {
+               int H, int W, const T* __restrict__ U2, const T* __restrict__ planes, int S, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int th = ST_TY + bh - 1, tw = ST_TX + bw - 1;
     T* tile = reinterpret_cast<T*>(smem_raw);        // [th][tw]
@@ -50,12 +51,13 @@ stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restric
         }
         const size_t pix = (size_t)y * W + x;
         if constexpr (MODE == 1) {
-            acc += U2[(size_t)c * n + pix];
             const T* pc = planes + (size_t)c * 2 * side * n;
-            for (int t1 = -S; t1 <= S; ++t1) {
-                acc += pc[(size_t)(t1 + S) * n + pix];
-                acc -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
+            T rs = T(0);
+            for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
+                rs += pc[(size_t)(t1 + S) * n + pix];
+                rs -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
             }
+            acc += U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
         }
         out[(size_t)c * n + pix] = acc;
     }

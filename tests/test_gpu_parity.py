@@ -15,7 +15,8 @@ torch = pytest.importorskip("torch")
 from oracle import nlpr  # noqa: E402
 from paper_2210_04184_gb300 import build as _build  # noqa: E402
 from paper_2210_04184_gb300.fuse import (Fusion, FUSE_OPT_GRAPH, FUSE_OPT_LATENT_IMPL,  # noqa: E402
-                                         FUSE_OPT_LATENT_STAGES, FUSE_OPT_LATENT_THREADS)
+                                         FUSE_OPT_LATENT_STAGES, FUSE_OPT_LATENT_THREADS,
+                                         FUSE_OPT_HALF_WINDOW)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -110,11 +111,13 @@ def test_weights_bf16_rounding():
 # ------------------------------------------------------------------------------ solve parity
 
 
+@pytest.mark.parametrize("half", [1, 0])
 @pytest.mark.parametrize("iters", [1, 2, 3])
-def test_first_iterations_state_parity(iters):
+def test_first_iterations_state_parity(iters, half):
     # Element-by-element state after 1, 2, 3 iterations (X update, P1/P2, duals, latent pass).
+    # Half-window mode keeps the offsets of W+ = {tau1 > 0} U {tau1 = 0, tau2 > 0} only.
     p = small()
-    g = gpu_solve(p, iters, want_state=True)
+    g = gpu_solve(p, iters, want_state=True, opts=[(FUSE_OPT_HALF_WINDOW, half)])
     Xo, st, _ = oracle_solve(p, iters)
     n = p.H * p.W
     Ls = p.L_s
@@ -128,12 +131,15 @@ def test_first_iterations_state_parity(iters):
     assert np.abs(lam2 - nlpr.to_lhw(st.Lam2)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P2)).max()
     assert np.abs(u2 - nlpr.to_lhw(st.P2 + st.Lam2)).max() <= 1e-5 * np.abs(nlpr.to_lhw(st.P2)).max()
     # latent state, stored re-indexed by source pixel: Sig'_{tau k}(m) = Sigma_{tau k}(m + k)
-    nW, nP = len(nlpr.search_offsets(p.S)), len(nlpr.patch_offsets(p.K))
-    sig = s[5 * img:5 * img + nW * nP * img].reshape(nW, nP, Ls, p.H, p.W)
-    for t in range(nW):
+    offs = nlpr.search_offsets(p.S)
+    kept = [t for t, tau in enumerate(offs) if not half or tau[0] > 0 or (tau[0] == 0 and tau[1] > 0)]
+    nP = len(nlpr.patch_offsets(p.K))
+    sig = s[5 * img:5 * img + len(kept) * nP * img].reshape(len(kept), nP, Ls, p.H, p.W)
+    assert s.size == 5 * img + len(kept) * nP * img + Ls * 2 * (2 * p.S + 1) * p.H * p.W
+    for j, t in enumerate(kept):
         for kk, k in enumerate(nlpr.patch_offsets(p.K)):
             ref = nlpr.to_lhw(np.roll(st.Sig[t, kk], shift=(-k[0], -k[1]), axis=(0, 1)))
-            assert np.abs(sig[t, kk] - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+            assert np.abs(sig[j, kk] - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
 
 
 CASES = {
@@ -148,23 +154,25 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("half", [1, 0])
 @pytest.mark.parametrize("impl", [1, 0])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_fp32_parity(name, impl):
+def test_fp32_parity(name, impl, half):
     kw = dict(CASES[name])
     iters = kw.pop("iters")
     p = small(**kw)
-    g = gpu_solve(p, iters, opts=[(FUSE_OPT_LATENT_IMPL, impl)])
+    g = gpu_solve(p, iters, opts=[(FUSE_OPT_LATENT_IMPL, impl), (FUSE_OPT_HALF_WINDOW, half)])
     Xo, _, _ = oracle_solve(p, iters)
     assert rel(g["X"], Xo) <= 1e-5
     Zo = np.einsum("chw,cl->lhw", Xo, p.E)
     assert rel(g["Z"], Zo) <= 1e-5
 
 
+@pytest.mark.parametrize("half", [1, 0])
 @pytest.mark.parametrize("impl", [1, 0])
-def test_fp64_parity(impl):
+def test_fp64_parity(impl, half):
     p = small(H=40, W=36, L_l=5, L_h=2, L_s=3, K=1, S=2)
-    g = gpu_solve(p, 25, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_LATENT_IMPL, impl)])
+    g = gpu_solve(p, 25, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_LATENT_IMPL, impl), (FUSE_OPT_HALF_WINDOW, half)])
     Xo, _, _ = oracle_solve(p, 25)
     assert rel(g["X"], Xo) <= 1e-11
 
@@ -211,7 +219,7 @@ def test_latent_ring_shapes_bitwise_equal(threads, stages):
     # The pipelined latent pass gives bit-identical results for every block / ring shape and
     # matches the register-staged form (same arithmetic per element, same summation order).
     p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=9, blur_sigma=1.7)
-    ref = gpu_solve(p, 6, opts=[(FUSE_OPT_LATENT_IMPL, 0)])["X"]
+    ref = gpu_solve(p, 6, opts=[(FUSE_OPT_LATENT_IMPL, 0)])["X"]          # default: half window
     got = gpu_solve(p, 6, opts=[(FUSE_OPT_LATENT_IMPL, 1), (FUSE_OPT_LATENT_THREADS, threads),
                                 (FUSE_OPT_LATENT_STAGES, stages)])["X"]
     assert np.array_equal(got, ref)
@@ -264,3 +272,14 @@ def test_run_host_matches_device_path():
     fuse_run_host(f.ctx, Yl.ctypes.data, Yh.ctypes.data, None, 10, X.ctypes.data, Z.ctypes.data)
     assert np.array_equal(X.astype(np.float64), g["X"])
     assert np.array_equal(Z.astype(np.float64), g["Z"])
+
+
+def test_half_window_equals_full_window():
+    # The half-window state reproduces the full-window iterates up to summation order.
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=9, blur_sigma=1.7)
+    a = gpu_solve(p, 30, opts=[(FUSE_OPT_HALF_WINDOW, 0)])["X"]
+    b = gpu_solve(p, 30, opts=[(FUSE_OPT_HALF_WINDOW, 1)])["X"]
+    assert rel(b, a) <= 2e-6
+    a64 = gpu_solve(p, 30, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_HALF_WINDOW, 0)])["X"]
+    b64 = gpu_solve(p, 30, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_HALF_WINDOW, 1)])["X"]
+    assert rel(b64, a64) <= 1e-13
