@@ -29,6 +29,12 @@ sys.path.insert(0, str(ROOT))
 import numpy as np  # noqa: E402
 
 METRIC = "ADMM throughput (megapixel*band*iter/s)"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch, from the
+# ncu capture summarised in profiles/latent_tma_kernel_hsms128.md (128x128 case, the same kernel
+# and launch shape), scaled to the workload by its pixel count (the traffic is proportional to
+# it).  Must be re-measured whenever the latent kernel changes.
+LATENT_TRAFFIC_PER_PIXEL = {"hsms": 1.5249e9 / (128 * 128)}
 UNIT = "Mpx*band*iter/s"
 
 
@@ -42,6 +48,7 @@ def _args():
     ap.add_argument("--iters", type=int, default=None, help="override the workload's iteration count")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-FP32 comparison")
     return ap.parse_args()
 
 
@@ -187,6 +194,47 @@ def run_reference(a, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def fp64_compare(p, meta, f32ctx, yl, yh, Z32):
+    """The FP64 GPU form of the same workload (FP64 iterates and weights) against the FP32 form:
+    iterations per second of each and the relative error of Z (FP32 with the run's weight type,
+    and FP32 with FP32 weights) against the FP64 result, at the workload's iteration count."""
+    import torch
+    from paper_2210_04184_gb300.fuse import Fusion
+
+    def timed(ctx, Yl, Yh, Zout):
+        from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream
+        st = torch.cuda.current_stream()
+        fuse_set_stream(ctx.ctx, st.cuda_stream)
+        fuse_weights(ctx.ctx, Yh.data_ptr())
+        fuse_solve(ctx.ctx, Yl.data_ptr(), Yh.data_ptr(), 2, 0, None, None)     # warm (graph capture)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fuse_solve(ctx.ctx, Yl.data_ptr(), Yh.data_ptr(), p.iters, 0, None, Zout.data_ptr())
+        e1.record(st)
+        ctx.sync()
+        return p.iters / (e0.elapsed_time(e1) / 1e3)
+
+    yl64, yh64 = yl.double(), yh.double()
+    Z64 = torch.empty((p.L_l, p.H, p.W), dtype=torch.float64, device="cuda")
+    f64 = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    it64 = timed(f64, yl64, yh64, Z64)
+    f64.close()
+    it32 = timed(f32ctx, yl, yh, Z32)
+    nz = torch.linalg.norm(Z64)
+    err32 = float(torch.linalg.norm(Z32.double() - Z64) / nz)
+    out = {"fp64_iters_per_s": it64, "fp32_iters_per_s": it32, "speedup": it32 / it64,
+           "rel_err_Z_fp32_vs_fp64": err32, "fp32_weights": meta["wdtype"]}
+    if meta["wdtype"] != "f32":
+        fw = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+        Zw = torch.empty_like(Z32)
+        timed(fw, yl, yh, Zw)
+        fw.close()
+        out["rel_err_Z_fp32_f32weights_vs_fp64"] = float(torch.linalg.norm(Zw.double() - Z64) / nz)
+    out["equal_error_1e-4"] = out.get("rel_err_Z_fp32_f32weights_vs_fp64", err32) <= 1e-4
+    return out
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -270,6 +318,10 @@ def run_ours(a, rank, world, local_rank):
                "h2d_bytes_per_step": hyl.numel() * hyl.element_size() + hyh.numel() * hyh.element_size(),
                "d2h_bytes_per_step": hz.numel() * hz.element_size()}
 
+    fp64 = None
+    if not a.no_fp64 and meta["dtype"] == "f32":
+        fp64 = fp64_compare(p, meta, f, yl, yh, Z)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -279,6 +331,9 @@ def run_ours(a, rank, world, local_rank):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     per_launch_ms = lat_ms / max(lat_n, 1)
+    traffic = None
+    if a.workload.startswith("hsms") and meta["wdtype"] == "bf16" and meta["dtype"] == "f32":
+        traffic = LATENT_TRAFFIC_PER_PIXEL["hsms"] * p.H * p.W
     lb = latent_bytes(p, esz, wsz)
     achieved = lb / (per_launch_ms / 1e3) / 1e9
     out = {
@@ -288,12 +343,13 @@ def run_ours(a, rank, world, local_rank):
         "config": _config(p, meta, a.workload, world),
         "iters_per_s": p.iters * a.steps * world / (ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "kernel": "latent_kernel",
+                     "frac": achieved / hbm, "traffic": traffic, "kernel": "latent_tma_kernel",
                      "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms,
                      "launches": lat_n, "peak_source": peak_src},
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
+        "fp64_compare": fp64,
     }
     if not a.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(p)

@@ -73,7 +73,7 @@ enum {
     FUSE_OPT_GRAPH = 2,          /* 1 (default): replay iterations from a captured CUDA graph */
     FUSE_OPT_LATENT_IMPL = 3,    /* latent pass: 1 (default) bulk-copy ring, 0 register-staged loads */
     FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 256) */
-    FUSE_OPT_LATENT_STAGES = 5,  /* ring slots of the bulk-copy latent pass, 2..32 (default 8) */
+    FUSE_OPT_LATENT_STAGES = 5,  /* ring slots of the bulk-copy latent pass, 2..32 (default 6) */
     FUSE_OPT_WAIT_LIMIT = 6,     /* polls before a device barrier wait gives up (default 2^22) */
     FUSE_OPT_HALF_WINDOW = 7     /* 1 (default): keep the latent state for one offset of each
                                     +-tau pair (exact by the window symmetry, half the state);

@@ -68,6 +68,16 @@ def latent_update(X, st, su):
     return Q, Sig
 
 
+def latent_update_inplace(X, st, su):
+    """As latent_update, overwriting st.Q and st.Sig (eqs. Qj_main, dualvar3_main)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    H, W, L = X.shape
+    om = np.ascontiguousarray(su.omega, dtype=np.float64)
+    lib().oracle_latent(_p(X), _p(om), _p(st.Q), _p(st.Sig), H, W, L, su.K, su.S,
+                        float(su.lam2), float(su.rho))
+    return st.Q, st.Sig
+
+
 def dt_sum(Q: np.ndarray, Sig: np.ndarray, K: int, S: int) -> np.ndarray:
     H, W, L = Q.shape[2:]
     out = np.empty((H, W, L))

@@ -404,18 +404,23 @@ def admm_step(st: State, su: Setup, x_solver=None, latent_fn=None, dtsum_fn=None
 
 
 def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
-         x_solver=None, fast=False, callback=None):
+         x_solver=None, fast=False, callback=None, inplace=False):
     """Run `iters` ADMM iterations from `state` (zero initialisation by default).
 
     Images in (H, W, L) layout.  fast=True uses the C loops of oracle/loops.c for the
-    Q/Sigma updates and the D^T sum (same arithmetic, explicit loops).
+    Q/Sigma updates and the D^T sum (same arithmetic, explicit loops); with inplace=True those
+    loops overwrite Q and Sigma in place (the old values are not needed once C is formed),
+    so large problems hold one copy of the latent variables.
     Returns (X, state, setup)."""
     su = setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega)
-    st = state.copy() if state is not None else State.zeros(su.H, su.W, su.L_s, K, S)
+    if state is not None:
+        st = state if inplace else state.copy()
+    else:
+        st = State.zeros(su.H, su.W, su.L_s, K, S)
     latent_fn = dtsum_fn = None
     if fast:
         from . import cloops
-        latent_fn = cloops.latent_update
+        latent_fn = cloops.latent_update_inplace if inplace else cloops.latent_update
         dtsum_fn = cloops.dt_sum
     for _ in range(iters):
         st = admm_step(st, su, x_solver, latent_fn, dtsum_fn)

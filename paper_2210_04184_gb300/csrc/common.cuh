@@ -59,14 +59,20 @@ __device__ __forceinline__ void st_stream(vecT<double, 2>* p, const vecT<double,
     __stcs(reinterpret_cast<double2*>(p), make_double2(a.v[0], a.v[1]));
 }
 
-// Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1.
-// Full mode: tau1 in [-S, S], all tau2 (skipping (0,0)); state index = row-major index in W.
+// Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1
+// (blockIdx.z).  Full mode: tau1 in [-S, S], all tau2 (skipping (0,0)); state index =
+// row-major index in W.
 // Half mode (one offset of each +-tau pair, W+ = {tau1 > 0} U {tau1 = 0, tau2 > 0}): tau1 in
 // [0, S]; state index = row-major index in W+.  Weight index is always the full-W index.
 struct TauMap {
     int S;
     int half;
-    __device__ __forceinline__ int t1_of_block(int by) const { return half ? by : by - S; }
+    // Block rows are ordered heavy first: the tau1 = 0 row, which has fewer offsets, comes last
+    // so that the shortest blocks fill the tail of the launch.
+    __device__ __forceinline__ int t1_of_block(int by) const {
+        if (half) return by < S ? by + 1 : 0;
+        return by < 2 * S ? (by < S ? by - S : by - S + 1) : 0;
+    }
     __device__ __forceinline__ int nt2(int t1) const {
         return t1 == 0 ? (half ? S : 2 * S) : 2 * S + 1;
     }

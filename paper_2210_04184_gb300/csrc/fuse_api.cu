@@ -75,7 +75,7 @@ struct fuse_ctx {
     cudaGraphExec_t gexec = nullptr;
     int fault_alloc = -1, alloc_count = 0;
     // latent pass variant: 0 = register-staged loads, 1 = bulk-copy (TMA) ring
-    int lat_impl = 1, lat_target = 256, lat_stages = 8;
+    int lat_impl = 1, lat_target = 256, lat_stages = 6;
     int lt_Ty = 1, lt_ncons = 0;
     size_t lt_smem = 0;
     int* d_err = nullptr;
@@ -183,6 +183,7 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     if (2 * (K + S) + 1 > g->H || 2 * (K + S) + 1 > g->W) return fail(c, FUSE_EINVAL, "2(K+S)+1 exceeds the image");
     if (bh < 1 || bw < 1 || !(bh & 1) || !(bw & 1) || bh > g->H || bw > g->W)
         return fail(c, FUSE_EINVAL, "blur size must be odd and fit the image");
+    if (bh > 15 || bw > 15) return fail(c, FUSE_EUNSUPPORTED, "blur larger than 15 x 15");
     if (dtype != FUSE_F32 && dtype != FUSE_F64) return fail(c, FUSE_EINVAL, "dtype must be F32 or F64");
     if (dtype == FUSE_F32 && wdtype != FUSE_F32 && wdtype != FUSE_BF16)
         return fail(c, FUSE_EUNSUPPORTED, "F32 context needs BF16 or F32 weights");
@@ -227,8 +228,12 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     if (sh->st_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "blur too large");
     // pixel / band mixing
     sh->px_threads = 128;
-    while (sh->px_threads > 32 && (size_t)g->L_s * sh->px_threads * esz > 96 * 1024) sh->px_threads /= 2;
-    sh->px_smem = (size_t)g->L_s * sh->px_threads * esz;
+    if (g->L_s <= 32) {
+        sh->px_smem = 2 * (size_t)g->L_s * g->L_s * esz;
+    } else {
+        while (sh->px_threads > 32 && (size_t)g->L_s * sh->px_threads * esz > 96 * 1024) sh->px_threads /= 2;
+        sh->px_smem = (size_t)g->L_s * sh->px_threads * esz;
+    }
     int lmax = g->L_l > g->L_h ? g->L_l : g->L_h;
     if (g->L_s > lmax) lmax = g->L_s;
     sh->mix_smem_max = (size_t)lmax * 32 * esz;
@@ -287,9 +292,9 @@ struct Impl {
         CK(c, cudaFuncSetAttribute(fft_rows_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fr_smem));
         CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fr_smem));
         CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fc_smem));
-        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
-        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
-        CK(c, cudaFuncSetAttribute(pixel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->px_smem));
+
+        CK(c, cudaFuncSetAttribute(pixel_kernel_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->px_smem));
+        if (stencil_attr(c) != FUSE_OK) return c->sticky;
         CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
         return FUSE_OK;
     }
@@ -310,6 +315,49 @@ struct Impl {
                      CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 3, V>, A, kMaxSmem)); break;
         }
         return FUSE_OK;
+    }
+
+    template <int MODE, int BH>
+    static void stencil_bh(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
+        dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
+        stencil_kernel<T, MODE, BH><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(
+            (const T*)in, (T*)out, (const T*)taps, c->bw, c->H, c->W, (const T*)c->U2, (const T*)c->planes, c->S,
+            c->half);
+    }
+
+    // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
+    template <int MODE>
+    static void stencil(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
+        switch (c->bh) {
+            case 1: stencil_bh<MODE, 1>(c, s, in, out, taps); break;
+            case 3: stencil_bh<MODE, 3>(c, s, in, out, taps); break;
+            case 5: stencil_bh<MODE, 5>(c, s, in, out, taps); break;
+            case 7: stencil_bh<MODE, 7>(c, s, in, out, taps); break;
+            case 9: stencil_bh<MODE, 9>(c, s, in, out, taps); break;
+            case 11: stencil_bh<MODE, 11>(c, s, in, out, taps); break;
+            case 13: stencil_bh<MODE, 13>(c, s, in, out, taps); break;
+            default: stencil_bh<MODE, 15>(c, s, in, out, taps); break;
+        }
+    }
+
+    template <int BH>
+    static fuse_status stencil_attr_bh(fuse_ctx* c) {
+        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 0, BH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
+        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 1, BH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
+        return FUSE_OK;
+    }
+
+    static fuse_status stencil_attr(fuse_ctx* c) {
+        switch (c->bh) {
+            case 1: return stencil_attr_bh<1>(c);
+            case 3: return stencil_attr_bh<3>(c);
+            case 5: return stencil_attr_bh<5>(c);
+            case 7: return stencil_attr_bh<7>(c);
+            case 9: return stencil_attr_bh<9>(c);
+            case 11: return stencil_attr_bh<11>(c);
+            case 13: return stencil_attr_bh<13>(c);
+            default: return stencil_attr_bh<15>(c);
+        }
     }
 
     static fuse_status band_mix(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* M, size_t npix,
@@ -337,7 +385,7 @@ struct Impl {
     static void launch_latent(fuse_ctx* c, cudaStream_t s) {
         constexpr int VEC = 16 / sizeof(T);
         const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
-        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), rowsW, (unsigned)c->Ls);
+        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
         latent_kernel<T, WT, K, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
             (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lat_Ty,
             (T)(c->lam2 / c->rho), c->half);
@@ -347,7 +395,7 @@ struct Impl {
     static void launch_latent_tma(fuse_ctx* c, cudaStream_t s) {
         constexpr int VEC = 16 / sizeof(T);
         const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
-        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), rowsW, (unsigned)c->Ls);
+        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)c->Ls, rowsW);
         latent_tma_kernel<T, WT, K, VEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(
             (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lt_Ty,
             c->lt_ncons, c->lat_stages, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit, c->half);
@@ -377,11 +425,7 @@ struct Impl {
     // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.
     static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed) {
         const size_t n = c->n;
-        dim3 sgrid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-        dim3 sblock(ST_TX, ST_BY);
-        stencil_kernel<T, 1><<<sgrid, sblock, c->st_smem, s>>>(
-            (const T*)c->U1, (T*)c->C, (const T*)c->tapsT, c->bh, c->bw, c->H, c->W, (const T*)c->U2,
-            (const T*)c->planes, c->S, c->half);
+        stencil<1>(c, s, c->U1, c->C, c->tapsT);
         dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
         fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
             (const T*)c->C, (cplx<T>*)c->Y, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
@@ -390,12 +434,18 @@ struct Impl {
             (cplx<T>*)c->Y, (const T*)c->fpf, c->H, c->W, c->planH, (const cplx<T>*)c->twH, c->fc_cw);
         fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
             (const cplx<T>*)c->Y, (T*)c->X, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
-        stencil_kernel<T, 0><<<sgrid, sblock, c->st_smem, s>>>(
-            (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S, 0);
+        stencil<0>(c, s, c->X, c->BX, c->tapsB);
         const unsigned pblocks = (unsigned)((n + c->px_threads - 1) / c->px_threads);
-        pixel_kernel<T><<<pblocks, c->px_threads, c->px_smem, s>>>(
-            (const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2, (const T*)c->D9a,
-            (const T*)c->D9b, (const T*)c->M1, (const T*)c->F, c->H, c->W, c->Ls, c->d, (T)c->rho);
+        const T rho = (T)c->rho;
+#define FUSE_PIXEL_ARGS (const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2, \
+    (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1, (const T*)c->F, c->H, c->W, c->Ls, c->d, rho
+        if (c->Ls <= 4) pixel_kernel<T, 4><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+        else if (c->Ls <= 8) pixel_kernel<T, 8><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+        else if (c->Ls <= 16) pixel_kernel<T, 16><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+        else if (c->Ls <= 20) pixel_kernel<T, 20><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+        else if (c->Ls <= 32) pixel_kernel<T, 32><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+        else pixel_kernel_wide<T><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
+#undef FUSE_PIXEL_ARGS
         if (timed) {
             if (c->ev_used == c->ev.size()) {
                 Event2 e{};
@@ -430,9 +480,7 @@ void Impl<T>::latent_any(fuse_ctx* c, cudaStream_t s) {
 template <typename T>
 fuse_status Impl<T>::objective(fuse_ctx* c, const void* Yl, const void* Yh, double out[4]) {
     const size_t n = c->n;
-    dim3 sgrid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-    stencil_kernel<T, 0><<<sgrid, dim3(ST_TX, ST_BY), c->st_smem, c->stream>>>(
-        (const T*)c->X, (T*)c->BX, (const T*)c->tapsB, c->bh, c->bw, c->H, c->W, nullptr, nullptr, c->S, 0);
+    stencil<0>(c, c->stream, c->X, c->BX, c->tapsB);
     const unsigned nb = (unsigned)((n + 255) / 256);
     obj_data_kernel<T><<<nb, 256, 0, c->stream>>>((const T*)c->X, (const T*)c->BX, (const T*)Yl, (const T*)Yh,
                                                    c->objE, c->objER, c->H, c->W, c->d, c->Ls, c->Ll, c->Lh,

@@ -48,9 +48,9 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
     const int x0 = (tid - r * tpr) * VEC;
     const int y = blockIdx.x * Ty + r;
     const TauMap tm{S, half};
-    const int t1 = tm.t1_of_block(blockIdx.y);
+    const int t1 = tm.t1_of_block(blockIdx.z);
     const int nt2 = tm.nt2(t1);
-    const int c = blockIdx.z;
+    const int c = blockIdx.y;
     const bool active = y < H;
     const size_t n = (size_t)H * W;
     const int side = 2 * S + 1;
@@ -165,8 +165,8 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
     const int y0 = blockIdx.x * Ty;
     const int rows = min(Ty, H - y0);
     const TauMap tm{S, half};
-    const int t1 = tm.t1_of_block(blockIdx.y);
-    const int c = blockIdx.z;
+    const int t1 = tm.t1_of_block(blockIdx.z);
+    const int c = blockIdx.y;
     const size_t n = (size_t)H * W;
     const int nt2 = tm.nt2(t1);
     const int nq = nt2 * NP;

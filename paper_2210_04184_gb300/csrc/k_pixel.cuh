@@ -5,25 +5,96 @@
 //   Lambda1 <- Lambda1 - (B X - P1),  Lambda2 <- Lambda2 - (X - P2)      (eqs. dualvar1_main, 2)
 // and writes U1 = P1 + Lambda1, U2 = P2 + Lambda2 for the next right-hand side.
 // S^T S is the 0/1 mask of pixels with i1 = i2 = 0 (mod d); S^T Y_l E^T at those pixels is
-// D9a[c][i1/d][i2/d]; lambda1/rho Y_h R^T E^T is D9b[c][i1][i2].  The per-pixel band vector
-// is staged in shared memory [L_s][blockDim]; the L_s x L_s matrices are read uniformly.
+// D9a[c][i1/d][i2/d]; lambda1/rho Y_h R^T E^T is D9b[c][i1][i2].
 #pragma once
 #include "common.cuh"
 
 namespace fuse {
 
-template <typename T>
+// One thread per pixel; the pixel's band vectors live in registers (MAXLS >= L_s, loops unrolled
+// with guards so the arrays are indexed statically), every input band is loaded once, and the
+// L_s x L_s matrices sit in shared memory and are read uniformly by the warp.
+template <typename T, int MAXLS>
 __global__ void __launch_bounds__(128)
 pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ Lam1, T* __restrict__ U1,
              T* __restrict__ Lam2, T* __restrict__ U2, const T* __restrict__ D9a, const T* __restrict__ D9b,
              const T* __restrict__ M1, const T* __restrict__ F, int H, int W, int Ls, int d, T rho) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sF = reinterpret_cast<T*>(smem_raw);              // [Ls][Ls]
+    T* sM = sF + (size_t)Ls * Ls;                        // [Ls][Ls]
+    const int tid = threadIdx.x, nb = blockDim.x;
+    for (int i = tid; i < Ls * Ls; i += nb) { sF[i] = F[i]; sM[i] = M1[i]; }
+    __syncthreads();
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * nb + tid;
+    if (p >= n) return;
+    T a[MAXLS], w[MAXLS];
+    // P2 and Lambda2: a = X - Lambda2 + lambda1/rho Y_h R^T E^T, w = X - Lambda2
+#pragma unroll
+    for (int j = 0; j < MAXLS; ++j) {
+        if (j < Ls) {
+            w[j] = X[(size_t)j * n + p] - Lam2[(size_t)j * n + p];
+            a[j] = w[j] + D9b[(size_t)j * n + p];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < MAXLS; ++c) {
+        if (c < Ls) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < MAXLS; ++j)
+                if (j < Ls) acc += a[j] * sF[j * Ls + c];
+            const T l2 = acc - w[c];
+            Lam2[(size_t)c * n + p] = l2;
+            U2[(size_t)c * n + p] = acc + l2;
+        }
+    }
+    // P1 and Lambda1: w = B X - Lambda1
+#pragma unroll
+    for (int j = 0; j < MAXLS; ++j)
+        if (j < Ls) w[j] = BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p];
+    const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+    if ((y % d) == 0 && (x % d) == 0) {
+        const size_t nl = (size_t)(H / d) * (W / d);
+        const size_t pl = (size_t)(y / d) * (W / d) + x / d;
+#pragma unroll
+        for (int j = 0; j < MAXLS; ++j)
+            if (j < Ls) a[j] = rho * w[j] + D9a[(size_t)j * nl + pl];
+#pragma unroll
+        for (int c = 0; c < MAXLS; ++c) {
+            if (c < Ls) {
+                T acc = T(0);
+#pragma unroll
+                for (int j = 0; j < MAXLS; ++j)
+                    if (j < Ls) acc += a[j] * sM[j * Ls + c];
+                const T l1 = acc - w[c];
+                Lam1[(size_t)c * n + p] = l1;
+                U1[(size_t)c * n + p] = acc + l1;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < MAXLS; ++c) {
+            if (c < Ls) {                                    // P1 = B X - Lambda1, Lambda1 = 0
+                Lam1[(size_t)c * n + p] = T(0);
+                U1[(size_t)c * n + p] = w[c];
+            }
+        }
+    }
+}
+
+// Same closed forms for L_s > 32: the band vector is staged in shared memory [L_s][blockDim].
+template <typename T>
+__global__ void __launch_bounds__(128)
+pixel_kernel_wide(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ Lam1, T* __restrict__ U1,
+                  T* __restrict__ Lam2, T* __restrict__ U2, const T* __restrict__ D9a, const T* __restrict__ D9b,
+                  const T* __restrict__ M1, const T* __restrict__ F, int H, int W, int Ls, int d, T rho) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* a = reinterpret_cast<T*>(smem_raw);     // [Ls][blockDim]
     const int tid = threadIdx.x, nb = blockDim.x;
     const size_t n = (size_t)H * W;
     const size_t p = (size_t)blockIdx.x * nb + tid;
     if (p >= n) return;
-    // P2 and Lambda2
     for (int j = 0; j < Ls; ++j) a[j * nb + tid] = X[j * n + p] - Lam2[j * n + p] + D9b[j * n + p];
     for (int c = 0; c < Ls; ++c) {
         T acc = T(0);
@@ -33,13 +104,11 @@ pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ 
         Lam2[c * n + p] = l2;
         U2[c * n + p] = acc + l2;
     }
-    // P1 and Lambda1
     const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
     if ((y % d) == 0 && (x % d) == 0) {
         const size_t nl = (size_t)(H / d) * (W / d);
         const size_t pl = (size_t)(y / d) * (W / d) + x / d;
-        for (int j = 0; j < Ls; ++j)
-            a[j * nb + tid] = rho * (BX[j * n + p] - Lam1[j * n + p]) + D9a[j * nl + pl];
+        for (int j = 0; j < Ls; ++j) a[j * nb + tid] = rho * (BX[j * n + p] - Lam1[j * n + p]) + D9a[j * nl + pl];
         for (int c = 0; c < Ls; ++c) {
             T acc = T(0);
             for (int j = 0; j < Ls; ++j) acc += a[j * nb + tid] * __ldg(M1 + j * Ls + c);
@@ -50,7 +119,7 @@ pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ 
         }
     } else {
         for (int c = 0; c < Ls; ++c) {
-            const T w1 = BX[c * n + p] - Lam1[c * n + p];   // P1 = w1, Lambda1 = 0
+            const T w1 = BX[c * n + p] - Lam1[c * n + p];
             Lam1[c * n + p] = T(0);
             U1[c * n + p] = w1;
         }

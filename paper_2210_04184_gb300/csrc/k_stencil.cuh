@@ -6,7 +6,8 @@
 //         (half-window mode: tau1 >= 0 only and R doubled, see k_latent.cuh)
 //         the right-hand side C = B^T(P1 + Lambda1) + P2 + Lambda2 + sum D^T(Q + Sigma)
 //         (Sec. IV-A, after eq. x_linear_system_main), with R from the latent pass planes.
-// Tiles of 32 x 32 pixels of one band; the halo is loaded with circular wrap.
+// Tiles of 32 x 32 pixels of one band; the halo is loaded with circular wrap.  Blur sizes are
+// odd and at most 15 x 15.
 #pragma once
 #include "common.cuh"
 
@@ -14,15 +15,21 @@ namespace fuse {
 
 constexpr int ST_TX = 32, ST_TY = 32, ST_BY = 8;
 
-template <typename T, int MODE>
+// Each thread computes QY = 4 vertically adjacent outputs; for every tap column v it holds the
+// BH + QY - 1 tile values of its column in registers, so each shared-memory read feeds up to
+// QY multiply-adds.  BH is a compile-time odd size (1..15); bw is a runtime odd size.
+template <typename T, int MODE, int BH>
 __global__ void __launch_bounds__(256)
-stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ taps, int bh, int bw,
+stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ taps, int bw,
                int H, int W, const T* __restrict__ U2, const T* __restrict__ planes, int S, int half) {
+    constexpr int QY = ST_TY / ST_BY;                 // 4 outputs per thread
+    constexpr int NR = BH + QY - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int th = ST_TY + bh - 1, tw = ST_TX + bw - 1;
-    T* tile = reinterpret_cast<T*>(smem_raw);        // [th][tw]
-    T* tp = tile + (size_t)th * tw;                  // [bh][bw]
-    const int rh = bh / 2, rw = bw / 2;
+    const int th = ST_TY + BH - 1, tw = ST_TX + bw - 1;
+    T* tile = reinterpret_cast<T*>(smem_raw);         // [th][tw]
+    T* tp = tile + (size_t)th * tw;                   // [BH][bw]
+    constexpr int rh = BH / 2;
+    const int rw = bw / 2;
     const int c = blockIdx.z;
     const int x0 = blockIdx.x * ST_TX, y0 = blockIdx.y * ST_TY;
     const size_t n = (size_t)H * W;
@@ -33,22 +40,31 @@ stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restric
         const int rr = idx / tw, cc = idx - rr * tw;
         tile[idx] = inc[(size_t)wrapn(y0 - rh + rr, H) * W + wrapn(x0 - rw + cc, W)];
     }
-    for (int idx = tid; idx < bh * bw; idx += nthr) tp[idx] = taps[idx];
+    for (int idx = tid; idx < BH * bw; idx += nthr) tp[idx] = taps[idx];
     __syncthreads();
     const int x = x0 + threadIdx.x;
     if (x >= W) return;
+    const int ly0 = threadIdx.y * QY;                 // first of this thread's QY rows
+    T acc[QY];
+#pragma unroll
+    for (int q = 0; q < QY; ++q) acc[q] = T(0);
+    for (int v = 0; v < bw; ++v) {
+        T col[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) col[r] = tile[(size_t)(ly0 + r) * tw + threadIdx.x + v];
+#pragma unroll
+        for (int u = 0; u < BH; ++u) {
+            const T t = tp[u * bw + v];
+#pragma unroll
+            for (int q = 0; q < QY; ++q) acc[q] += t * col[q + u];
+        }
+    }
     const int side = 2 * S + 1;
 #pragma unroll
-    for (int q = 0; q < ST_TY / ST_BY; ++q) {
-        const int ly = threadIdx.y + q * ST_BY;
-        const int y = y0 + ly;
+    for (int q = 0; q < QY; ++q) {
+        const int y = y0 + ly0 + q;
         if (y >= H) break;
-        T acc = T(0);
-        for (int u = 0; u < bh; ++u) {
-            const T* trow = tile + (size_t)(ly + u) * tw + threadIdx.x;
-            const T* krow = tp + u * bw;
-            for (int v = 0; v < bw; ++v) acc += krow[v] * trow[v];
-        }
+        T val = acc[q];
         const size_t pix = (size_t)y * W + x;
         if constexpr (MODE == 1) {
             const T* pc = planes + (size_t)c * 2 * side * n;
@@ -57,9 +73,9 @@ stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restric
                 rs += pc[(size_t)(t1 + S) * n + pix];
                 rs -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
             }
-            acc += U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
+            val += U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
         }
-        out[(size_t)c * n + pix] = acc;
+        out[(size_t)c * n + pix] = val;
     }
 }
 

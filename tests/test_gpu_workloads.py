@@ -1,0 +1,132 @@
+"""Parity at the workloads' own sizes and launch configurations (bench.py's defaults).
+
+- pansharpening 128x128x4, FP64, 50 iterations: whole run against the oracle (1e-11);
+- unrolled-forward workload 256x256x31 -> L_s 8, 20 iterations: whole run (1e-5);
+- HS+MS 256x256x93 -> L_s 20 (the benchmark workload): the first three iterations against the
+  oracle (the third is the first with a nonzero latent state), and after the full 100
+  iterations the invariant |Sigma'| <= mu on sampled state entries;
+- HS+PAN parameters (128 bands -> 20, 11x11 blur, K = 2, S = 5) on a 64x64 crop: 8 iterations.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2210_04184_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle import nlpr  # noqa: E402
+from paper_2210_04184_gb300 import build as _build  # noqa: E402
+from paper_2210_04184_gb300.fuse import Fusion  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+
+
+def _host_gib():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _gpu(p, iters, dtype, wdtype, omega=None):
+    td = torch.float64 if dtype == "f64" else torch.float32
+    f = Fusion.from_problem(p, dtype=dtype, wdtype=wdtype)
+    yl = torch.tensor(p.Yl, dtype=td, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=td, device="cuda")
+    if omega is None:
+        f.weights(yh)
+    else:
+        f.set_weights(torch.tensor(omega, dtype=f.wtdtype, device="cuda"))
+    X, Z = f.solve(yl, yh, iters, want_Z=True)
+    f.sync()
+    return X.double().cpu().numpy(), Z.double().cpu().numpy(), f
+
+
+def _oracle(p, iters, omega):
+    X, st, _ = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S,
+                         p.lam1, p.lam2, p.rho, omega, iters, fast=True, inplace=True)
+    return nlpr.to_lhw(X)
+
+
+def test_pansharpen_fp64_full_size():
+    p, meta = synth.workload("pansharpen_128")
+    assert meta["dtype"] == "f64"
+    X, Z, _ = _gpu(p, p.iters, "f64", "f64")
+    from oracle import cloops
+    om = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    Xo = _oracle(p, p.iters, om)
+    assert rel(X, Xo) <= 1e-11
+    assert rel(Z, np.einsum("chw,cl->lhw", Xo, p.E)) <= 1e-11
+
+
+def test_unrolled_forward_full_size():
+    p, meta = synth.workload("unrolled_256")
+    X, Z, _ = _gpu(p, p.iters, "f32", "f32")
+    from oracle import cloops
+    om = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    Xo = _oracle(p, p.iters, om)
+    assert rel(X, Xo) <= 1e-5
+
+
+def test_hsms_full_size_first_iterations():
+    p, meta = synth.workload("hsms_256")
+    need = 2 * 48 * 25 * 20 * 256 * 256 * 8 / 2 ** 30 + 4          # Q and Sigma in FP64
+    if _host_gib() < need * 1.2:
+        pytest.skip(f"host has {_host_gib():.0f} GiB available, the oracle needs {need:.0f}")
+    from oracle import cloops
+    om = nlpr.round_bf16(cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h))
+    X, _, _ = _gpu(p, 3, "f32", "bf16", omega=om)
+    Xo = _oracle(p, 3, om)
+    assert rel(X, Xo) <= 1e-5
+
+
+def test_hsms_full_size_latent_invariant():
+    # After the benchmark's 100 iterations every latent entry satisfies |Sigma'| <= mu
+    # (Sigma' = -clamp(v, -mu, mu), eqs. Qj_main and dualvar3_main); checked on a sample.
+    p, meta = synth.workload("hsms_256")
+    X, Z, f = _gpu(p, p.iters, "f32", "bf16")
+    assert np.all(np.isfinite(X))
+    st = f.get_state()
+    om = f.get_weights().double().cpu().numpy()
+    n, Ls = p.H * p.W, p.L_s
+    img = n * Ls
+    kept = [t for t, tau in enumerate(nlpr.search_offsets(p.S)) if tau[0] > 0 or (tau[0] == 0 and tau[1] > 0)]
+    poffs = nlpr.patch_offsets(p.K)
+    sig = st[5 * img * 4:(5 * img + len(kept) * len(poffs) * img) * 4].view(torch.float32)
+    sig = sig.reshape(len(kept), len(poffs), Ls, p.H, p.W)
+    rng = np.random.default_rng(5)
+    coef = np.float32(p.lam2 / p.rho)
+    nz = 0
+    for _ in range(4000):
+        j = int(rng.integers(len(kept))); kk = int(rng.integers(len(poffs)))
+        c = int(rng.integers(Ls)); y = int(rng.integers(p.H)); x = int(rng.integers(p.W))
+        k = poffs[kk]
+        mu = coef * np.float32(om[kept[j], (y + k[0]) % p.H, (x + k[1]) % p.W])
+        s = float(sig[j, kk, c, y, x].item())
+        assert abs(s) <= mu * (1 + 1e-6)
+        nz += s != 0.0
+    assert nz > 0
+
+
+def test_hspan_parameters_on_crop():
+    p = synth.make_problem(H=64, W=64, L_l=128, L_h=1, L_s=20, d=4, blur_size=11, blur_sigma=2.0,
+                           snr_l=30.0, snr_h=30.0, K=2, S=5, kind="hspan", seed=synth.SEED_BASE + 2)
+    X, _, _ = _gpu(p, 8, "f32", "f32")
+    from oracle import cloops
+    om = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    Xo = _oracle(p, 8, om)
+    assert rel(X, Xo) <= 1e-5

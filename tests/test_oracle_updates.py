@@ -173,3 +173,17 @@ def test_first_two_iterates_closed_form():
     C = nlpr.blur_t(2 * P1.reshape(H, W, L_s), kern) + 2 * P2.reshape(H, W, L_s)
     ref = nlpr.solve_x_dense(C, kern, K, S)
     assert np.abs(X2 - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_inplace_latent_loops_match():
+    rng = _rng(16)
+    H, W, L, K, S = 8, 10, 2, 1, 1
+    su = nlpr.setup(np.zeros((H, W, L)), np.zeros((H, W, 1)), np.ones((1, 1)), 1,
+                    rng.random((L, 1)), np.eye(L), K, S, 1.0, 0.4, 0.3, rng.random((8, H, W)))
+    st = nlpr.State.zeros(H, W, L, K, S)
+    st.Sig = rng.standard_normal(st.Sig.shape) * 0.2
+    X = rng.standard_normal((H, W, L))
+    Qa, Sa = cloops.latent_update(X, st, su)
+    st2 = st.copy()
+    Qb, Sb = cloops.latent_update_inplace(X, st2, su)
+    assert np.array_equal(Qa, Qb) and np.array_equal(Sa, Sb) and Sb is st2.Sig
