@@ -72,12 +72,17 @@ enum {
     FUSE_OPT_PROFILE = 1,        /* 1: time every latent-pass launch with CUDA events (no graph) */
     FUSE_OPT_GRAPH = 2,          /* 1 (default): replay iterations from a captured CUDA graph */
     FUSE_OPT_LATENT_IMPL = 3,    /* latent pass: 1 (default) bulk-copy ring, 0 register-staged loads */
-    FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 256) */
+    FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 128;
+                                    256 in batches) */
     FUSE_OPT_LATENT_STAGES = 5,  /* ring slots of the bulk-copy latent pass, 2..32 (default 6) */
     FUSE_OPT_WAIT_LIMIT = 6,     /* polls before a device barrier wait gives up (default 2^22) */
-    FUSE_OPT_HALF_WINDOW = 7     /* 1 (default): keep the latent state for one offset of each
+    FUSE_OPT_HALF_WINDOW = 7,    /* 1 (default): keep the latent state for one offset of each
                                     +-tau pair (exact by the window symmetry, half the state);
                                     0: full window.  Switching reallocates the state and clears it. */
+    FUSE_OPT_LATENT_BANDS = 8,   /* bands streamed by one latent block, 1..64 (default 1;
+                                    2 in batches) */
+    FUSE_OPT_FFT_ROWS = 9,       /* rows per block of the row FFT passes: 1, 2, 4 or 8 */
+    FUSE_OPT_FFT_COLS = 10       /* columns per block of the column FFT pass: power of 2 <= 32 */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -177,6 +182,16 @@ fuse_status fuse_set_state(fuse_ctx* ctx, const void* src);
  * leave the previous setting in place. */
 fuse_status fuse_set_option(fuse_ctx* ctx, int option, long long value);
 
+/* Current value of an option (FUSE_OPT_*). */
+fuse_status fuse_get_option(fuse_ctx* ctx, int option, long long* value);
+
+/* Launch-shape tuner: with the context's weights and the given inputs (as in fuse_solve), times
+ * `iters` iterations for each candidate shape of the latent pass (consumer threads 128/192/256,
+ * ring slots 4/6/8, bands per block 1/2) and of the FFT passes (rows per block 1..8, columns per
+ * block 2..16) and keeps the fastest.  Results do not depend on the shapes (bit-identical).
+ * Leaves the context without state: the next fuse_solve starts from zero.  Synchronous. */
+fuse_status fuse_autotune(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters);
+
 /* Wait for all work issued on the context's stream and report device-side failures:
  * FUSE_ETIMEOUT if a bounded barrier wait inside a kernel gave up since the last check
  * (the results of that work are then invalid), FUSE_ECUDA on an execution error. */
@@ -211,6 +226,43 @@ fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev, int H, int
  * returns FUSE_OK when the wait gave up and its timeout was reported to the host as designed,
  * leaving the context usable.  Synchronous. */
 fuse_status fuse_selftest(fuse_ctx* ctx, int which);
+
+/* ---- Batches of independent problems (uneven sizes) ------------------------------------
+ * A batch runs the ADMM of several contexts together: each iteration is one launch per
+ * phase (right-hand side, three FFT passes, B X, pixel updates, latent pass) over the work of
+ * every problem, replayed from one captured CUDA graph.  The contexts must share dtype,
+ * wdtype, K, S, L_s (<= 32), blur size and half-window mode; sizes (H, W, ratio, L_l, L_h) may
+ * differ.  The batch does not own the contexts: destroy the batch before them.  Creating a
+ * batch moves every context onto the batch's stream. */
+typedef struct fuse_batch fuse_batch;
+
+/* Build the launch tables for ctxs[0..n) (device memory for the tables is allocated here).
+ * Errors: FUSE_EINVAL (mismatched or duplicate contexts), FUSE_EUNSUPPORTED, FUSE_ENOMEM. */
+fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, void* stream);
+
+/* Solve every problem of the batch from a zero start for `iters` iterations.  Yl[i], Yh[i] are
+ * the device inputs of problem i (as in fuse_solve); X_out, Z_out are nullable arrays of
+ * nullable device outputs.  Every context must hold weights (fuse_weights or
+ * fuse_set_weights).  Asynchronous on the batch's stream. */
+fuse_status fuse_batch_solve(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters,
+                             void* const* X_out, void* const* Z_out);
+
+/* FUSE_OPT_PROFILE, FUSE_OPT_GRAPH, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES,
+ * FUSE_OPT_LATENT_BANDS. */
+fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value);
+
+/* Launch-shape tuner of a batch (latent pass: consumer threads, ring slots, bands per block),
+ * timing `iters` batched iterations per candidate; inputs as in fuse_batch_solve.  Synchronous. */
+fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters);
+
+/* As fuse_profile, for the batched launches (FUSE_K_LATENT: the batched latent pass). */
+fuse_status fuse_batch_profile(fuse_batch* b, int which, double* ms, long long* launches, int reset);
+
+/* Synchronise the batch's stream and report device-side failures of any of its problems. */
+fuse_status fuse_batch_sync(fuse_batch* b);
+
+fuse_status fuse_batch_destroy(fuse_batch* b);
+const char* fuse_batch_last_error(const fuse_batch* b);
 
 /* Last error text of the context ("" if none); valid until the next call on ctx. */
 const char* fuse_last_error(const fuse_ctx* ctx);

@@ -28,6 +28,9 @@ template <typename T, int N> struct alignas(sizeof(T) * N) vecT { T v[N]; };
 
 // Weight storage type -> arithmetic type.
 __device__ __forceinline__ float wload(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float wconv(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float wconv(float v) { return v; }
+__device__ __forceinline__ double wconv(double v) { return v; }
 __device__ __forceinline__ float wload(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double wload(const double* p) { return __ldg(p); }
 
@@ -57,6 +60,40 @@ __device__ __forceinline__ vecT<double, 2> ld_stream(const vecT<double, 2>* p) {
 }
 __device__ __forceinline__ void st_stream(vecT<double, 2>* p, const vecT<double, 2>& a) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(a.v[0], a.v[1]));
+}
+
+// Vectors of VEC elements (VEC * sizeof(T) = 16 or 32 bytes) moved as 16-byte parts.
+template <typename T, int VEC>
+__device__ __forceinline__ void vload(const T* p, T (&v)[VEC]) {
+    constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+    for (int q = 0; q < VEC / PER; ++q) {
+        const vecT<T, PER> a = reinterpret_cast<const vecT<T, PER>*>(p)[q];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) v[q * PER + j] = a.v[j];
+    }
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[VEC]) {
+    constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+    for (int q = 0; q < VEC / PER; ++q) {
+        vecT<T, PER> a;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) a.v[j] = v[q * PER + j];
+        reinterpret_cast<vecT<T, PER>*>(p)[q] = a;
+    }
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void vstore_stream(T* p, const T (&v)[VEC]) {
+    constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+    for (int q = 0; q < VEC / PER; ++q) {
+        vecT<T, PER> a;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) a.v[j] = v[q * PER + j];
+        st_stream(reinterpret_cast<vecT<T, PER>*>(p) + q, a);
+    }
 }
 
 // Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1
@@ -90,5 +127,27 @@ struct TauMap {
         return t1 == 0 ? t2 - 1 : S + (t1 - 1) * (2 * S + 1) + (t2 + S);
     }
 };
+
+// A batched launch is a 1D grid whose blocks are split into segments; segment s covers the
+// blocks [start, start + gx*gy*gz) of problem `prob`, laid out x fastest, with block row z
+// starting at z0.  Segments are sorted by start.
+struct Segment {
+    int prob, start, gx, gy, gz, z0;
+};
+
+__device__ __forceinline__ void segment_of_block(const Segment* __restrict__ seg, int nseg, int b, int* prob,
+                                                 int* bx, int* by, int* bz) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&seg[mid].start) <= b) lo = mid; else hi = mid - 1;
+    }
+    const Segment s = seg[lo];
+    const int id = b - s.start;
+    *prob = s.prob;
+    *bx = id % s.gx;
+    *by = (id / s.gx) % s.gy;
+    *bz = s.z0 + id / (s.gx * s.gy);
+}
 
 }  // namespace fuse

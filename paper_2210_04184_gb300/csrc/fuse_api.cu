@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -75,7 +76,7 @@ struct fuse_ctx {
     cudaGraphExec_t gexec = nullptr;
     int fault_alloc = -1, alloc_count = 0;
     // latent pass variant: 0 = register-staged loads, 1 = bulk-copy (TMA) ring
-    int lat_impl = 1, lat_target = 256, lat_stages = 6;
+    int lat_impl = 1, lat_target = 128, lat_stages = 6, lat_bpb = 1;
     int lt_Ty = 1, lt_ncons = 0;
     size_t lt_smem = 0;
     int* d_err = nullptr;
@@ -265,9 +266,12 @@ Sizes sizes_of(const fuse_geometry* g, int K, int S, int ratio, size_t esz, size
 }
 
 // Launch shape of the bulk-copy latent pass: about `target` consumer threads per block (full
-// rows), `stages` ring slots; false if it does not fit in shared memory.
+// rows, 32 bytes of pixels per thread), `stages` ring slots; false if W is not a multiple of
+// the vector or the ring does not fit in shared memory (the register-staged pass is used then).
 bool latent_tma_shape(fuse_ctx* c) {
-    const int tpr = c->W / c->vec;
+    const int tvec = (int)(32 / c->esz);        // 8 floats or 4 doubles per thread and chunk
+    if (c->W % tvec) return false;
+    const int tpr = c->W / tvec;
     int Ty = c->lat_target / tpr;
     if (Ty < 1) Ty = 1;
     if (Ty > c->H) Ty = c->H;
@@ -286,78 +290,125 @@ bool latent_tma_shape(fuse_ctx* c) {
 // typed launch sequence
 // ---------------------------------------------------------------------------------------
 
+// Compile-time dispatch helpers: call f(std::integral_constant<int, V>{}) for a runtime value.
+template <typename F>
+void with_bh(int bh, F&& f) {
+    switch (bh) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        case 5: f(std::integral_constant<int, 5>{}); break;
+        case 7: f(std::integral_constant<int, 7>{}); break;
+        case 9: f(std::integral_constant<int, 9>{}); break;
+        case 11: f(std::integral_constant<int, 11>{}); break;
+        case 13: f(std::integral_constant<int, 13>{}); break;
+        default: f(std::integral_constant<int, 15>{}); break;
+    }
+}
+
+template <typename F>
+void with_k(int K, F&& f) {
+    switch (K) {
+        case 0: f(std::integral_constant<int, 0>{}); break;
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        default: f(std::integral_constant<int, 3>{}); break;
+    }
+}
+
+// MAXLS bucket of the register-resident pixel kernel (0 = wide kernel).
+inline int pixel_bucket(int Ls) {
+    return Ls <= 4 ? 4 : Ls <= 8 ? 8 : Ls <= 16 ? 16 : Ls <= 20 ? 20 : Ls <= 32 ? 32 : 0;
+}
+
+template <typename F>
+void with_maxls(int Ls, F&& f) {
+    switch (pixel_bucket(Ls)) {
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        case 20: f(std::integral_constant<int, 20>{}); break;
+        case 32: f(std::integral_constant<int, 32>{}); break;
+        default: f(std::integral_constant<int, 0>{}); break;
+    }
+}
+
 template <typename T>
 struct Impl {
-    static fuse_status set_attrs(fuse_ctx* c) {
-        CK(c, cudaFuncSetAttribute(fft_rows_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fr_smem));
-        CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fr_smem));
-        CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->fc_smem));
+    static constexpr int VEC = 16 / sizeof(T);
+    static constexpr int TVEC = 32 / sizeof(T);        // pixels per thread of the bulk-copy pass
 
-        CK(c, cudaFuncSetAttribute(pixel_kernel_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->px_smem));
-        if (stencil_attr(c) != FUSE_OK) return c->sticky;
-        CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    // ---- argument blocks of the iteration kernels ----
+    static StencilArgs<T> st_args(fuse_ctx* c, const void* in, void* out, const void* taps) {
+        return StencilArgs<T>{(const T*)in, (T*)out, (const T*)taps, c->bw, c->H, c->W,
+                              (const T*)c->U2, (const T*)c->planes, c->S, c->half};
+    }
+    static FFTArgs<T> fft_args(fuse_ctx* c, int rpb, int cw) {
+        return FFTArgs<T>{(const T*)c->C, (cplx<T>*)c->Y, (T*)c->X, (const T*)c->fpf, c->H, c->W, c->Ls,
+                          c->planW, c->planH, (const cplx<T>*)c->twW, (const cplx<T>*)c->twH, rpb, cw};
+    }
+    static PixelArgs<T> px_args(fuse_ctx* c) {
+        return PixelArgs<T>{(const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2,
+                            (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1, (const T*)c->F,
+                            c->H, c->W, c->Ls, c->d, (T)c->rho};
+    }
+    template <typename WT>
+    static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb) {
+        return LatentArgs<T, WT>{(const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W,
+                                 c->Ls, c->S, Ty, ncons, D, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit,
+                                 c->half, bpb};
+    }
+
+    static fuse_status set_attrs(fuse_ctx* c) {
+        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        // The cap is a property of the kernel function shared by every context in the process,
+        // so it is set to the largest size any context may request, never to this context's.
+        CK(c, cudaFuncSetAttribute(fft_rows_fwd_kernel<T>, A, kMaxSmem));
+        CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, A, kMaxSmem));
+        CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, A, kMaxSmem));
+        CK(c, cudaFuncSetAttribute(pixel_kernel_wide<T>, A, kMaxSmem));
+        cudaError_t e = cudaSuccess;
+        with_bh(c->bh, [&](auto bh) {
+            constexpr int BH = decltype(bh)::value;
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 0, BH>, A, kMaxSmem);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 1, BH>, A, kMaxSmem);
+        });
+        CK(c, e);
+        CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, A, kMaxSmem));
         return FUSE_OK;
     }
 
     template <typename WT>
     static fuse_status set_attrs_w(fuse_ctx* c) {
-        CK(c, cudaFuncSetAttribute(weights_kernel<T, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->w_smem));
-        constexpr int V = 16 / sizeof(T);
         const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        switch (c->K) {
-            case 0: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 0, V>, A, (int)c->lat_smem));
-                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 0, V>, A, kMaxSmem)); break;
-            case 1: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 1, V>, A, (int)c->lat_smem));
-                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 1, V>, A, kMaxSmem)); break;
-            case 2: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 2, V>, A, (int)c->lat_smem));
-                    CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 2, V>, A, kMaxSmem)); break;
-            default: CK(c, cudaFuncSetAttribute(latent_kernel<T, WT, 3, V>, A, (int)c->lat_smem));
-                     CK(c, cudaFuncSetAttribute(latent_tma_kernel<T, WT, 3, V>, A, kMaxSmem)); break;
-        }
+        CK(c, cudaFuncSetAttribute(weights_kernel<T, WT>, A, kMaxSmem));
+        cudaError_t e = cudaSuccess;
+        with_k(c->K, [&](auto k) {
+            constexpr int K = decltype(k)::value;
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_kernel<T, WT, K, VEC>, A, kMaxSmem);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, K, TVEC>, A, kMaxSmem);
+        });
+        CK(c, e);
         return FUSE_OK;
-    }
-
-    template <int MODE, int BH>
-    static void stencil_bh(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
-        dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-        stencil_kernel<T, MODE, BH><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(
-            (const T*)in, (T*)out, (const T*)taps, c->bw, c->H, c->W, (const T*)c->U2, (const T*)c->planes, c->S,
-            c->half);
     }
 
     // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
     template <int MODE>
     static void stencil(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
-        switch (c->bh) {
-            case 1: stencil_bh<MODE, 1>(c, s, in, out, taps); break;
-            case 3: stencil_bh<MODE, 3>(c, s, in, out, taps); break;
-            case 5: stencil_bh<MODE, 5>(c, s, in, out, taps); break;
-            case 7: stencil_bh<MODE, 7>(c, s, in, out, taps); break;
-            case 9: stencil_bh<MODE, 9>(c, s, in, out, taps); break;
-            case 11: stencil_bh<MODE, 11>(c, s, in, out, taps); break;
-            case 13: stencil_bh<MODE, 13>(c, s, in, out, taps); break;
-            default: stencil_bh<MODE, 15>(c, s, in, out, taps); break;
-        }
+        dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
+        const StencilArgs<T> a = st_args(c, in, out, taps);
+        with_bh(c->bh, [&](auto bh) {
+            stencil_kernel<T, MODE, decltype(bh)::value><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a);
+        });
     }
 
-    template <int BH>
-    static fuse_status stencil_attr_bh(fuse_ctx* c) {
-        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 0, BH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
-        CK(c, cudaFuncSetAttribute(stencil_kernel<T, 1, BH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->st_smem));
-        return FUSE_OK;
-    }
-
-    static fuse_status stencil_attr(fuse_ctx* c) {
-        switch (c->bh) {
-            case 1: return stencil_attr_bh<1>(c);
-            case 3: return stencil_attr_bh<3>(c);
-            case 5: return stencil_attr_bh<5>(c);
-            case 7: return stencil_attr_bh<7>(c);
-            case 9: return stencil_attr_bh<9>(c);
-            case 11: return stencil_attr_bh<11>(c);
-            case 13: return stencil_attr_bh<13>(c);
-            default: return stencil_attr_bh<15>(c);
-        }
+    static void pixel(fuse_ctx* c, cudaStream_t s) {
+        const unsigned pblocks = (unsigned)((c->n + c->px_threads - 1) / c->px_threads);
+        const PixelArgs<T> a = px_args(c);
+        with_maxls(c->Ls, [&](auto m) {
+            constexpr int M = decltype(m)::value;
+            if constexpr (M == 0) pixel_kernel_wide<T><<<pblocks, c->px_threads, c->px_smem, s>>>(a);
+            else pixel_kernel<T, M><<<pblocks, c->px_threads, c->px_smem, s>>>(a);
+        });
     }
 
     static fuse_status band_mix(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* M, size_t npix,
@@ -381,71 +432,45 @@ struct Impl {
         return FUSE_OK;
     }
 
-    template <typename WT, int K>
-    static void launch_latent(fuse_ctx* c, cudaStream_t s) {
-        constexpr int VEC = 16 / sizeof(T);
-        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
-        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
-        latent_kernel<T, WT, K, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
-            (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lat_Ty,
-            (T)(c->lam2 / c->rho), c->half);
-    }
-
-    template <typename WT, int K>
-    static void launch_latent_tma(fuse_ctx* c, cudaStream_t s) {
-        constexpr int VEC = 16 / sizeof(T);
-        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
-        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)c->Ls, rowsW);
-        latent_tma_kernel<T, WT, K, VEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(
-            (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lt_Ty,
-            c->lt_ncons, c->lat_stages, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit, c->half);
-    }
-
     template <typename WT>
     static void latent(fuse_ctx* c, cudaStream_t s) {
+        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
         if (c->lat_impl == 1) {
-            switch (c->K) {
-                case 0: launch_latent_tma<WT, 0>(c, s); break;
-                case 1: launch_latent_tma<WT, 1>(c, s); break;
-                case 2: launch_latent_tma<WT, 2>(c, s); break;
-                default: launch_latent_tma<WT, 3>(c, s); break;
-            }
+            dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)((c->Ls + c->lat_bpb - 1) / c->lat_bpb),
+                      rowsW);
+            const LatentArgs<T, WT> a = lat_args<WT>(c, c->lt_Ty, c->lt_ncons, c->lat_stages, c->lat_bpb);
+            with_k(c->K, [&](auto k) {
+                latent_tma_kernel<T, WT, decltype(k)::value, TVEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
+            });
             return;
         }
-        switch (c->K) {
-            case 0: launch_latent<WT, 0>(c, s); break;
-            case 1: launch_latent<WT, 1>(c, s); break;
-            case 2: launch_latent<WT, 2>(c, s); break;
-            default: launch_latent<WT, 3>(c, s); break;
-        }
+        dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
+        with_k(c->K, [&](auto k) {
+            latent_kernel<T, WT, decltype(k)::value, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
+                (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S,
+                c->lat_Ty, (T)(c->lam2 / c->rho), c->half);
+        });
     }
 
     static void latent_any(fuse_ctx* c, cudaStream_t s);
 
     // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.
     static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed) {
-        const size_t n = c->n;
         stencil<1>(c, s, c->U1, c->C, c->tapsT);
+        CKL(c, "stencil_kernel (right-hand side)");
+        const FFTArgs<T> fa = fft_args(c, c->fr_rpb, c->fc_cw);
         dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
-        fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
-            (const T*)c->C, (cplx<T>*)c->Y, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
+        fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+        CKL(c, "fft_rows_fwd_kernel");
         dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
-        fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(
-            (cplx<T>*)c->Y, (const T*)c->fpf, c->H, c->W, c->planH, (const cplx<T>*)c->twH, c->fc_cw);
-        fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(
-            (const cplx<T>*)c->Y, (T*)c->X, c->H, c->W, c->Ls, c->planW, (const cplx<T>*)c->twW, c->fr_rpb);
+        fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
+        CKL(c, "fft_cols_kernel");
+        fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+        CKL(c, "fft_rows_inv_kernel");
         stencil<0>(c, s, c->X, c->BX, c->tapsB);
-        const unsigned pblocks = (unsigned)((n + c->px_threads - 1) / c->px_threads);
-        const T rho = (T)c->rho;
-#define FUSE_PIXEL_ARGS (const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2, \
-    (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1, (const T*)c->F, c->H, c->W, c->Ls, c->d, rho
-        if (c->Ls <= 4) pixel_kernel<T, 4><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-        else if (c->Ls <= 8) pixel_kernel<T, 8><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-        else if (c->Ls <= 16) pixel_kernel<T, 16><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-        else if (c->Ls <= 20) pixel_kernel<T, 20><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-        else if (c->Ls <= 32) pixel_kernel<T, 32><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-        else pixel_kernel_wide<T><<<pblocks, c->px_threads, c->px_smem, s>>>(FUSE_PIXEL_ARGS);
-#undef FUSE_PIXEL_ARGS
+        CKL(c, "stencil_kernel (B X)");
+        pixel(c, s);
+        CKL(c, "pixel_kernel");
         if (timed) {
             if (c->ev_used == c->ev.size()) {
                 Event2 e{};
@@ -460,7 +485,7 @@ struct Impl {
         } else {
             latent_any(c, s);
         }
-        CKL(c, "iteration kernels");
+        CKL(c, "latent kernel");
         return FUSE_OK;
     }
 
@@ -626,6 +651,290 @@ fuse_status upload(fuse_ctx* c, void** dst, const std::vector<double>& v) {
 
 fuse_status upload_any(fuse_ctx* c, void** dst, const std::vector<double>& v) {
     return c->dtype == FUSE_F64 ? upload<double>(c, dst, v) : upload<float>(c, dst, v);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// batches of independent problems of uneven sizes: one launch per ADMM phase
+// ---------------------------------------------------------------------------------------
+
+struct fuse_batch {
+    std::vector<fuse_ctx*> ctx;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int device = 0;
+    fuse_dtype dtype = FUSE_F32, wdtype = FUSE_F32;
+    int K = 0, S = 0, Ls = 0, bh = 1, bw = 1, half = 1;
+    // launch shapes shared by all problems
+    int lat_target = 256, lat_stages = 6, lat_ncons = 0, lat_bpb = 2;
+    size_t lat_smem = 0, st_smem = 0, fr_smem = 0, fc_smem = 0, px_smem = 0;
+    int fr_rpb = 4, fc_cw = 8;
+    // device tables: [args of every problem] and segments per kernel
+    void* d_lat = nullptr; Segment* d_lat_seg = nullptr; int lat_nseg = 0, lat_blocks = 0;
+    void* d_st1 = nullptr; void* d_st0 = nullptr; Segment* d_st_seg = nullptr; int st_nseg = 0, st_blocks = 0;
+    void* d_fft = nullptr; Segment* d_fr_seg = nullptr; Segment* d_fc_seg = nullptr;
+    int fr_nseg = 0, fr_blocks = 0, fc_nseg = 0, fc_blocks = 0;
+    void* d_px = nullptr; Segment* d_px_seg = nullptr; int px_nseg = 0, px_blocks = 0;
+    std::vector<void*> allocs;
+    bool profile = false, use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<Event2> ev;
+    size_t ev_used = 0;
+    double latent_ms = 0.0;
+    long long launches_all = 0, launches_latent = 0;
+    fuse_status sticky = FUSE_OK;
+    std::string err;
+};
+
+namespace {
+
+fuse_status bfail(fuse_batch* b, fuse_status s, const std::string& msg) {
+    if (b) {
+        if (b->sticky == FUSE_OK) b->sticky = s;
+        b->err = msg;
+    }
+    return s;
+}
+
+#define BCK(b, expr)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            char m_[512];                                                                     \
+            snprintf(m_, sizeof m_, "%s: %s", #expr, cudaGetErrorString(e_));                 \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? FUSE_ENOMEM : FUSE_ECUDA, m_); \
+        }                                                                                     \
+    } while (0)
+
+template <typename V>
+fuse_status bupload(fuse_batch* b, void** dst, const std::vector<V>& v) {
+    cudaError_t e = cudaMalloc(dst, v.size() * sizeof(V) + 16);
+    if (e != cudaSuccess) { *dst = nullptr; cudaGetLastError(); return bfail(b, FUSE_ENOMEM, "cudaMalloc (batch tables)"); }
+    b->allocs.push_back(*dst);
+    BCK(b, cudaMemcpy(*dst, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return FUSE_OK;
+}
+
+// Appends the segments of one problem's (gx, gy, gz) grid starting at block `*next`.
+void add_segment(std::vector<Segment>& seg, int prob, int gx, int gy, int gz, int z0, int* next) {
+    if (gx <= 0 || gy <= 0 || gz <= 0) return;
+    seg.push_back(Segment{prob, *next, gx, gy, gz, z0});
+    *next += gx * gy * gz;
+}
+
+template <typename T, typename WT>
+struct BatchImpl {
+    static constexpr int VEC = 32 / sizeof(T);          // pixels per thread of the latent pass
+
+    static fuse_status build(fuse_batch* b) {
+        const int n = (int)b->ctx.size();
+        const size_t esz = sizeof(T), csz = 2 * sizeof(T);
+        const int side = 2 * b->S + 1;
+        const int rows = b->half ? b->S + 1 : side;
+        // latent: per-problem Ty, common consumer count and ring depth
+        std::vector<LatentArgs<T, WT>> la(n);
+        std::vector<int> Ty(n);
+        b->lat_ncons = 32;
+        for (int i = 0; i < n; ++i) {
+            fuse_ctx* c = b->ctx[i];
+            if (c->W % VEC) return bfail(b, FUSE_EUNSUPPORTED, "batched problems need W a multiple of 32 bytes of pixels");
+            const int tpr = c->W / VEC;
+            int ty = b->lat_target / tpr;
+            ty = ty < 1 ? 1 : (ty > c->H ? c->H : ty);
+            while (ty > 1 && ((tpr * ty + 31) / 32) * 32 + 32 > 288) --ty;
+            const int nc = ((tpr * ty + 31) / 32) * 32;
+            if (nc + 32 > 288) return bfail(b, FUSE_EUNSUPPORTED, "image too wide for the batched latent pass");
+            Ty[i] = ty;
+            if (nc > b->lat_ncons) b->lat_ncons = nc;
+        }
+        b->lat_smem = 0;
+        for (int i = 0; i < n; ++i) {
+            fuse_ctx* c = b->ctx[i];
+            la[i] = Impl<T>::template lat_args<WT>(c, Ty[i], b->lat_ncons, b->lat_stages, b->lat_bpb);
+            const size_t sm = (size_t)(b->lat_stages + side) * Ty[i] * c->W * esz + 2 * (size_t)b->lat_stages * 8;
+            if (sm > b->lat_smem) b->lat_smem = sm;
+        }
+        if (b->lat_smem > (size_t)kMaxSmem) return bfail(b, FUSE_EUNSUPPORTED, "batched latent ring exceeds shared memory");
+        std::vector<Segment> seg;
+        int next = 0;
+        const int groups = (b->Ls + b->lat_bpb - 1) / b->lat_bpb;
+        for (int i = 0; i < n; ++i)          // heavy block rows (tau1 != 0) of every problem first
+            add_segment(seg, i, (b->ctx[i]->H + Ty[i] - 1) / Ty[i], groups, rows - 1, 0, &next);
+        for (int i = 0; i < n; ++i)          // then the lighter tau1 = 0 rows
+            add_segment(seg, i, (b->ctx[i]->H + Ty[i] - 1) / Ty[i], groups, 1, rows - 1, &next);
+        b->lat_nseg = (int)seg.size();
+        b->lat_blocks = next;
+        fuse_status st;
+        if ((st = bupload(b, &b->d_lat, la)) != FUSE_OK) return st;
+        if ((st = bupload(b, (void**)&b->d_lat_seg, seg)) != FUSE_OK) return st;
+
+        // stencils (same blur for all problems)
+        std::vector<StencilArgs<T>> s1(n), s0(n);
+        seg.clear();
+        next = 0;
+        for (int i = 0; i < n; ++i) {
+            fuse_ctx* c = b->ctx[i];
+            s1[i] = Impl<T>::st_args(c, c->U1, c->C, c->tapsT);
+            s0[i] = Impl<T>::st_args(c, c->X, c->BX, c->tapsB);
+            add_segment(seg, i, (c->W + ST_TX - 1) / ST_TX, (c->H + ST_TY - 1) / ST_TY, b->Ls, 0, &next);
+        }
+        b->st_smem = b->ctx[0]->st_smem;
+        b->st_nseg = (int)seg.size();
+        b->st_blocks = next;
+        if ((st = bupload(b, &b->d_st1, s1)) != FUSE_OK) return st;
+        if ((st = bupload(b, &b->d_st0, s0)) != FUSE_OK) return st;
+        if ((st = bupload(b, (void**)&b->d_st_seg, seg)) != FUSE_OK) return st;
+
+        // FFT passes: 256 threads, rpb rows (tpr = 256 / rpb) or CW columns per block
+        std::vector<FFTArgs<T>> fa(n);
+        std::vector<Segment> sr, sc;
+        int nr = 0, ncl = 0;
+        b->fr_smem = b->fc_smem = 0;
+        for (int i = 0; i < n; ++i) {
+            fuse_ctx* c = b->ctx[i];
+            fa[i] = Impl<T>::fft_args(c, b->fr_rpb, b->fc_cw);
+            add_segment(sr, i, (c->H + b->fr_rpb - 1) / b->fr_rpb, c->npair, 1, 0, &nr);
+            add_segment(sc, i, (c->W + b->fc_cw - 1) / b->fc_cw, c->npair, 1, 0, &ncl);
+            const size_t r = 2 * (size_t)b->fr_rpb * c->W * csz;
+            const size_t cc = (size_t)b->fc_cw * (2 * c->H + 1) * csz;
+            if (r > b->fr_smem) b->fr_smem = r;
+            if (cc > b->fc_smem) b->fc_smem = cc;
+        }
+        if (b->fr_smem > (size_t)kMaxSmem || b->fc_smem > (size_t)kMaxSmem)
+            return bfail(b, FUSE_EUNSUPPORTED, "image too large for the batched FFT");
+        b->fr_nseg = (int)sr.size(); b->fr_blocks = nr;
+        b->fc_nseg = (int)sc.size(); b->fc_blocks = ncl;
+        if ((st = bupload(b, &b->d_fft, fa)) != FUSE_OK) return st;
+        if ((st = bupload(b, (void**)&b->d_fr_seg, sr)) != FUSE_OK) return st;
+        if ((st = bupload(b, (void**)&b->d_fc_seg, sc)) != FUSE_OK) return st;
+
+        // pixel updates
+        std::vector<PixelArgs<T>> pa(n);
+        seg.clear();
+        next = 0;
+        for (int i = 0; i < n; ++i) {
+            fuse_ctx* c = b->ctx[i];
+            pa[i] = Impl<T>::px_args(c);
+            add_segment(seg, i, (int)((c->n + 127) / 128), 1, 1, 0, &next);
+        }
+        b->px_smem = 2 * (size_t)b->Ls * b->Ls * esz;
+        b->px_nseg = (int)seg.size();
+        b->px_blocks = next;
+        if ((st = bupload(b, &b->d_px, pa)) != FUSE_OK) return st;
+        if ((st = bupload(b, (void**)&b->d_px_seg, seg)) != FUSE_OK) return st;
+
+        // attributes
+        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaSuccess;
+        with_k(b->K, [&](auto k) {
+            e = cudaFuncSetAttribute(latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC>, A, kMaxSmem);
+        });
+        BCK(b, e);
+        with_bh(b->bh, [&](auto bh) {
+            constexpr int BH = decltype(bh)::value;
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 0, BH>, A, kMaxSmem);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 1, BH>, A, kMaxSmem);
+        });
+        BCK(b, e);
+        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 0>, A, kMaxSmem));
+        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 1>, A, kMaxSmem));
+        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 2>, A, kMaxSmem));
+        return FUSE_OK;
+    }
+
+    // One batched ADMM iteration: 7 launches cover every problem.
+    static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed) {
+        with_bh(b->bh, [&](auto bh) {
+            stencil_batch_kernel<T, 1, decltype(bh)::value><<<b->st_blocks, dim3(ST_TX, ST_BY), b->st_smem, s>>>(
+                (const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg);
+        });
+        fft_batch_kernel<T, 0><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
+        fft_batch_kernel<T, 1><<<b->fc_blocks, 256, b->fc_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fc_seg, b->fc_nseg);
+        fft_batch_kernel<T, 2><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
+        with_bh(b->bh, [&](auto bh) {
+            stencil_batch_kernel<T, 0, decltype(bh)::value><<<b->st_blocks, dim3(ST_TX, ST_BY), b->st_smem, s>>>(
+                (const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg);
+        });
+        with_maxls(b->Ls, [&](auto m) {
+            constexpr int M = decltype(m)::value;
+            if constexpr (M != 0)
+                pixel_batch_kernel<T, M><<<b->px_blocks, 128, b->px_smem, s>>>((const PixelArgs<T>*)b->d_px,
+                                                                             b->d_px_seg, b->px_nseg);
+        });
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            if (b->ev_used == b->ev.size()) {
+                Event2 e{};
+                BCK(b, cudaEventCreate(&e.a));
+                BCK(b, cudaEventCreate(&e.b));
+                b->ev.push_back(e);
+            }
+            e0 = b->ev[b->ev_used].a;
+            e1 = b->ev[b->ev_used].b;
+            b->ev_used++;
+            BCK(b, cudaEventRecord(e0, s));
+        }
+        with_k(b->K, [&](auto k) {
+            latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
+                (const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg);
+        });
+        if (timed) BCK(b, cudaEventRecord(e1, s));
+        BCK(b, cudaGetLastError());
+        return FUSE_OK;
+    }
+};
+
+fuse_status batch_build(fuse_batch* b) {
+    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::build(b);
+    if (b->wdtype == FUSE_BF16) return BatchImpl<float, __nv_bfloat16>::build(b);
+    return BatchImpl<float, float>::build(b);
+}
+
+fuse_status batch_iterate(fuse_batch* b, cudaStream_t s, bool timed) {
+    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::iterate(b, s, timed);
+    if (b->wdtype == FUSE_BF16) return BatchImpl<float, __nv_bfloat16>::iterate(b, s, timed);
+    return BatchImpl<float, float>::iterate(b, s, timed);
+}
+
+void batch_release(fuse_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    for (auto& e : b->ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    b->ev.clear();
+    for (void* p : b->allocs) if (p) cudaFree(p);
+    b->allocs.clear();
+}
+
+fuse_status batch_run(fuse_batch* b, int iters) {
+    if (iters <= 0) return FUSE_OK;
+    if (b->profile || !b->use_graph) {
+        for (int t = 0; t < iters; ++t) {
+            fuse_status st = batch_iterate(b, b->stream, b->profile);
+            if (st != FUSE_OK) return st;
+            b->launches_all += 7;
+            b->launches_latent += 1;
+        }
+        return FUSE_OK;
+    }
+    if (!b->gexec) {
+        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        fuse_status st = batch_iterate(b, b->cap_stream, false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
+        BCK(b, e);
+        b->graph = g;
+        BCK(b, cudaGraphInstantiate(&b->gexec, b->graph, 0));
+    }
+    for (int t = 0; t < iters; ++t) {
+        BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+        b->launches_all += 7;
+        b->launches_latent += 1;
+    }
+    return FUSE_OK;
 }
 
 }  // namespace
@@ -985,6 +1294,12 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
     switch (option) {
         case FUSE_OPT_PROFILE: c->profile = value != 0; return FUSE_OK;
         case FUSE_OPT_GRAPH: c->use_graph = value != 0; return FUSE_OK;
+        case FUSE_OPT_LATENT_BANDS:
+            if (value < 1 || value > 64) return fail(c, FUSE_EINVAL, "bands per latent block must be in [1, 64]");
+            c->lat_bpb = (int)value;
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
         case FUSE_OPT_LATENT_IMPL:
         case FUSE_OPT_LATENT_THREADS:
         case FUSE_OPT_LATENT_STAGES: {
@@ -993,11 +1308,35 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             if (option == FUSE_OPT_LATENT_THREADS) c->lat_target = (int)value;
             if (option == FUSE_OPT_LATENT_STAGES) c->lat_stages = (int)value;
             if (c->lat_target < 32 || c->lat_target > 256 || c->lat_stages < 2 || c->lat_stages > 32 ||
-                !latent_tma_shape(c)) {
+                (c->lat_impl == 1 && !latent_tma_shape(c))) {
                 c->lat_impl = old_impl; c->lat_target = old_t; c->lat_stages = old_d;
                 latent_tma_shape(c);
                 return fail(c, FUSE_EINVAL, "latent launch option out of range");
             }
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
+        }
+        case FUSE_OPT_FFT_ROWS: {
+            const int rpb = (int)value;
+            const size_t csz = 2 * c->esz;
+            if (rpb < 1 || rpb > 8 || (rpb & (rpb - 1)) || 2 * (size_t)rpb * c->W * csz > (size_t)kMaxSmem)
+                return fail(c, FUSE_EINVAL, "FFT rows per block must be 1, 2, 4 or 8 and fit shared memory");
+            c->fr_rpb = rpb;
+            c->fr_tpr = 256 / rpb;
+            c->fr_smem = 2 * (size_t)rpb * c->W * csz;
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
+        }
+        case FUSE_OPT_FFT_COLS: {
+            const int cw = (int)value;
+            const size_t csz = 2 * c->esz;
+            if (cw < 1 || cw > 32 || (cw & (cw - 1)) || (size_t)cw * (2 * c->H + 1) * csz > (size_t)kMaxSmem)
+                return fail(c, FUSE_EINVAL, "FFT columns per block must be a power of 2 <= 32 and fit shared memory");
+            c->fc_cw = cw;
+            c->fc_tpc = 256 / cw;
+            c->fc_smem = (size_t)cw * (2 * c->H + 1) * csz;
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
             return FUSE_OK;
@@ -1053,6 +1392,101 @@ fuse_status fuse_profile(fuse_ctx* c, int which, double* ms, long long* launches
     return FUSE_OK;
 }
 
+// Device time of `iters` iterations (direct launches) of the current configuration, in ms.
+static fuse_status time_iterations(fuse_ctx* c, int iters, double* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(c, cudaEventCreate(&a));
+    CK(c, cudaEventCreate(&b));
+    const bool g = c->use_graph, pr = c->profile;
+    c->use_graph = false;
+    c->profile = false;
+    fuse_status st = run_iterations(c, 1);                 // warm-up
+    if (st == FUSE_OK) {
+        cudaEventRecord(a, c->stream);
+        st = run_iterations(c, iters);
+        cudaEventRecord(b, c->stream);
+    }
+    c->use_graph = g;
+    c->profile = pr;
+    float t = 0.f;
+    if (st == FUSE_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess)
+        *ms = t;
+    else if (st == FUSE_OK)
+        st = fail(c, FUSE_ECUDA, "autotune timing failed");
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+fuse_status fuse_autotune(fuse_ctx* c, const void* Yl, const void* Yh, int iters) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (!Yl || !Yh || iters < 1) return fail(c, FUSE_EINVAL, "autotune needs inputs and iters >= 1");
+    if (!c->have_weights) return FUSE_ESTATE;
+    // inputs and a zero state (the timed iterations run on it; the next solve starts over)
+    st = solve_impl(c, Yl, Yh, 0, 0, nullptr, nullptr);
+    if (st != FUSE_OK) return st;
+    double best = 1e30, t = 0;
+    // 1. latent pass: ring shape and bands per block
+    if (c->lat_impl == 1) {
+        const int bt = c->lat_target, bs = c->lat_stages, bb = c->lat_bpb;
+        int best_t = bt, best_s = bs, best_b = bb;
+        const int threads[] = {128, 192, 256}, stages[] = {4, 6, 8}, bands[] = {1, 2};
+        for (int th : threads)
+            for (int sg : stages)
+                for (int bd : bands) {
+                    c->lat_target = th; c->lat_stages = sg; c->lat_bpb = bd;
+                    if (!latent_tma_shape(c)) continue;
+                    if ((st = time_iterations(c, iters, &t)) != FUSE_OK) return st;
+                    if (t < best) { best = t; best_t = th; best_s = sg; best_b = bd; }
+                }
+        c->lat_target = best_t; c->lat_stages = best_s; c->lat_bpb = best_b;
+        latent_tma_shape(c);
+    }
+    // 2. FFT passes: rows per block, then columns per block
+    {
+        best = 1e30;
+        const int old_r = c->fr_rpb;
+        int best_r = old_r;
+        for (int r : {1, 2, 4, 8}) {
+            if (fuse_set_option(c, FUSE_OPT_FFT_ROWS, r) != FUSE_OK) { fuse_reset_error(c); continue; }
+            if ((st = time_iterations(c, iters, &t)) != FUSE_OK) return st;
+            if (t < best) { best = t; best_r = r; }
+        }
+        fuse_set_option(c, FUSE_OPT_FFT_ROWS, best_r);
+        best = 1e30;
+        int best_c = c->fc_cw;
+        for (int cw : {2, 4, 8, 16}) {
+            if (fuse_set_option(c, FUSE_OPT_FFT_COLS, cw) != FUSE_OK) { fuse_reset_error(c); continue; }
+            if ((st = time_iterations(c, iters, &t)) != FUSE_OK) return st;
+            if (t < best) { best = t; best_c = cw; }
+        }
+        fuse_set_option(c, FUSE_OPT_FFT_COLS, best_c);
+    }
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    c->have_state = false;
+    c->have_x = false;
+    return FUSE_OK;
+}
+
+fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
+    if (!c || !value) return FUSE_EINVAL;
+    switch (option) {
+        case FUSE_OPT_PROFILE: *value = c->profile; return FUSE_OK;
+        case FUSE_OPT_GRAPH: *value = c->use_graph; return FUSE_OK;
+        case FUSE_OPT_LATENT_IMPL: *value = c->lat_impl; return FUSE_OK;
+        case FUSE_OPT_LATENT_THREADS: *value = c->lat_target; return FUSE_OK;
+        case FUSE_OPT_LATENT_STAGES: *value = c->lat_stages; return FUSE_OK;
+        case FUSE_OPT_WAIT_LIMIT: *value = c->wait_limit; return FUSE_OK;
+        case FUSE_OPT_HALF_WINDOW: *value = c->half; return FUSE_OK;
+        case FUSE_OPT_LATENT_BANDS: *value = c->lat_bpb; return FUSE_OK;
+        case FUSE_OPT_FFT_ROWS: *value = c->fr_rpb; return FUSE_OK;
+        case FUSE_OPT_FFT_COLS: *value = c->fc_cw; return FUSE_OK;
+        default: return FUSE_EINVAL;
+    }
+}
+
 fuse_status fuse_sync(fuse_ctx* c) {
     fuse_status st = guard(c);
     if (st != FUSE_OK) return st;
@@ -1084,6 +1518,212 @@ fuse_status fuse_selftest(fuse_ctx* c, int which) {
 }
 
 const char* fuse_last_error(const fuse_ctx* c) { return c ? c->err.c_str() : ""; }
+
+fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, void* stream) {
+    if (!out || !ctxs || n < 1) return FUSE_EINVAL;
+    *out = nullptr;
+    fuse_ctx* c0 = ctxs[0];
+    if (!c0) return FUSE_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        fuse_ctx* c = ctxs[i];
+        if (!c || c->sticky != FUSE_OK) return FUSE_EINVAL;
+        if (c->dtype != c0->dtype || c->wdtype != c0->wdtype || c->K != c0->K || c->S != c0->S ||
+            c->Ls != c0->Ls || c->bh != c0->bh || c->bw != c0->bw || c->half != c0->half || c->device != c0->device)
+            return FUSE_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return FUSE_EINVAL;
+    }
+    if (pixel_bucket(c0->Ls) == 0) return FUSE_EUNSUPPORTED;
+    fuse_batch* b = new (std::nothrow) fuse_batch();
+    if (!b) return FUSE_ENOMEM;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)stream;
+    b->device = c0->device;
+    b->dtype = c0->dtype; b->wdtype = c0->wdtype;
+    b->K = c0->K; b->S = c0->S; b->Ls = c0->Ls; b->bh = c0->bh; b->bw = c0->bw; b->half = c0->half;
+    b->fc_cw = c0->dtype == FUSE_F64 ? 4 : 8;
+    if (cudaSetDevice(b->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return FUSE_ECUDA;
+    }
+    for (fuse_ctx* c : b->ctx) c->stream = b->stream;
+    fuse_status st = batch_build(b);
+    if (st != FUSE_OK) {
+        batch_release(b);
+        cudaStreamDestroy(b->cap_stream);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return FUSE_OK;
+}
+
+fuse_status fuse_batch_solve(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters,
+                             void* const* X_out, void* const* Z_out) {
+    if (!b || !Yl || !Yh) return FUSE_EINVAL;
+    if (b->sticky != FUSE_OK) return FUSE_ESTATE;
+    if (iters < 0) return bfail(b, FUSE_EINVAL, "iters must be >= 0");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, FUSE_ECUDA, "cudaSetDevice");
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i) {
+        fuse_ctx* c = b->ctx[i];
+        if (!Yl[i] || !Yh[i]) return bfail(b, FUSE_EINVAL, "NULL input of a problem");
+        if (c->sticky != FUSE_OK || !c->have_weights) return bfail(b, FUSE_ESTATE, "a problem has no weights or holds an error");
+        c->stream = b->stream;
+        const bool f64 = c->dtype == FUSE_F64;
+        fuse_status st = f64 ? Impl<double>::band_mix(c, b->stream, Yl[i], c->D9a, c->Et, c->nl, c->Ll, c->Ls)
+                             : Impl<float>::band_mix(c, b->stream, Yl[i], c->D9a, c->Et, c->nl, c->Ll, c->Ls);
+        if (st == FUSE_OK)
+            st = f64 ? Impl<double>::band_mix(c, b->stream, Yh[i], c->D9b, c->Mh, c->n, c->Lh, c->Ls)
+                     : Impl<float>::band_mix(c, b->stream, Yh[i], c->D9b, c->Mh, c->n, c->Lh, c->Ls);
+        if (st == FUSE_OK) st = zero_state(c, b->stream);
+        if (st != FUSE_OK) return bfail(b, st, "problem " + std::to_string(i) + ": " + c->err);
+        c->have_state = true;
+    }
+    fuse_status st = batch_run(b, iters);
+    if (st != FUSE_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        fuse_ctx* c = b->ctx[i];
+        c->have_x = true;
+        const size_t img = c->n * c->Ls * c->esz;
+        if (X_out && X_out[i]) BCK(b, cudaMemcpyAsync(X_out[i], c->X, img, cudaMemcpyDeviceToDevice, b->stream));
+        if (Z_out && Z_out[i]) {
+            const bool f64 = c->dtype == FUSE_F64;
+            st = f64 ? Impl<double>::band_mix(c, b->stream, c->X, Z_out[i], c->Emix, c->n, c->Ls, c->Ll)
+                     : Impl<float>::band_mix(c, b->stream, c->X, Z_out[i], c->Emix, c->n, c->Ls, c->Ll);
+            if (st != FUSE_OK) return bfail(b, st, "problem " + std::to_string(i) + ": " + c->err);
+        }
+    }
+    return FUSE_OK;
+}
+
+fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value) {
+    if (!b) return FUSE_EINVAL;
+    if (b->sticky != FUSE_OK) return FUSE_ESTATE;
+    switch (option) {
+        case FUSE_OPT_PROFILE: b->profile = value != 0; return FUSE_OK;
+        case FUSE_OPT_GRAPH: b->use_graph = value != 0; return FUSE_OK;
+        case FUSE_OPT_LATENT_THREADS:
+        case FUSE_OPT_LATENT_STAGES:
+        case FUSE_OPT_LATENT_BANDS: {
+            const int old_t = b->lat_target, old_d = b->lat_stages, old_b = b->lat_bpb;
+            if (option == FUSE_OPT_LATENT_THREADS) b->lat_target = (int)value;
+            else if (option == FUSE_OPT_LATENT_STAGES) b->lat_stages = (int)value;
+            else b->lat_bpb = (int)value;
+            if (b->lat_target < 32 || b->lat_target > 256 || b->lat_stages < 2 || b->lat_stages > 32 ||
+                b->lat_bpb < 1 || b->lat_bpb > 64) {
+                b->lat_target = old_t; b->lat_stages = old_d; b->lat_bpb = old_b;
+                return bfail(b, FUSE_EINVAL, "latent launch option out of range");
+            }
+            cudaStreamSynchronize(b->stream);
+            batch_release(b);
+            fuse_status st = batch_build(b);
+            if (st != FUSE_OK) {
+                b->sticky = FUSE_OK;
+                b->lat_target = old_t; b->lat_stages = old_d; b->lat_bpb = old_b;
+                batch_release(b);
+                if (batch_build(b) != FUSE_OK) return bfail(b, FUSE_ECUDA, "cannot rebuild the batch tables");
+                return bfail(b, FUSE_EINVAL, "latent launch option does not fit the batch");
+            }
+            return FUSE_OK;
+        }
+        default: return bfail(b, FUSE_EINVAL, "unknown batch option");
+    }
+}
+
+fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters) {
+    if (!b || !Yl || !Yh || iters < 1) return FUSE_EINVAL;
+    if (b->sticky != FUSE_OK) return FUSE_ESTATE;
+    const bool g = b->use_graph, pr = b->profile;
+    b->use_graph = false;
+    b->profile = false;
+    fuse_status st = fuse_batch_solve(b, Yl, Yh, 0, nullptr, nullptr);   // inputs and zero state
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == FUSE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = bfail(b, FUSE_ECUDA, "cudaEventCreate");
+    double best = 1e30;
+    int bt = b->lat_target, bs = b->lat_stages, bb = b->lat_bpb;
+    const int threads[] = {128, 256}, stages[] = {4, 6, 8}, bands[] = {1, 2, 4};
+    for (int th : threads)
+        for (int sg : stages)
+            for (int bd : bands) {
+                if (st != FUSE_OK) break;
+                if (fuse_batch_set_option(b, FUSE_OPT_LATENT_THREADS, th) != FUSE_OK ||
+                    fuse_batch_set_option(b, FUSE_OPT_LATENT_STAGES, sg) != FUSE_OK ||
+                    fuse_batch_set_option(b, FUSE_OPT_LATENT_BANDS, bd) != FUSE_OK) {
+                    b->sticky = FUSE_OK;
+                    continue;
+                }
+                st = batch_run(b, 1);
+                cudaEventRecord(e0, b->stream);
+                if (st == FUSE_OK) st = batch_run(b, iters);
+                cudaEventRecord(e1, b->stream);
+                float t = 0.f;
+                if (st == FUSE_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && t < best) {
+                    best = t; bt = th; bs = sg; bb = bd;
+                }
+            }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->use_graph = g;
+    b->profile = pr;
+    if (st != FUSE_OK) return st;
+    fuse_batch_set_option(b, FUSE_OPT_LATENT_THREADS, bt);
+    fuse_batch_set_option(b, FUSE_OPT_LATENT_STAGES, bs);
+    return fuse_batch_set_option(b, FUSE_OPT_LATENT_BANDS, bb);
+}
+
+fuse_status fuse_batch_profile(fuse_batch* b, int which, double* ms, long long* launches, int reset) {
+    if (!b) return FUSE_EINVAL;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->ev_used; ++i) {
+        float t = 0.f;
+        BCK(b, cudaEventElapsedTime(&t, b->ev[i].a, b->ev[i].b));
+        b->latent_ms += t;
+    }
+    b->ev_used = 0;
+    long long extra = 0;
+    for (fuse_ctx* c : b->ctx) extra += c->launches_all;
+    if (which == FUSE_K_LATENT) {
+        if (ms) *ms = b->latent_ms;
+        if (launches) *launches = b->launches_latent;
+    } else if (which == FUSE_K_ALL) {
+        if (ms) *ms = 0.0;
+        if (launches) *launches = b->launches_all + extra;
+    } else {
+        return bfail(b, FUSE_EINVAL, "unknown kernel group");
+    }
+    if (reset) {
+        b->latent_ms = 0.0; b->launches_latent = 0; b->launches_all = 0;
+        for (fuse_ctx* c : b->ctx) c->launches_all = 0;
+    }
+    return FUSE_OK;
+}
+
+fuse_status fuse_batch_sync(fuse_batch* b) {
+    if (!b) return FUSE_EINVAL;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (fuse_ctx* c : b->ctx) {
+        fuse_status st = fuse_sync(c);
+        if (st != FUSE_OK) return bfail(b, st, c->err);
+    }
+    return FUSE_OK;
+}
+
+fuse_status fuse_batch_destroy(fuse_batch* b) {
+    if (!b) return FUSE_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return FUSE_OK;
+}
+
+const char* fuse_batch_last_error(const fuse_batch* b) { return b ? b->err.c_str() : ""; }
 
 fuse_status fuse_reset_error(fuse_ctx* c) {
     if (!c) return FUSE_EINVAL;

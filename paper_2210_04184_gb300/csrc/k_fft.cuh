@@ -82,17 +82,20 @@ __device__ __forceinline__ void fft_stage(const cplx<T>* in, cplx<T>* out, int N
 }
 
 // Runs all stages (block-wide barriers between stages); returns the buffer with the result.
+// Every thread of the block must call it; nt = 0 marks a thread with no line to transform.
 template <typename T>
 __device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, const FFTPlan& P, const cplx<T>* __restrict__ tw,
                              int sign, int t, int nt) {
     int Ns = 1;
     for (int s = 0; s < P.nst; ++s) {
         const int r = P.rad[s];
-        switch (r) {
-            case 4: fft_stage<T, 4>(a, b, P.N, Ns, sign, tw, t, nt); break;
-            case 2: fft_stage<T, 2>(a, b, P.N, Ns, sign, tw, t, nt); break;
-            case 3: fft_stage<T, 3>(a, b, P.N, Ns, sign, tw, t, nt); break;
-            default: fft_stage<T, 5>(a, b, P.N, Ns, sign, tw, t, nt); break;
+        if (nt > 0) {                    // threads without a line (nt = 0) only join the barriers
+            switch (r) {
+                case 4: fft_stage<T, 4>(a, b, P.N, Ns, sign, tw, t, nt); break;
+                case 2: fft_stage<T, 2>(a, b, P.N, Ns, sign, tw, t, nt); break;
+                case 3: fft_stage<T, 3>(a, b, P.N, Ns, sign, tw, t, nt); break;
+                default: fft_stage<T, 5>(a, b, P.N, Ns, sign, tw, t, nt); break;
+            }
         }
         __syncthreads();
         cplx<T>* tmp = a; a = b; b = tmp;
@@ -101,107 +104,148 @@ __device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, const FFTPlan& P, const cpl
     return a;
 }
 
-// Rows forward: z(y, .) = C_{2p}(y, .) + i C_{2p+1}(y, .), transformed along x.
-// Block: rpb rows x tpr threads; grid (ceil(H/rpb), ceil(L_s/2)).
 template <typename T>
-__global__ void __launch_bounds__(256)
-fft_rows_fwd_kernel(const T* __restrict__ C, cplx<T>* __restrict__ Y, int H, int W, int Ls,
-                    FFTPlan P, const cplx<T>* __restrict__ tw, int rpb) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+struct FFTArgs {
+    const T* C;          // rows forward: real input [L_s][H][W]
+    cplx<T>* Y;          // complex work array [ceil(L_s/2)][H][W]
+    T* X;                // rows inverse: real output [L_s][H][W]
+    const T* f;          // per-frequency factor [H][W], scaled by 1/(HW)
+    int H, W, Ls;
+    FFTPlan planW, planH;
+    const cplx<T>* twW;
+    const cplx<T>* twH;
+    int rpb;             // rows per block (row passes)
+    int CW;              // columns per block (column pass)
+};
+
+// Rows forward, block (bx, p): rows [bx rpb, bx rpb + rpb) of band pair p;
+// z(y, .) = C_{2p}(y, .) + i C_{2p+1}(y, .), transformed along x.
+template <typename T>
+__device__ __forceinline__ void fft_rows_fwd_body(const FFTArgs<T>& a, int bx, int p, unsigned char* smem_raw) {
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int H = a.H, W = a.W, Ls = a.Ls, rpb = a.rpb;
     const int tpr = blockDim.x / rpb;
     const int rr = threadIdx.x / tpr, t = threadIdx.x - rr * tpr;
-    const int y = blockIdx.x * rpb + rr;
-    const int p = blockIdx.y;
+    const int y = bx * rpb + rr;
     const size_t n = (size_t)H * W;
     cplx<T>* b0 = sm + (size_t)rr * 2 * W;
     cplx<T>* b1 = b0 + W;
-    const bool ok = y < H;
-    const T* re = C + (size_t)(2 * p) * n + (size_t)y * W;
+    const bool ok = y < H && rr < rpb;
+    const T* re = a.C + (size_t)(2 * p) * n + (size_t)y * W;
     const bool has_im = 2 * p + 1 < Ls;
-    const T* im = C + (size_t)(2 * p + 1) * n + (size_t)y * W;
-    for (int x = t; x < W; x += tpr) {
-        cplx<T> z = {T(0), T(0)};
-        if (ok) { z.x = re[x]; if (has_im) z.y = im[x]; }
-        b0[x] = z;
-    }
+    const T* im = a.C + (size_t)(2 * p + 1) * n + (size_t)y * W;
+    if (rr < rpb)
+        for (int x = t; x < W; x += tpr) {
+            cplx<T> z = {T(0), T(0)};
+            if (ok) { z.x = re[x]; if (has_im) z.y = im[x]; }
+            b0[x] = z;
+        }
     __syncthreads();
-    cplx<T>* res = fft_smem(b0, b1, P, tw, -1, t, tpr);
+    cplx<T>* res = fft_smem(b0, b1, a.planW, a.twW, -1, t, rr < rpb ? tpr : 0);
     if (ok)
-        for (int x = t; x < W; x += tpr) Y[(size_t)p * n + (size_t)y * W + x] = res[x];
+        for (int x = t; x < W; x += tpr) a.Y[(size_t)p * n + (size_t)y * W + x] = res[x];
 }
 
-// Columns: forward along y, multiply by f(u, v), inverse along y, for CW columns per block.
-// Block: CW x tpc threads (warp-major per column); grid (ceil(W/CW), ceil(L_s/2)).
+// Columns, block (bx, p): forward along y, multiply by f(u, v), inverse along y, for the CW
+// columns starting at bx CW of band pair p (warp-major per column).
 template <typename T>
-__global__ void __launch_bounds__(256)
-fft_cols_kernel(cplx<T>* __restrict__ Y, const T* __restrict__ f, int H, int W, FFTPlan P,
-                const cplx<T>* __restrict__ tw, int CW) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fft_cols_body(const FFTArgs<T>& a, int bx, int p, unsigned char* smem_raw) {
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int H = a.H, W = a.W, CW = a.CW;
     const int tpc = blockDim.x / CW;
     const int cw = threadIdx.x / tpc, t = threadIdx.x - cw * tpc;
-    const int x0 = blockIdx.x * CW;
-    const int p = blockIdx.y;
+    const int x0 = bx * CW;
     const size_t n = (size_t)H * W;
     const int pitch = 2 * H + 1;
-    cplx<T>* Yp = Y + (size_t)p * n;
-    for (int idx = threadIdx.x; idx < H * CW; idx += blockDim.x) {
-        const int row = idx / CW, cc = idx - row * CW;
-        const int x = x0 + cc;
-        sm[(size_t)cc * pitch + row] = x < W ? Yp[(size_t)row * W + x] : cplx<T>{T(0), T(0)};
-    }
+    cplx<T>* Yp = a.Y + (size_t)p * n;
+    const int nld = blockDim.x - blockDim.x % CW;     // threads that take part in loads/stores
+    if ((int)threadIdx.x < nld)
+        for (int idx = threadIdx.x; idx < H * CW; idx += nld) {
+            const int row = idx / CW, cc = idx - row * CW;
+            const int x = x0 + cc;
+            sm[(size_t)cc * pitch + row] = x < W ? Yp[(size_t)row * W + x] : cplx<T>{T(0), T(0)};
+        }
     __syncthreads();
-    cplx<T>* b0 = sm + (size_t)cw * pitch;
+    const bool mine = cw < CW;
+    cplx<T>* b0 = sm + (size_t)(mine ? cw : 0) * pitch;
     cplx<T>* b1 = b0 + H;
-    cplx<T>* res = fft_smem(b0, b1, P, tw, -1, t, tpc);
+    cplx<T>* res = fft_smem(b0, b1, a.planH, a.twH, -1, t, mine ? tpc : 0);
     const int x = x0 + cw;
-    if (x < W) {
+    if (mine && x < W) {
         for (int u = t; u < H; u += tpc) {
-            const T g = f[(size_t)u * W + x];
+            const T g = a.f[(size_t)u * W + x];
             res[u].x *= g;
             res[u].y *= g;
         }
     }
     __syncthreads();
     cplx<T>* other = res == b0 ? b1 : b0;
-    res = fft_smem(res, other, P, tw, +1, t, tpc);
+    res = fft_smem(res, other, a.planH, a.twH, +1, t, mine ? tpc : 0);
     // the result buffer of column cc sits at the same parity for every column
     const int off = (int)(res - b0);
-    for (int idx = threadIdx.x; idx < H * CW; idx += blockDim.x) {
-        const int row = idx / CW, cc = idx - row * CW;
-        const int xx = x0 + cc;
-        if (xx < W) Yp[(size_t)row * W + xx] = sm[(size_t)cc * pitch + off + row];
-    }
+    if ((int)threadIdx.x < nld)
+        for (int idx = threadIdx.x; idx < H * CW; idx += nld) {
+            const int row = idx / CW, cc = idx - row * CW;
+            const int xx = x0 + cc;
+            if (xx < W) Yp[(size_t)row * W + xx] = sm[(size_t)cc * pitch + off + row];
+        }
 }
 
-// Rows inverse: X_{2p} = Re, X_{2p+1} = Im of the inverse transform along x (f carries 1/(HW)).
+// Rows inverse, block (bx, p): X_{2p} = Re, X_{2p+1} = Im of the inverse transform along x
+// (f carries 1/(HW)).
 template <typename T>
-__global__ void __launch_bounds__(256)
-fft_rows_inv_kernel(const cplx<T>* __restrict__ Y, T* __restrict__ X, int H, int W, int Ls,
-                    FFTPlan P, const cplx<T>* __restrict__ tw, int rpb) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fft_rows_inv_body(const FFTArgs<T>& a, int bx, int p, unsigned char* smem_raw) {
     cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+    const int H = a.H, W = a.W, Ls = a.Ls, rpb = a.rpb;
     const int tpr = blockDim.x / rpb;
     const int rr = threadIdx.x / tpr, t = threadIdx.x - rr * tpr;
-    const int y = blockIdx.x * rpb + rr;
-    const int p = blockIdx.y;
+    const int y = bx * rpb + rr;
     const size_t n = (size_t)H * W;
     cplx<T>* b0 = sm + (size_t)rr * 2 * W;
     cplx<T>* b1 = b0 + W;
-    const bool ok = y < H;
-    for (int x = t; x < W; x += tpr)
-        b0[x] = ok ? Y[(size_t)p * n + (size_t)y * W + x] : cplx<T>{T(0), T(0)};
+    const bool ok = y < H && rr < rpb;
+    if (rr < rpb)
+        for (int x = t; x < W; x += tpr)
+            b0[x] = ok ? a.Y[(size_t)p * n + (size_t)y * W + x] : cplx<T>{T(0), T(0)};
     __syncthreads();
-    cplx<T>* res = fft_smem(b0, b1, P, tw, +1, t, tpr);
+    cplx<T>* res = fft_smem(b0, b1, a.planW, a.twW, +1, t, rr < rpb ? tpr : 0);
     if (!ok) return;
-    T* re = X + (size_t)(2 * p) * n + (size_t)y * W;
+    T* re = a.X + (size_t)(2 * p) * n + (size_t)y * W;
     const bool has_im = 2 * p + 1 < Ls;
-    T* im = X + (size_t)(2 * p + 1) * n + (size_t)y * W;
+    T* im = a.X + (size_t)(2 * p + 1) * n + (size_t)y * W;
     for (int x = t; x < W; x += tpr) {
         re[x] = res[x].x;
         if (has_im) im[x] = res[x].y;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fft_rows_fwd_kernel(FFTArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_rows_fwd_body<T>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) fft_cols_kernel(FFTArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_cols_body<T>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) fft_rows_inv_kernel(FFTArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fft_rows_inv_body<T>(a, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Batched forms (one launch over many problems, see Segment).
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256)
+fft_batch_kernel(const FFTArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const FFTArgs<T> a = args[prob];
+    if constexpr (PASS == 0) fft_rows_fwd_body<T>(a, bx, by, smem_raw);
+    else if constexpr (PASS == 1) fft_cols_body<T>(a, bx, by, smem_raw);
+    else fft_rows_inv_body<T>(a, bx, by, smem_raw);
 }
 
 }  // namespace fuse

@@ -132,7 +132,8 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
 }  // namespace fuse
 
 // ---------------------------------------------------------------------------------------
-// Pipelined form of the same pass: the latent state is streamed through a shared-memory ring
+// Pipelined form of the same pass (each consumer thread owns VEC pixels; VEC * sizeof(T) is
+// 16 or 32 bytes): the latent state is streamed through a shared-memory ring
 // by bulk asynchronous copies (cp.async.bulk, 1D TMA), issued by one producer warp, so the
 // number of bytes in flight no longer depends on registers.  One chunk = the block's rows of
 // one (tau, k) plane of Sig' (Ty*W contiguous elements).  Consumers wait on the chunk's
@@ -144,12 +145,40 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
 
 namespace fuse {
 
+template <typename T, typename WT>
+struct LatentArgs {
+    const T* X;
+    const WT* omega;
+    T* Sig;
+    T* planes;
+    int H, W, Ls, S, Ty, ncons, D;
+    T coef;
+    int* err;
+    unsigned limit;
+    int half;
+    int bpb;            // bands per block: the ring keeps streaming across them
+};
+
+__device__ __forceinline__ void consumer_barrier(int ncons) {
+    asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
+}
+
+// Block (bx, g, row) of one problem: rows [bx*Ty, bx*Ty + Ty), bands [g*bpb, g*bpb + bpb),
+// tau1 row `row`.  The bands are processed one after the other while the producer keeps the
+// ring full; between bands the consumers meet at a named barrier (the producer never waits on
+// it) to form and store that band's adjoint partial sums.
 template <typename T, typename WT, int K, int VEC>
-__global__ void __launch_bounds__(288)
-latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restrict__ Sig,
-                  T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, int ncons, int D, T coef,
-                  int* __restrict__ err, unsigned limit, int half) {
-    extern __shared__ __align__(128) unsigned char smem_tma[];
+__device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, int bx, int g, int row,
+                                                unsigned char* smem_tma) {
+    const T* __restrict__ X = args.X;
+    const WT* __restrict__ omega = args.omega;
+    T* __restrict__ Sig = args.Sig;
+    T* __restrict__ planes = args.planes;
+    const int H = args.H, W = args.W, Ls = args.Ls, S = args.S, Ty = args.Ty, ncons = args.ncons, D = args.D;
+    const T coef = args.coef;
+    int* __restrict__ err = args.err;
+    const unsigned limit = args.limit;
+    const int half = args.half;
     constexpr int PS = 2 * K + 1;
     constexpr int NP = PS * PS;
     const int side = 2 * S + 1;
@@ -162,25 +191,17 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
 
     const int tid = threadIdx.x;
     const int tpr = W / VEC;
-    const int y0 = blockIdx.x * Ty;
+    const int y0 = bx * Ty;
     const int rows = min(Ty, H - y0);
     const TauMap tm{S, half};
-    const int t1 = tm.t1_of_block(blockIdx.z);
-    const int c = blockIdx.y;
+    const int t1 = tm.t1_of_block(row);
     const size_t n = (size_t)H * W;
     const int nt2 = tm.nt2(t1);
-    const int nq = nt2 * NP;
+    const int c0 = g * args.bpb;
+    const int nb = min(args.bpb, Ls - c0);
+    const int per_band = nt2 * NP;
+    const int nq = nb * per_band;
     const unsigned bytes = (unsigned)(rows * W * (int)sizeof(T));
-
-    // consumer geometry (threads >= tpr*Ty own no pixels)
-    const int r = tid / tpr;
-    const int x0 = (tid - r * tpr) * VEC;
-    const int y = y0 + r;
-    const bool owner = tid < tpr * Ty;
-    const bool active = owner && r < rows;
-    T A[VEC];
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) A[j] = T(0);
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) {
@@ -204,9 +225,11 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
                     s_abort = 1;
                     break;
                 }
-                const int j = q / NP, kidx = q - j * NP;
+                const int item = q / per_band, rem = q - item * per_band;
+                const int j = rem / NP, kidx = rem - j * NP;
                 const int t2 = tm.t2_of(t1, j);
-                const T* src = Sig + ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + c) * n + (size_t)y0 * W;
+                const T* src = Sig + ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + (c0 + item)) * n +
+                               (size_t)y0 * W;
                 mbar_arrive_expect_tx(&full[slot], bytes);
                 tma_load_1d(ring + (size_t)slot * tile, src, bytes, &full[slot], pol);
                 issued = q + 1;
@@ -217,58 +240,75 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
             for (int q = issued > D ? issued - D : 0; q < issued; ++q)
                 if (!mbar_wait(&full[q % D], (unsigned)((q / D) & 1), dlim, err, 1)) break;
         }
-    } else {
-        // ---------------- consumers ----------------
-        const int lane = tid & 31;
-        const T* Xc = X + (size_t)c * n;
-        T Xm[VEC];
+        return;
+    }
+
+    // ---------------- consumers (threads >= tpr*Ty own no pixels) ----------------
+    const int lane = tid & 31;
+    const int r = tid / tpr;
+    const int x0 = (tid - r * tpr) * VEC;
+    const int y = y0 + r;
+    const bool owner = tid < tpr * Ty;
+    const bool active = owner && r < rows;
+    // circular indices that do not depend on the offset or the band, computed once
+    int wcol[VEC + 2 * K];                     // weight columns x0 - K + j
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) Xm[j] = active ? Xc[(size_t)y * W + x0 + j] : T(0);
-        int slot = 0;
-        unsigned par = 0;
+    for (int j = 0; j < VEC + 2 * K; ++j) wcol[j] = wrap1(x0 - K + j, W);
+    size_t wrow[PS];                           // weight rows y + k1
+#pragma unroll
+    for (int k1 = -K; k1 <= K; ++k1) wrow[k1 + K] = (size_t)wrap1(y + k1, H) * W;
+    const size_t xsrow = (size_t)wrap1(y - t1, H) * W;   // row of X(m - tau)
+    const size_t pix = (size_t)y * W + x0;
+    const size_t kstride = (size_t)Ls * n;
+    int slot = 0;
+    unsigned par = 0;
+    for (int item = 0; item < nb; ++item) {
+        const int c = c0 + item;
+        const T* Xc = X + (size_t)c * n;
+        T Xm[VEC], A[VEC];
+        if (active) vload<T, VEC>(Xc + pix, Xm);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (!active) Xm[j] = T(0);
+            A[j] = T(0);
+        }
         for (int jt = 0; jt < nt2; ++jt) {
             const int t2 = tm.t2_of(t1, jt);
-            T Hacc[VEC];
+            T Hacc[VEC], delta[VEC];
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
-            {
-                T delta[VEC];
-                const int ys = wrap1(y - t1, H);
+            for (int j = 0; j < VEC; ++j) {
+                Hacc[j] = T(0);
+                delta[j] = active ? Xm[j] - Xc[xsrow + wrap1(x0 + j - t2, W)] : T(0);
+            }
+            const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
+            T* gp = Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
 #pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                    delta[j] = active ? Xm[j] - Xc[(size_t)ys * W + wrap1(x0 + j - t2, W)] : T(0);
-                const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
-                T* gp = Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0;
-                const size_t kstride = (size_t)Ls * n;
+            for (int k1 = 0; k1 < PS; ++k1) {
+                T mu[VEC + 2 * K];
+                const WT* orow = om + wrow[k1];
 #pragma unroll
-                for (int k1 = -K; k1 <= K; ++k1) {
-                    T mu[VEC + 2 * K];
-                    const int yw = wrap1(y + k1, H);
+                for (int j = 0; j < VEC + 2 * K; ++j) mu[j] = active ? coef * (T)wload(orow + wcol[j]) : T(0);
 #pragma unroll
-                    for (int j = 0; j < VEC + 2 * K; ++j)
-                        mu[j] = active ? coef * (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W)) : T(0);
+                for (int k2 = 0; k2 < PS; ++k2) {
+                    const unsigned lim = s_abort ? 64u : limit;
+                    if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                    if (active) {
+                        T sv[VEC];
+                        vload<T, VEC>(ring + (size_t)slot * tile + (size_t)r * W + x0, sv);
 #pragma unroll
-                    for (int k2 = 0; k2 < PS; ++k2) {
-                        const unsigned lim = s_abort ? 64u : limit;
-                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
-                        if (active) {
-                            vecT<T, VEC> s = *reinterpret_cast<const vecT<T, VEC>*>(
-                                ring + (size_t)slot * tile + (size_t)r * W + x0);
-#pragma unroll
-                            for (int j = 0; j < VEC; ++j) {
-                                const T u = s.v[j] - delta[j];
-                                const T m = mu[j + k2];
-                                const T s2 = tmin(tmax(u, -m), m);
-                                Hacc[j] += T(2) * s2 - u;
-                                s.v[j] = s2;
-                            }
-                            st_stream(reinterpret_cast<vecT<T, VEC>*>(gp), s);
+                        for (int j = 0; j < VEC; ++j) {
+                            const T u = sv[j] - delta[j];
+                            const T m = mu[j + k2];
+                            const T s2 = tmin(tmax(u, -m), m);
+                            Hacc[j] += T(2) * s2 - u;
+                            sv[j] = s2;
                         }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&empty[slot]);
-                        gp += kstride;
-                        if (++slot == D) { slot = 0; par ^= 1u; }
+                        vstore_stream<T, VEC>(gp, sv);
                     }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[slot]);
+                    gp += kstride;
+                    if (++slot == D) { slot = 0; par ^= 1u; }
                 }
             }
             if (owner) {
@@ -279,23 +319,41 @@ latent_tma_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __re
                 }
             }
         }
+        consumer_barrier(ncons);                 // every H_tau of this band is in Hs
+        if (active) {
+            T V[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) V[j] = T(0);
+            for (int jt = 0; jt < nt2; ++jt) {
+                const int t2 = tm.t2_of(t1, jt);
+                const T* hrow = Hs + ((size_t)(t2 + S) * Ty + r) * W;
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) V[j] += hrow[wrap1(x0 + j + t2, W)];
+            }
+            vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
+            vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
+        }
+        if (item + 1 < nb) consumer_barrier(ncons);   // Hs is read before the next band rewrites it
     }
-    __syncthreads();
-    if (!active) return;
-    T V[VEC];
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) V[j] = T(0);
-    for (int jt = 0; jt < nt2; ++jt) {
-        const int t2 = tm.t2_of(t1, jt);
-        const T* row = Hs + ((size_t)(t2 + S) * Ty + r) * W;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) V[j] += row[wrap1(x0 + j + t2, W)];
-    }
-    vecT<T, VEC> va, vv;
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) { va.v[j] = A[j]; vv.v[j] = V[j]; }
-    *reinterpret_cast<vecT<T, VEC>*>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + (size_t)y * W + x0) = va;
-    *reinterpret_cast<vecT<T, VEC>*>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + (size_t)y * W + x0) = vv;
+}
+
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(288, 2) latent_tma_kernel(LatentArgs<T, WT> args) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    latent_tma_body<T, WT, K, VEC>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
+}
+
+// One launch over many problems (batched uneven sizes): blocks are mapped to (problem, block)
+// by the segment table; every problem's launch shape fits the common block size and shared
+// memory size of the launch.
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(288, 2)
+latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const LatentArgs<T, WT> a = args[prob];
+    latent_tma_body<T, WT, K, VEC>(a, bx, by, bz, smem_tma);
 }
 
 }  // namespace fuse

@@ -14,19 +14,41 @@ namespace fuse {
 // One thread per pixel; the pixel's band vectors live in registers (MAXLS >= L_s, loops unrolled
 // with guards so the arrays are indexed statically), every input band is loaded once, and the
 // L_s x L_s matrices sit in shared memory and are read uniformly by the warp.
+template <typename T>
+struct PixelArgs {
+    const T* X;
+    const T* BX;
+    T* Lam1;
+    T* U1;
+    T* Lam2;
+    T* U2;
+    const T* D9a;
+    const T* D9b;
+    const T* M1;
+    const T* F;
+    int H, W, Ls, d;
+    T rho;
+};
+
 template <typename T, int MAXLS>
-__global__ void __launch_bounds__(128)
-pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ Lam1, T* __restrict__ U1,
-             T* __restrict__ Lam2, T* __restrict__ U2, const T* __restrict__ D9a, const T* __restrict__ D9b,
-             const T* __restrict__ M1, const T* __restrict__ F, int H, int W, int Ls, int d, T rho) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, unsigned char* smem_raw) {
+    const T* __restrict__ X = args.X;
+    const T* __restrict__ BX = args.BX;
+    T* __restrict__ Lam1 = args.Lam1;
+    T* __restrict__ U1 = args.U1;
+    T* __restrict__ Lam2 = args.Lam2;
+    T* __restrict__ U2 = args.U2;
+    const T* __restrict__ D9a = args.D9a;
+    const T* __restrict__ D9b = args.D9b;
+    const int H = args.H, W = args.W, Ls = args.Ls, d = args.d;
+    const T rho = args.rho;
     T* sF = reinterpret_cast<T*>(smem_raw);              // [Ls][Ls]
     T* sM = sF + (size_t)Ls * Ls;                        // [Ls][Ls]
     const int tid = threadIdx.x, nb = blockDim.x;
-    for (int i = tid; i < Ls * Ls; i += nb) { sF[i] = F[i]; sM[i] = M1[i]; }
+    for (int i = tid; i < Ls * Ls; i += nb) { sF[i] = args.F[i]; sM[i] = args.M1[i]; }
     __syncthreads();
     const size_t n = (size_t)H * W;
-    const size_t p = (size_t)blockIdx.x * nb + tid;
+    const size_t p = (size_t)bx * nb + tid;
     if (p >= n) return;
     T a[MAXLS], w[MAXLS];
     // P2 and Lambda2: a = X - Lambda2 + lambda1/rho Y_h R^T E^T, w = X - Lambda2
@@ -83,12 +105,37 @@ pixel_kernel(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ 
     }
 }
 
+template <typename T, int MAXLS>
+__global__ void __launch_bounds__(128) pixel_kernel(PixelArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pixel_body<T, MAXLS>(a, blockIdx.x, smem_raw);
+}
+
+template <typename T, int MAXLS>
+__global__ void __launch_bounds__(128)
+pixel_batch_kernel(const PixelArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const PixelArgs<T> a = args[prob];
+    pixel_body<T, MAXLS>(a, bx, smem_raw);
+}
+
 // Same closed forms for L_s > 32: the band vector is staged in shared memory [L_s][blockDim].
 template <typename T>
-__global__ void __launch_bounds__(128)
-pixel_kernel_wide(const T* __restrict__ X, const T* __restrict__ BX, T* __restrict__ Lam1, T* __restrict__ U1,
-                  T* __restrict__ Lam2, T* __restrict__ U2, const T* __restrict__ D9a, const T* __restrict__ D9b,
-                  const T* __restrict__ M1, const T* __restrict__ F, int H, int W, int Ls, int d, T rho) {
+__global__ void __launch_bounds__(128) pixel_kernel_wide(PixelArgs<T> args) {
+    const T* __restrict__ X = args.X;
+    const T* __restrict__ BX = args.BX;
+    T* __restrict__ Lam1 = args.Lam1;
+    T* __restrict__ U1 = args.U1;
+    T* __restrict__ Lam2 = args.Lam2;
+    T* __restrict__ U2 = args.U2;
+    const T* __restrict__ D9a = args.D9a;
+    const T* __restrict__ D9b = args.D9b;
+    const T* __restrict__ M1 = args.M1;
+    const T* __restrict__ F = args.F;
+    const int H = args.H, W = args.W, Ls = args.Ls, d = args.d;
+    const T rho = args.rho;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* a = reinterpret_cast<T*>(smem_raw);     // [Ls][blockDim]
     const int tid = threadIdx.x, nb = blockDim.x;

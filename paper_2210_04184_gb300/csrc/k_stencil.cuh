@@ -15,32 +15,42 @@ namespace fuse {
 
 constexpr int ST_TX = 32, ST_TY = 32, ST_BY = 8;
 
+template <typename T>
+struct StencilArgs {
+    const T* in;
+    T* out;
+    const T* taps;
+    int bw, H, W;
+    const T* U2;        // MODE 1 only
+    const T* planes;    // MODE 1 only
+    int S, half;
+};
+
 // Each thread computes QY = 4 vertically adjacent outputs; for every tap column v it holds the
 // BH + QY - 1 tile values of its column in registers, so each shared-memory read feeds up to
 // QY multiply-adds.  BH is a compile-time odd size (1..15); bw is a runtime odd size.
+// Block (bx, by, c): the 32 x 32 tile at columns 32 bx, rows 32 by of band c.
 template <typename T, int MODE, int BH>
-__global__ void __launch_bounds__(256)
-stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ taps, int bw,
-               int H, int W, const T* __restrict__ U2, const T* __restrict__ planes, int S, int half) {
+__device__ __forceinline__ void stencil_body(const StencilArgs<T>& a, int bx, int by, int c,
+                                             unsigned char* smem_raw) {
     constexpr int QY = ST_TY / ST_BY;                 // 4 outputs per thread
     constexpr int NR = BH + QY - 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int bw = a.bw, H = a.H, W = a.W, S = a.S, half = a.half;
     const int th = ST_TY + BH - 1, tw = ST_TX + bw - 1;
     T* tile = reinterpret_cast<T*>(smem_raw);         // [th][tw]
     T* tp = tile + (size_t)th * tw;                   // [BH][bw]
     constexpr int rh = BH / 2;
     const int rw = bw / 2;
-    const int c = blockIdx.z;
-    const int x0 = blockIdx.x * ST_TX, y0 = blockIdx.y * ST_TY;
+    const int x0 = bx * ST_TX, y0 = by * ST_TY;
     const size_t n = (size_t)H * W;
-    const T* inc = in + (size_t)c * n;
+    const T* __restrict__ inc = a.in + (size_t)c * n;
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
     const int nthr = ST_TX * ST_BY;
     for (int idx = tid; idx < th * tw; idx += nthr) {
         const int rr = idx / tw, cc = idx - rr * tw;
         tile[idx] = inc[(size_t)wrapn(y0 - rh + rr, H) * W + wrapn(x0 - rw + cc, W)];
     }
-    for (int idx = tid; idx < BH * bw; idx += nthr) tp[idx] = taps[idx];
+    for (int idx = tid; idx < BH * bw; idx += nthr) tp[idx] = a.taps[idx];
     __syncthreads();
     const int x = x0 + threadIdx.x;
     if (x >= W) return;
@@ -67,16 +77,32 @@ stencil_kernel(const T* __restrict__ in, T* __restrict__ out, const T* __restric
         T val = acc[q];
         const size_t pix = (size_t)y * W + x;
         if constexpr (MODE == 1) {
-            const T* pc = planes + (size_t)c * 2 * side * n;
+            const T* pc = a.planes + (size_t)c * 2 * side * n;
             T rs = T(0);
             for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
                 rs += pc[(size_t)(t1 + S) * n + pix];
                 rs -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
             }
-            val += U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
+            val += a.U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
         }
-        out[(size_t)c * n + pix] = val;
+        a.out[(size_t)c * n + pix] = val;
     }
+}
+
+template <typename T, int MODE, int BH>
+__global__ void __launch_bounds__(256) stencil_kernel(StencilArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stencil_body<T, MODE, BH>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+template <typename T, int MODE, int BH>
+__global__ void __launch_bounds__(256)
+stencil_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const StencilArgs<T> a = args[prob];
+    stencil_body<T, MODE, BH>(a, bx, by, bz, smem_raw);
 }
 
 }  // namespace fuse

@@ -22,7 +22,7 @@ FUSE_ETIMEOUT, FUSE_ENONFINITE, FUSE_ESTATE, FUSE_EUNSUPPORTED = 4, 5, 6, 7
 FUSE_F32, FUSE_F64, FUSE_BF16 = 0, 1, 2
 FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
 FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
-FUSE_OPT_HALF_WINDOW = 7
+FUSE_OPT_HALF_WINDOW, FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS = 7, 8, 9, 10
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -76,8 +76,19 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
         "fuse_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
         "fuse_sync": (_ST, [_VP]),
+        "fuse_get_option": (_ST, [_VP, _I, ctypes.POINTER(ctypes.c_longlong)]),
+        "fuse_autotune": (_ST, [_VP, _VP, _VP, _I]),
+        "fuse_batch_autotune": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I]),
         "fuse_selftest": (_ST, [_VP, _I]),
         "fuse_phi_static": (_ST, [_VP, _VP, _I, _I, _I, _I, _I, _I, _I, _VP, _VP]),
+        "fuse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
+        "fuse_batch_solve": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP),
+                                   ctypes.POINTER(_VP)]),
+        "fuse_batch_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
+        "fuse_batch_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
+        "fuse_batch_sync": (_ST, [_VP]),
+        "fuse_batch_destroy": (_ST, [_VP]),
+        "fuse_batch_last_error": (ctypes.c_char_p, [_VP]),
         "fuse_last_error": (ctypes.c_char_p, [_VP]),
         "fuse_reset_error": (_ST, [_VP]),
         "fuse_status_string": (ctypes.c_char_p, [_I]),
@@ -196,6 +207,20 @@ def fuse_profile(ctx, which: int, reset: bool = False) -> tuple[float, int]:
     return ms.value, n.value
 
 
+def fuse_get_option(ctx, option: int) -> int:
+    v = ctypes.c_longlong(0)
+    _check(load().fuse_get_option(ctx, option, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def fuse_autotune(ctx, Yl_dev: int, Yh_dev: int, iters: int = 2):
+    _check(load().fuse_autotune(ctx, _VP(Yl_dev), _VP(Yh_dev), iters), ctx)
+
+
+def fuse_batch_autotune(b, Yl_devs, Yh_devs, iters: int = 2):
+    _bcheck(load().fuse_batch_autotune(b, _ptrs(Yl_devs), _ptrs(Yh_devs), iters), b)
+
+
 def fuse_sync(ctx):
     _check(load().fuse_sync(ctx), ctx)
 
@@ -208,6 +233,60 @@ def fuse_phi_static(X_dev: int, omega_dev: int, H: int, W: int, L_s: int, K: int
                     dtype: int, wdtype: int, phi_dev: int, stream: int = 0):
     _check(load().fuse_phi_static(_VP(X_dev), _VP(omega_dev), H, W, L_s, K, S, dtype, wdtype,
                                   _VP(phi_dev), _VP(stream or None)))
+
+
+def _bcheck(st: int, b=None):
+    if st != FUSE_OK:
+        msg = ""
+        if b is not None and _lib is not None:
+            raw = _lib.fuse_batch_last_error(b)
+            msg = raw.decode() if raw else ""
+        raise FuseError(st, msg)
+
+
+def _ptrs(vals):
+    arr = (_VP * len(vals))()
+    for i, v in enumerate(vals):
+        arr[i] = v or None
+    return arr
+
+
+def fuse_batch_create(ctxs, stream: int = 0):
+    out = _VP()
+    arr = (_VP * len(ctxs))(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    _bcheck(load().fuse_batch_create(ctypes.byref(out), arr, len(ctxs), _VP(stream or None)))
+    return out
+
+
+def fuse_batch_solve(b, Yl_devs, Yh_devs, iters: int, X_outs=None, Z_outs=None):
+    n = len(Yl_devs)
+    xo = _ptrs(X_outs) if X_outs is not None else None
+    zo = _ptrs(Z_outs) if Z_outs is not None else None
+    _bcheck(load().fuse_batch_solve(b, _ptrs(Yl_devs), _ptrs(Yh_devs), iters, xo, zo), b)
+
+
+def fuse_batch_set_option(b, option: int, value: int):
+    _bcheck(load().fuse_batch_set_option(b, option, value), b)
+
+
+def fuse_batch_profile(b, which: int, reset: bool = False):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _bcheck(load().fuse_batch_profile(b, which, ctypes.byref(ms), ctypes.byref(n), int(reset)), b)
+    return ms.value, n.value
+
+
+def fuse_batch_sync(b):
+    _bcheck(load().fuse_batch_sync(b), b)
+
+
+def fuse_batch_destroy(b):
+    _bcheck(load().fuse_batch_destroy(b))
+
+
+def fuse_batch_last_error(b) -> str:
+    raw = load().fuse_batch_last_error(b)
+    return raw.decode() if raw else ""
 
 
 def fuse_last_error(ctx) -> str:
@@ -321,10 +400,66 @@ class Fusion:
     def sync(self):
         fuse_sync(self.ctx)
 
+    def autotune(self, Yl, Yh, iters=2):
+        d = self.ratio
+        yl = self._t(Yl, (self.L_l, self.H // d, self.W // d))
+        yh = self._t(Yh, (self.L_h, self.H, self.W))
+        self._sync_stream()
+        fuse_autotune(self.ctx, yl.data_ptr(), yh.data_ptr(), iters)
+        return {k: fuse_get_option(self.ctx, v) for k, v in
+                (("latent_threads", FUSE_OPT_LATENT_THREADS), ("latent_stages", FUSE_OPT_LATENT_STAGES),
+                 ("latent_bands", FUSE_OPT_LATENT_BANDS), ("fft_rows", FUSE_OPT_FFT_ROWS),
+                 ("fft_cols", FUSE_OPT_FFT_COLS))}
+
     def close(self):
         if getattr(self, "ctx", None):
             fuse_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FusionBatch:
+    """Several Fusion contexts solved together (one launch per ADMM phase over all problems)."""
+
+    def __init__(self, fusions, stream=None):
+        import torch
+        self.torch = torch
+        self.fusions = list(fusions)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        self.b = fuse_batch_create([f.ctx for f in self.fusions], s)
+
+    def solve(self, Yls, Yhs, iters, want_X=True, want_Z=False):
+        t = self.torch
+        yl = [f._t(y, (f.L_l, f.H // f.ratio, f.W // f.ratio)) for f, y in zip(self.fusions, Yls)]
+        yh = [f._t(y, (f.L_h, f.H, f.W)) for f, y in zip(self.fusions, Yhs)]
+        Xs = [t.empty((f.L_s, f.H, f.W), dtype=f.tdtype, device="cuda") for f in self.fusions] if want_X else None
+        Zs = [t.empty((f.L_l, f.H, f.W), dtype=f.tdtype, device="cuda") for f in self.fusions] if want_Z else None
+        fuse_batch_solve(self.b, [y.data_ptr() for y in yl], [y.data_ptr() for y in yh], iters,
+                         [x.data_ptr() for x in Xs] if Xs else None, [z.data_ptr() for z in Zs] if Zs else None)
+        self._keep = (yl, yh)
+        return Xs, Zs
+
+    def set_option(self, option, value):
+        fuse_batch_set_option(self.b, option, value)
+
+    def profile(self, which=FUSE_K_LATENT, reset=False):
+        return fuse_batch_profile(self.b, which, reset)
+
+    def autotune(self, Yls, Yhs, iters=2):
+        fuse_batch_autotune(self.b, [y.data_ptr() for y in Yls], [y.data_ptr() for y in Yhs], iters)
+
+    def sync(self):
+        fuse_batch_sync(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            fuse_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -227,3 +227,14 @@ def batch_sizes(n: int = 64, seed: int = SEED_BASE + 4) -> list[int]:
     """Square sizes for the batched uneven-tile workload, uniform over {96,...,384}."""
     rng = np.random.default_rng(seed)
     return [int(s) for s in rng.choice([96, 128, 192, 256, 320, 384], size=n)]
+
+
+def batch_workload(n: int = 64, seed: int = SEED_BASE + 4, sizes=None) -> list[Problem]:
+    """The batched uneven-tile workload: n HS+MS problems, square sizes uniform over
+    {96, 128, 192, 256, 320, 384}, 31 bands, MS 3 bands, ratio 4, 9x9 blur (sigma 1.7), 35 dB,
+    patch 3x3 (K=1), search 7x7 (S=3), L_s = 8, 100 iterations each."""
+    sizes = sizes if sizes is not None else batch_sizes(n, seed)
+    return [make_problem(H=sz, W=sz, L_l=31, L_h=3, L_s=8, d=4, blur_size=9, blur_sigma=1.7, snr_l=35.0,
+                         snr_h=35.0, K=1, S=3, iters=100, kind="hsms", seed=seed + 1000 * (i + 1),
+                         name=f"batch{i}_{sz}")
+            for i, sz in enumerate(sizes)]
