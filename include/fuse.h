@@ -82,7 +82,9 @@ enum {
     FUSE_OPT_LATENT_BANDS = 8,   /* bands streamed by one latent block, 1..64 (default 1;
                                     2 in batches) */
     FUSE_OPT_FFT_ROWS = 9,       /* rows per block of the row FFT passes: 1, 2, 4 or 8 */
-    FUSE_OPT_FFT_COLS = 10       /* columns per block of the column FFT pass: power of 2 <= 32 */
+    FUSE_OPT_FFT_COLS = 10,      /* columns per block of the column FFT pass: power of 2 <= 32 */
+    FUSE_OPT_GRAD_SEGMENT = 11   /* iterations per checkpointed segment of fuse_grad_forward
+                                    (default 0: one segment, every iteration taped) */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -221,6 +223,52 @@ fuse_status fuse_profile(fuse_ctx* ctx, int which, double* ms, long long* launch
  * capture.  Calls no allocating routine.  Errors: FUSE_EINVAL, FUSE_EUNSUPPORTED, FUSE_ECUDA. */
 fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev, int H, int W, int L_s, int K,
                             int S, fuse_dtype dtype, fuse_dtype wdtype, double* phi_dev, void* stream);
+
+/* ---- Reverse pass (differentiation of K unrolled iterations) -----------------------------
+ * The ADMM of Sec. IV run for a fixed number K of iterations from zero state is a
+ * differentiable map (Y_l, Y_h, lambda1, lambda2, rho) -> X_K; the paper does not
+ * differentiate it, these entry points do, by the exact adjoint of every update in reverse
+ * order: the soft threshold of eq. Qj_main (derivative taken as 0 at |v| = mu), the closed
+ * forms of eqs. Qm_update and Qh_update, the dual updates, and the X update of eq. inv (A is
+ * symmetric, so its adjoint is the same per-frequency division).  The weights omega are held
+ * fixed.
+ *
+ * Checkpointing: the forward keeps, for each of its iterations, X and the entering Lambda1,
+ * Lambda2 and Sigma (the tape).  With FUSE_OPT_GRAD_SEGMENT = s > 0 the iterations are grouped
+ * in segments of s: the tape holds s iterations, the full state entering each later segment is
+ * saved, and the reverse pass re-runs each earlier segment from its saved state (recompute).
+ * Device memory: fuse_grad_bytes.  The workspace is allocated on first use and kept. */
+
+/* Bytes of the reverse-pass workspace for `iters` iterations under the current options. */
+fuse_status fuse_grad_bytes(fuse_ctx* ctx, int iters, size_t* bytes);
+
+/* Forward pass with checkpoints: `iters` iterations from zero state on Y_l, Y_h (as in
+ * fuse_solve, cold start) with the context's weights; X of the last iteration to X_out
+ * (nullable, device [L_s][H][W]).  Leaves the context's state as fuse_solve would.  Any later
+ * call that changes inputs or state (fuse_solve, fuse_weights, fuse_set_weights,
+ * fuse_set_state, FUSE_OPT_HALF_WINDOW) invalidates the checkpoints.  Asynchronous.
+ * Errors: FUSE_EINVAL, FUSE_ESTATE (no weights), FUSE_EUNSUPPORTED (L_s > 32), FUSE_ENOMEM. */
+fuse_status fuse_grad_forward(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters,
+                              void* X_out);
+
+/* Reverse pass for the last fuse_grad_forward, for the loss L with
+ *   Xbar_dev  dL/dX  of the last iterate, device [L_s][H][W] (nullable),
+ *   Zbar_dev  dL/dZ, Z = X E, device [L_l][H][W] (nullable; both given: their effects add).
+ * Outputs (each nullable): Yl_bar_dev dL/dY_l [L_l][H/ratio][W/ratio], Yh_bar_dev dL/dY_h
+ * [L_h][H][W] (device, dtype), param_bar[3] = dL/dlambda1, dL/dlambda2, dL/drho (host,
+ * double; when given the call synchronises the stream).  With one segment the tape is kept
+ * and the call may be repeated with other dL/dX; with several segments the recomputation
+ * overwrites the context's ADMM state (the next warm fuse_solve starts from zero) and the
+ * checkpoints are consumed.  Sums are in the context's dtype, parameter sums in FP64.
+ * Errors: FUSE_EINVAL (no dL/dX nor dL/dZ), FUSE_ESTATE (no valid forward),
+ * FUSE_ENONFINITE, FUSE_ECUDA. */
+fuse_status fuse_grad_backward(fuse_ctx* ctx, const void* Xbar_dev, const void* Zbar_dev,
+                               void* Yl_bar_dev, void* Yh_bar_dev, double* param_bar);
+
+/* fuse_grad_forward followed by fuse_grad_backward. */
+fuse_status fuse_grad(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters,
+                      const void* Xbar_dev, const void* Zbar_dev, void* X_out, void* Yl_bar_dev,
+                      void* Yh_bar_dev, double* param_bar);
 
 /* Device self-check.  which = 1: a kernel waits (bounded) on a barrier that nothing completes;
  * returns FUSE_OK when the wait gave up and its timeout was reported to the host as designed,

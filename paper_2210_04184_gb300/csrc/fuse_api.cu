@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "k_fft.cuh"
+#include "k_grad.cuh"
 #include "k_latent.cuh"
 #include "k_objective.cuh"
 #include "k_pixel.cuh"
@@ -28,6 +29,8 @@ constexpr int kMaxSmem = 200 * 1024;
 struct Event2 { cudaEvent_t a, b; };
 
 }  // namespace
+
+struct GradWork;
 
 struct fuse_ctx {
     // problem
@@ -83,6 +86,13 @@ struct fuse_ctx {
     unsigned wait_limit = 1u << 22;
     // half-window latent state (one offset of each +-tau pair); 0 = full window
     int half = 1;
+    // reverse pass: workspace, iterations per checkpointed segment (0 = one segment), a counter
+    // bumped by every call that changes inputs or state (a taped forward is valid while unchanged)
+    GradWork* gw = nullptr;
+    int grad_seg = 0;
+    long long epoch = 0;
+    // host FP64 copies of (E E^T + rho I)^{-1}, F and E R, for the parameter derivatives
+    std::vector<double> hM1, hF, hER;
 };
 
 namespace {
@@ -595,6 +605,7 @@ fuse_status run_iterations(fuse_ctx* c, int iters) {
 fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, int warm, void* Xo, void* Zo) {
     const bool f64 = c->dtype == FUSE_F64;
     fuse_status st;
+    ++c->epoch;
     // S^T Y_l E^T on the sampled lattice and lambda1/rho Y_h R^T E^T (eqs. Qh_update, Qm_update)
     st = f64 ? Impl<double>::band_mix(c, c->stream, Yl, c->D9a, c->Et, c->nl, c->Ll, c->Ls)
              : Impl<float>::band_mix(c, c->stream, Yl, c->D9a, c->Et, c->nl, c->Ll, c->Ls);
@@ -622,6 +633,7 @@ fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, i
 
 fuse_status weights_impl(fuse_ctx* c, const void* G) {
     fuse_status st;
+    ++c->epoch;
     if (c->dtype == FUSE_F64) st = Impl<double>::weights<double>(c, G);
     else if (c->wdtype == FUSE_BF16) st = Impl<float>::weights<__nv_bfloat16>(c, G);
     else st = Impl<float>::weights<float>(c, G);
@@ -629,7 +641,11 @@ fuse_status weights_impl(fuse_ctx* c, const void* G) {
     return st;
 }
 
+void grad_free(GradWork* g);
+
 void release(fuse_ctx* c) {
+    grad_free(c->gw);
+    c->gw = nullptr;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (auto& e : c->ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -943,6 +959,8 @@ fuse_status batch_run(fuse_batch* b, int iters) {
 // entry points
 // ---------------------------------------------------------------------------------------
 
+#include "grad_impl.cuh"
+
 extern "C" {
 
 const char* fuse_status_string(fuse_status s) {
@@ -1095,6 +1113,9 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
             Fm[(size_t)i * Ls + j] = cr * t + (i == j ? 1.0 : 0.0);
         }
     if (!invert(M1, Ls) || !invert(Fm, Ls)) return bail(FUSE_EINVAL);
+    c->hM1 = M1;
+    c->hF = Fm;
+    c->hER = ER;
     // band-mixing matrices (Lin x Lout row-major)
     std::vector<double> Et((size_t)Ll * Ls), Mh((size_t)Lh * Ls), Emix(Em);
     for (int l = 0; l < Ll; ++l)
@@ -1189,6 +1210,7 @@ fuse_status fuse_set_weights(fuse_ctx* c, const void* w) {
     if (!w) return fail(c, FUSE_EINVAL, "weights pointer is NULL");
     CK(c, cudaMemcpyAsync(c->omega, w, (size_t)c->nW * c->n * c->wsz, cudaMemcpyDefault, c->stream));
     c->have_weights = true;
+    ++c->epoch;
     return FUSE_OK;
 }
 
@@ -1285,6 +1307,7 @@ fuse_status fuse_set_state(fuse_ctx* c, const void* src) {
     CK(c, cudaStreamSynchronize(c->stream));
     c->have_state = true;
     c->have_x = true;
+    ++c->epoch;
     return FUSE_OK;
 }
 
@@ -1294,6 +1317,10 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
     switch (option) {
         case FUSE_OPT_PROFILE: c->profile = value != 0; return FUSE_OK;
         case FUSE_OPT_GRAPH: c->use_graph = value != 0; return FUSE_OK;
+        case FUSE_OPT_GRAD_SEGMENT:
+            if (value < 0 || value > (1 << 30)) return fail(c, FUSE_EINVAL, "iterations per segment must be >= 0");
+            c->grad_seg = (int)value;
+            return FUSE_OK;
         case FUSE_OPT_LATENT_BANDS:
             if (value < 1 || value > 64) return fail(c, FUSE_EINVAL, "bands per latent block must be in [1, 64]");
             c->lat_bpb = (int)value;
@@ -1353,6 +1380,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             if (s2 != FUSE_OK) return s2;
             c->sig_bytes = bytes;
             c->half = h;
+            ++c->epoch;
             c->have_state = false;
             c->have_x = false;
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
@@ -1483,6 +1511,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_LATENT_BANDS: *value = c->lat_bpb; return FUSE_OK;
         case FUSE_OPT_FFT_ROWS: *value = c->fr_rpb; return FUSE_OK;
         case FUSE_OPT_FFT_COLS: *value = c->fc_cw; return FUSE_OK;
+        case FUSE_OPT_GRAD_SEGMENT: *value = c->grad_seg; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }
@@ -1730,6 +1759,40 @@ fuse_status fuse_reset_error(fuse_ctx* c) {
     c->sticky = FUSE_OK;
     c->err.clear();
     return FUSE_OK;
+}
+
+fuse_status fuse_grad_bytes(fuse_ctx* c, int iters, size_t* bytes) {
+    if (!c || !bytes || iters < 0) return FUSE_EINVAL;
+    *bytes = grad_bytes(c, iters);
+    return FUSE_OK;
+}
+
+fuse_status fuse_grad_forward(fuse_ctx* c, const void* Yl, const void* Yh, int iters, void* X_out) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (!Yl || !Yh) return fail(c, FUSE_EINVAL, "Y_l or Y_h is NULL");
+    if (iters < 0) return fail(c, FUSE_EINVAL, "iters must be >= 0");
+    if (!c->have_weights) return FUSE_ESTATE;
+    if (pixel_bucket(c->Ls) == 0) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass supports L_s <= 32");
+    return grad_forward_impl(c, Yl, Yh, iters, X_out);
+}
+
+fuse_status fuse_grad_backward(fuse_ctx* c, const void* Xbar, const void* Zbar, void* Yl_bar, void* Yh_bar,
+                               double* param_bar) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (!Xbar && !Zbar) return fail(c, FUSE_EINVAL, "both dL/dX and dL/dZ are NULL");
+    return grad_backward_impl(c, Xbar, Zbar, Yl_bar, Yh_bar, param_bar);
+}
+
+fuse_status fuse_grad(fuse_ctx* c, const void* Yl, const void* Yh, int iters, const void* Xbar, const void* Zbar,
+                      void* X_out, void* Yl_bar, void* Yh_bar, double* param_bar) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (!Xbar && !Zbar) return fail(c, FUSE_EINVAL, "both dL/dX and dL/dZ are NULL");
+    st = fuse_grad_forward(c, Yl, Yh, iters, X_out);
+    if (st != FUSE_OK) return st;
+    return grad_backward_impl(c, Xbar, Zbar, Yl_bar, Yh_bar, param_bar);
 }
 
 }  // extern "C"

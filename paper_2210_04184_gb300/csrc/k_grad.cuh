@@ -1,0 +1,270 @@
+// Reverse pass of one unrolled ADMM iteration (differentiation of the updates of Sec. IV).
+//
+// Forward iteration t, in the variables the solver keeps (state in: Lambda1, U1 = P1 + Lambda1,
+// Lambda2, U2 = P2 + Lambda2, the latent state Sigma and the adjoint sum R of the previous pass):
+//   C = B^T U1 + U2 + R,  X = A^{-1} C  (eq. inv),  BX = B X,
+//   pixel (eqs. Qm_update, Qh_update, dualvar1_main, dualvar2_main):
+//     w2 = X - Lambda2, a2 = w2 + D9b, P2 = a2 F, Lambda2' = P2 - w2, U2' = 2 P2 - w2,
+//     w1 = BX - Lambda1, P1 = (rho w1 + D9a) M1 where sampled, else w1,
+//     Lambda1' = P1 - w1, U1' = 2 P1 - w1;
+//   latent (eqs. Qj_main, dualvar3_main), per offset tau and patch offset k:
+//     v = D X - Sigma, Sigma' = -clamp(v, -mu, mu), G = v + 2 Sigma', R' = sum D^T G.
+// Reverse, given the adjoints (bars) of the iteration's outputs:
+//   latent: Gbar = D Rbar', inside = |v| < mu,
+//           vbar = inside ? -(Gbar + Sigmabar') : Gbar,  Sigmabar = -vbar,  Xbar += sum D^T vbar,
+//           mubar = -(Sigmabar' + 2 Gbar) sign(v) where not inside;
+//   pixel:  P2bar = Lambda2bar' + 2 U2bar', a2bar = P2bar F^T, w2bar = a2bar - Lambda2bar' - U2bar',
+//           Xbar += w2bar, Lambda2bar = -w2bar, D9bbar += a2bar, Fbar += a2^T P2bar;
+//           P1bar = Lambda1bar' + 2 U1bar', where sampled a1bar = P1bar M1^T,
+//           w1bar = rho a1bar - Lambda1bar' - U1bar', D9abar += a1bar, M1bar += a1^T P1bar,
+//           rhobar += a1bar . w1; elsewhere w1bar = U1bar';  BXbar = w1bar, Lambda1bar = -w1bar;
+//   X:      Xbar += B^T BXbar, Cbar = A^{-1} Xbar (A is symmetric),
+//           U1bar = B Cbar, U2bar = Rbar = Cbar for the previous iteration.
+// The clamp's derivative at |v| = mu is taken as 0 (the open interval), so the kink counts as
+// outside the dead zone.
+// Half-window mode: the kept offsets tau stand for the pairs +-tau.  Sigmabar is kept for the kept
+// offsets with the full window's values (the -tau half is its mirror image), so the adjoint sum
+// of vbar and the threshold partial sums are counted twice, like the forward adjoint sum.
+#pragma once
+#include "common.cuh"
+#include "k_objective.cuh"
+
+namespace fuse {
+
+// Latent reverse pass of one iteration.  Layouts as the forward latent pass: X [L_s][H][W],
+// omega [|W|][H][W], the state re-indexed by the source pixel m = i - k.  Reads the state
+// that entered the iteration (Sin) and the adjoint Rbar (= Cbar of the next iteration); Sb holds
+// the adjoint of the state the iteration produced and is overwritten with the adjoint of the state
+// that entered it.  The adjoint sum sum D^T vbar is written as planes A/V exactly as the forward
+// pass writes R (plane tau1 + S: A, plane (2S+1) + tau1 + S: V), and
+// part[block] += (half ? 2 : 1) sum mubar * omega(i) over the block's entries.
+// Threads: (W/VEC) x Ty rounded up to whole warps (for the block sum), each owning VEC consecutive
+// pixels; grid (ceil(H/Ty), L_s, rows of W).
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(256)
+latent_bwd_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* __restrict__ Sin,
+                  T* __restrict__ Sb, const T* __restrict__ Rb, T* __restrict__ planes, double* __restrict__ part,
+                  int H, int W, int Ls, int S, int Ty, T coef, int half) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Hs = reinterpret_cast<T*>(smem_raw);           // [(2S+1)][Ty][W]
+    constexpr int PS = 2 * K + 1;
+    constexpr int NP = PS * PS;
+    const int tpr = W / VEC;
+    const int tid = threadIdx.x;
+    const int r = tid / tpr;
+    const int x0 = (tid - r * tpr) * VEC;
+    const int y = blockIdx.x * Ty + r;
+    const TauMap tm{S, half};
+    const int t1 = tm.t1_of_block(blockIdx.z);
+    const int nt2 = tm.nt2(t1);
+    const int c = blockIdx.y;
+    const bool valid = r < Ty;                        // the block is rounded up to whole warps
+    const bool active = valid && y < H;
+    const size_t n = (size_t)H * W;
+    const int side = 2 * S + 1;
+    const T* Xc = X + (size_t)c * n;
+    const T* Rc = Rb + (size_t)c * n;
+    const size_t vstride = (size_t)Ls * n / VEC;
+    T Xm[VEC], Rm[VEC], A[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        Xm[j] = active ? Xc[(size_t)y * W + x0 + j] : T(0);
+        Rm[j] = active ? Rc[(size_t)y * W + x0 + j] : T(0);
+        A[j] = T(0);
+    }
+    double smu = 0.0;
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
+        T Hacc[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
+        if (active) {
+            const int ys = wrap1(y - t1, H);
+            T delta[VEC], gb[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                const size_t q = (size_t)ys * W + wrap1(x0 + j - t2, W);
+                delta[j] = Xm[j] - Xc[q];               // D X at the re-indexed pixel
+                gb[j] = Rm[j] - Rc[q];                  // Gbar = D Rbar
+            }
+            const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
+            const size_t base = ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0;
+            const vecT<T, VEC>* si = reinterpret_cast<const vecT<T, VEC>*>(Sin + base);
+            vecT<T, VEC>* sb = reinterpret_cast<vecT<T, VEC>*>(Sb + base);
+#pragma unroll
+            for (int k1 = -K; k1 <= K; ++k1) {
+                const int yw = wrap1(y + k1, H);
+                T w[VEC + 2 * K];
+#pragma unroll
+                for (int j = 0; j < VEC + 2 * K; ++j) w[j] = (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W));
+#pragma unroll
+                for (int k2 = 0; k2 < PS; ++k2) {
+                    const size_t off = (size_t)((k1 + K) * PS + k2) * vstride;
+                    const vecT<T, VEC> s_in = si[off];
+                    vecT<T, VEC> s_b = sb[off];
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        const T v = delta[j] - s_in.v[j];
+                        const T wt = w[j + k2];
+                        const bool inside = (v < T(0) ? -v : v) < coef * wt;
+                        const T vb = inside ? -(gb[j] + s_b.v[j]) : gb[j];
+                        if (!inside && v != T(0)) {
+                            const T mb = -(s_b.v[j] + T(2) * gb[j]);
+                            smu += (double)(v > T(0) ? mb * wt : -mb * wt);
+                        }
+                        Hacc[j] += vb;
+                        s_b.v[j] = -vb;
+                    }
+                    sb[off] = s_b;
+                }
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                A[j] += Hacc[j];
+                Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
+            }
+        }
+    }
+    double v1[1] = {half ? 2.0 * smu : smu};
+    block_sum<1, true>(v1, part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    __syncthreads();
+    if (!active) return;
+    T V[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) V[j] = T(0);
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
+        const T* hrow = Hs + ((size_t)(t2 + S) * Ty + r) * W;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) V[j] += hrow[wrap1(x0 + j + t2, W)];
+    }
+    vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + (size_t)y * W + x0, A);
+    vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + (size_t)y * W + x0, V);
+}
+
+// Pixel reverse pass of one iteration.
+template <typename T>
+struct PixelBwdArgs {
+    const T* X;        // X of the iteration
+    const T* BX;       // B X
+    const T* Lam1;     // Lambda1, Lambda2 that entered the iteration
+    const T* Lam2;
+    const T* U1b;      // adjoints of U1', U2' (= B Cbar, Cbar of the next iteration)
+    const T* U2b;
+    T* L1b;            // in: adjoints of Lambda1', Lambda2'; out: adjoints of Lambda1, Lambda2
+    T* L2b;
+    T* Xp;             // out: w2bar (the pixel pass's part of Xbar)
+    T* BXb;            // out: w1bar (the adjoint of B X)
+    T* D9ab;           // += a1bar on the sampled lattice [L_s][H/d][W/d]
+    T* D9bb;           // += a2bar
+    const T* D9a;
+    const T* D9b;
+    const T* M1;       // (E E^T + rho I)^{-1}, row-major
+    const T* F;        // (I + lambda1/rho E R R^T E^T)^{-1}, row-major
+    const T* Krho;     // d F / d rho, d F / d lambda1, d M1 / d rho (row-major)
+    const T* Klam;
+    const T* Kmu;
+    double* part;      // [blocks][3] += see pixel_bwd_kernel
+    int H, W, Ls, d;
+    T rho;
+};
+
+// One thread per pixel, band vectors in registers (MAXLS >= L_s).  Per block, part[3 b + q] +=
+//   q = 0: a2 Krho P2bar^T + a1 Kmu P1bar^T + a1bar . w1     (the rho partials of F, M1 and a1)
+//   q = 1: a2 Klam P2bar^T                                     (the lambda1 partial of F)
+//   q = 2: a2bar . D9b                                         (the rho and lambda1 partials of D9b)
+template <typename T, int MAXLS>
+__global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
+    const int H = g.H, W = g.W, Ls = g.Ls, d = g.d;
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double q[3] = {0.0, 0.0, 0.0};
+    if (p < n) {
+        T pb[MAXLS], a[MAXLS], wb[MAXLS];
+#pragma unroll
+        for (int j = 0; j < MAXLS; ++j) {
+            if (j < Ls) {
+                const T l2b = g.L2b[(size_t)j * n + p], u2b = g.U2b[(size_t)j * n + p];
+                pb[j] = l2b + T(2) * u2b;
+                wb[j] = -(l2b + u2b);
+                a[j] = g.X[(size_t)j * n + p] - g.Lam2[(size_t)j * n + p] + g.D9b[(size_t)j * n + p];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MAXLS; ++i) {
+            if (i < Ls) {
+                T ab = T(0), kr = T(0), kl = T(0);
+#pragma unroll
+                for (int j = 0; j < MAXLS; ++j) {
+                    if (j < Ls) {
+                        ab += pb[j] * g.F[i * Ls + j];
+                        kr += g.Krho[i * Ls + j] * pb[j];
+                        kl += g.Klam[i * Ls + j] * pb[j];
+                    }
+                }
+                const T d9b = g.D9b[(size_t)i * n + p];
+                q[0] += (double)(a[i] * kr);
+                q[1] += (double)(a[i] * kl);
+                q[2] += (double)(ab * d9b);
+                const T w2b = wb[i] + ab;
+                g.Xp[(size_t)i * n + p] = w2b;
+                g.L2b[(size_t)i * n + p] = -w2b;
+                g.D9bb[(size_t)i * n + p] += ab;
+            }
+        }
+        const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+#pragma unroll
+        for (int j = 0; j < MAXLS; ++j) {
+            if (j < Ls) {
+                const T l1b = g.L1b[(size_t)j * n + p], u1b = g.U1b[(size_t)j * n + p];
+                pb[j] = l1b + T(2) * u1b;
+                wb[j] = -(l1b + u1b);
+                a[j] = g.BX[(size_t)j * n + p] - g.Lam1[(size_t)j * n + p];      // w1
+            }
+        }
+        if ((y % d) == 0 && (x % d) == 0) {
+            const size_t nl = (size_t)(H / d) * (W / d);
+            const size_t pl = (size_t)(y / d) * (W / d) + x / d;
+#pragma unroll
+            for (int i = 0; i < MAXLS; ++i) {
+                if (i < Ls) {
+                    T ab = T(0), km = T(0);
+#pragma unroll
+                    for (int j = 0; j < MAXLS; ++j) {
+                        if (j < Ls) {
+                            ab += pb[j] * g.M1[i * Ls + j];
+                            km += g.Kmu[i * Ls + j] * pb[j];
+                        }
+                    }
+                    const T a1 = g.rho * a[i] + g.D9a[(size_t)i * nl + pl];
+                    q[0] += (double)(a1 * km) + (double)(ab * a[i]);
+                    const T w1b = wb[i] + g.rho * ab;
+                    g.BXb[(size_t)i * n + p] = w1b;
+                    g.L1b[(size_t)i * n + p] = -w1b;
+                    g.D9ab[(size_t)i * nl + pl] += ab;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < MAXLS; ++i) {
+                if (i < Ls) {
+                    const T w1b = wb[i] + pb[i];             // = U1bar'
+                    g.BXb[(size_t)i * n + p] = w1b;
+                    g.L1b[(size_t)i * n + p] = -w1b;
+                }
+            }
+        }
+    }
+    block_sum<3, true>(q, g.part + (size_t)blockIdx.x * 3);
+}
+
+// y += x over n elements.
+template <typename T>
+__global__ void __launch_bounds__(256) axpy_kernel(T* __restrict__ y, const T* __restrict__ x, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] += x[i];
+}
+
+}  // namespace fuse

@@ -12,8 +12,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block-wide sum of NV values per thread into out[NV] (thread 0 writes).  blockDim % 32 == 0.
-template <int NV>
+// Block-wide sum of NV values per thread into out[NV] (thread 0 writes; ACC adds to out instead
+// of overwriting it).  blockDim % 32 == 0.
+template <int NV, bool ACC = false>
 __device__ void block_sum(double (&v)[NV], double* out) {
     __shared__ double red[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -28,7 +29,7 @@ __device__ void block_sum(double (&v)[NV], double* out) {
         for (int q = 0; q < NV; ++q) {
             double s = lane < nw ? red[q][lane] : 0.0;
             s = warp_sum(s);
-            if (lane == 0) out[q] = s;
+            if (lane == 0) out[q] = ACC ? out[q] + s : s;
         }
     }
 }

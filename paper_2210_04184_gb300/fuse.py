@@ -23,6 +23,7 @@ FUSE_F32, FUSE_F64, FUSE_BF16 = 0, 1, 2
 FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
 FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
 FUSE_OPT_HALF_WINDOW, FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS = 7, 8, 9, 10
+FUSE_OPT_GRAD_SEGMENT = 11
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -80,6 +81,10 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_autotune": (_ST, [_VP, _VP, _VP, _I]),
         "fuse_batch_autotune": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I]),
         "fuse_selftest": (_ST, [_VP, _I]),
+        "fuse_grad_bytes": (_ST, [_VP, _I, ctypes.POINTER(ctypes.c_size_t)]),
+        "fuse_grad_forward": (_ST, [_VP, _VP, _VP, _I, _VP]),
+        "fuse_grad_backward": (_ST, [_VP, _VP, _VP, _VP, _VP, _D]),
+        "fuse_grad": (_ST, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _D]),
         "fuse_phi_static": (_ST, [_VP, _VP, _I, _I, _I, _I, _I, _I, _I, _VP, _VP]),
         "fuse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
         "fuse_batch_solve": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP),
@@ -235,6 +240,34 @@ def fuse_phi_static(X_dev: int, omega_dev: int, H: int, W: int, L_s: int, K: int
                                   _VP(phi_dev), _VP(stream or None)))
 
 
+def fuse_grad_bytes(ctx, iters: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().fuse_grad_bytes(ctx, iters, ctypes.byref(out)), ctx)
+    return int(out.value)
+
+
+def fuse_grad_forward(ctx, Yl_dev: int, Yh_dev: int, iters: int, X_out: int | None):
+    _check(load().fuse_grad_forward(ctx, _VP(Yl_dev), _VP(Yh_dev), iters, _VP(X_out or None)), ctx)
+
+
+def fuse_grad_backward(ctx, Xbar_dev: int | None, Zbar_dev: int | None, Yl_bar: int | None,
+                       Yh_bar: int | None, want_params: bool = True):
+    """Returns (dL/dlambda1, dL/dlambda2, dL/drho) when want_params, else None."""
+    pb = (ctypes.c_double * 3)()
+    _check(load().fuse_grad_backward(ctx, _VP(Xbar_dev or None), _VP(Zbar_dev or None), _VP(Yl_bar or None),
+                                     _VP(Yh_bar or None), pb if want_params else None), ctx)
+    return (pb[0], pb[1], pb[2]) if want_params else None
+
+
+def fuse_grad(ctx, Yl_dev: int, Yh_dev: int, iters: int, Xbar_dev: int | None, Zbar_dev: int | None,
+              X_out: int | None, Yl_bar: int | None, Yh_bar: int | None, want_params: bool = True):
+    pb = (ctypes.c_double * 3)()
+    _check(load().fuse_grad(ctx, _VP(Yl_dev), _VP(Yh_dev), iters, _VP(Xbar_dev or None), _VP(Zbar_dev or None),
+                            _VP(X_out or None), _VP(Yl_bar or None), _VP(Yh_bar or None),
+                            pb if want_params else None), ctx)
+    return (pb[0], pb[1], pb[2]) if want_params else None
+
+
 def _bcheck(st: int, b=None):
     if st != FUSE_OK:
         msg = ""
@@ -321,6 +354,7 @@ class Fusion:
         self.wdtype = wdtype
         self.tdtype = torch.float64 if dtype == "f64" else torch.float32
         self.wtdtype = {"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}[wdtype]
+        self._lam1, self._lam2, self._rho = float(lam1), float(lam2), float(rho)
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         self.ctx = fuse_init(self.geom, blur, ratio, R, E, K, S, lam1, lam2, rho, h,
                              DTYPES[dtype], DTYPES[wdtype], s)
@@ -411,6 +445,43 @@ class Fusion:
                  ("latent_bands", FUSE_OPT_LATENT_BANDS), ("fft_rows", FUSE_OPT_FFT_ROWS),
                  ("fft_cols", FUSE_OPT_FFT_COLS))}
 
+    # ---- reverse pass ----
+    def grad_forward(self, Yl, Yh, iters):
+        """`iters` iterations from zero state with checkpoints; returns X of the last one."""
+        d = self.ratio
+        yl = self._t(Yl, (self.L_l, self.H // d, self.W // d))
+        yh = self._t(Yh, (self.L_h, self.H, self.W))
+        X = self.torch.empty((self.L_s, self.H, self.W), dtype=self.tdtype, device="cuda")
+        self._sync_stream()
+        fuse_grad_forward(self.ctx, yl.data_ptr(), yh.data_ptr(), iters, X.data_ptr())
+        self._keep = (yl, yh)
+        return X
+
+    def grad_backward(self, Xbar=None, Zbar=None):
+        """Reverse pass of the last grad_forward for dL/dX (and/or dL/dZ) of the last iterate.
+        Returns (dL/dY_l, dL/dY_h, {"lam1", "lam2", "rho"})."""
+        t = self.torch
+        xb = self._t(Xbar, (self.L_s, self.H, self.W)) if Xbar is not None else None
+        zb = self._t(Zbar, (self.L_l, self.H, self.W)) if Zbar is not None else None
+        d = self.ratio
+        gl = t.empty((self.L_l, self.H // d, self.W // d), dtype=self.tdtype, device="cuda")
+        gh = t.empty((self.L_h, self.H, self.W), dtype=self.tdtype, device="cuda")
+        self._sync_stream()
+        p = fuse_grad_backward(self.ctx, xb.data_ptr() if xb is not None else None,
+                               zb.data_ptr() if zb is not None else None, gl.data_ptr(), gh.data_ptr())
+        return gl, gh, dict(lam1=p[0], lam2=p[1], rho=p[2])
+
+    def params(self):
+        """(lambda1, lambda2, rho) of the context as a float64 CPU tensor, for unrolled()."""
+        return self.torch.tensor([self._lam1, self._lam2, self._rho], dtype=self.torch.float64)
+
+    def unrolled(self, Yl, Yh, iters, params=None):
+        """X after `iters` iterations from zero state as a differentiable function of Y_l, Y_h and
+        params = (lambda1, lambda2, rho) (a tensor equal to the context's values, see params())."""
+        if params is None:
+            params = self.params()
+        return UnrolledADMM.apply(Yl, Yh, params, self, iters)
+
     def close(self):
         if getattr(self, "ctx", None):
             fuse_destroy(self.ctx)
@@ -466,3 +537,43 @@ class FusionBatch:
             self.close()
         except Exception:
             pass
+
+
+def _unrolled_function():
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        """X_K of K unrolled ADMM iterations (fuse_grad_forward) with its reverse pass
+        (fuse_grad_backward).  The weights omega are constants of the map."""
+
+        @staticmethod
+        def forward(ctx, Yl, Yh, params, fusion, iters):
+            p = [float(v) for v in params.detach().cpu().tolist()]
+            ref = (fusion._lam1, fusion._lam2, fusion._rho)
+            if any(abs(a - b) > 1e-12 * max(1.0, abs(b)) for a, b in zip(p, ref)):
+                raise ValueError(f"params {p} differ from the context's (lambda1, lambda2, rho) = {ref}")
+            ctx.fusion = fusion
+            ctx.pdev = params.device
+            ctx.pdtype = params.dtype
+            return fusion.grad_forward(Yl.detach(), Yh.detach(), iters)
+
+        @staticmethod
+        def backward(ctx, Xbar):
+            f = ctx.fusion
+            gl, gh, p = f.grad_backward(Xbar=Xbar.contiguous())
+            gp = torch.tensor([p["lam1"], p["lam2"], p["rho"]], dtype=ctx.pdtype, device=ctx.pdev)
+            return gl, gh, gp, None, None
+
+    return _Unrolled
+
+
+class _LazyFunction:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _unrolled_function()
+        return _LazyFunction._fn.apply(*args)
+
+
+UnrolledADMM = _LazyFunction()

@@ -1,0 +1,249 @@
+"""Reverse pass through K unrolled iterations (fuse_grad_*) against the oracle's FP64 reverse
+pass (oracle/grad.py) and against central differences of the GPU's own FP64 forward.
+
+The loss is L = <Wt, X_K> for a fixed seeded Wt, so dL/dX_K = Wt.  Tolerances: FP64 within
+1e-9 relative (both sides take the same clamp decisions up to rounding); FP32 within 2e-3
+relative (a clamp decision taken on an FP32 v within rounding of mu flips that entry's
+adjoint, so FP32 gradients carry a small decision noise on top of rounding)."""
+import numpy as np
+import pytest
+
+from paper_2210_04184_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle import grad as ograd, nlpr  # noqa: E402
+from paper_2210_04184_gb300 import build as _build  # noqa: E402
+from paper_2210_04184_gb300.fuse import (Fusion, FuseError, FUSE_ESTATE, FUSE_EINVAL,  # noqa: E402
+                                         FUSE_OPT_GRAD_SEGMENT, FUSE_OPT_HALF_WINDOW, fuse_reset_error)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def problem(seed=synth.SEED_BASE + 11, **kw):
+    base = dict(H=40, W=40, L_l=6, L_h=2, L_s=3, d=4, blur_size=5, blur_sigma=1.0, K=1, S=2,
+                lam1=0.7, lam2=2e-3, rho=2e-2, snr_l=30.0, snr_h=30.0)
+    base.update(kw)
+    return synth.make_problem(seed=seed, **base)
+
+
+def context(p, dtype, wdtype, omega, opts=()):
+    f = Fusion.from_problem(p, dtype=dtype, wdtype=wdtype)
+    for o, v in opts:
+        f.set_option(o, v)
+    f.set_weights(torch.tensor(omega, dtype=f.wtdtype, device="cuda"))
+    td = torch.float64 if dtype == "f64" else torch.float32
+    yl = torch.tensor(p.Yl, dtype=td, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=td, device="cuda")
+    return f, yl, yh
+
+
+def gpu_grad(f, yl, yh, iters, Wt):
+    td = yl.dtype
+    X = f.grad_forward(yl, yh, iters)
+    gl, gh, pr = f.grad_backward(Xbar=torch.tensor(Wt, dtype=td, device="cuda"))
+    f.sync()
+    return X.double().cpu().numpy(), gl.double().cpu().numpy(), gh.double().cpu().numpy(), pr
+
+
+def oracle_grad(p, iters, omega, Wt_lhw):
+    X, g = ograd.unrolled_grad(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S,
+                               p.lam1, p.lam2, p.rho, omega, iters, lambda X: nlpr.to_hwl(Wt_lhw))
+    return nlpr.to_lhw(X), nlpr.to_lhw(g["Yl"]), nlpr.to_lhw(g["Yh"]), g
+
+
+def weights64(p):
+    return nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+
+
+def compare(gpu, ora, tol, tol_x):
+    X, gl, gh, pr = gpu
+    Xo, glo, gho, go = ora
+    assert rel(X, Xo) <= tol_x
+    assert rel(gl, glo) <= tol, ("Yl", rel(gl, glo))
+    assert rel(gh, gho) <= tol, ("Yh", rel(gh, gho))
+    for k in ("lam1", "lam2", "rho"):
+        assert abs(pr[k] - go[k]) <= tol * max(abs(go[k]), 1e-12) + 1e-12, (k, pr[k], go[k])
+
+
+@pytest.mark.parametrize("half", [1, 0])
+def test_grad_matches_oracle_fp64(half):
+    p = problem()
+    om = weights64(p)
+    Wt = np.random.default_rng(7).standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f64", "f64", om, opts=((FUSE_OPT_HALF_WINDOW, half),))
+    compare(gpu_grad(f, yl, yh, 6, Wt), oracle_grad(p, 6, om, Wt), 1e-9, 1e-11)
+
+
+def test_grad_matches_oracle_fp64_k2_identity_subspace():
+    p = problem(seed=synth.SEED_BASE + 12, H=30, W=36, L_l=4, L_h=1, d=3, blur_size=7, K=2, S=1,
+                E_identity=True, kind="pansharpen")
+    om = weights64(p)
+    Wt = np.random.default_rng(8).standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f64", "f64", om)
+    compare(gpu_grad(f, yl, yh, 5, Wt), oracle_grad(p, 5, om, Wt), 1e-9, 1e-11)
+
+
+def test_grad_matches_oracle_fp32():
+    p = problem()
+    om = weights64(p).astype(np.float32).astype(np.float64)
+    Wt = np.random.default_rng(9).standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f32", "f32", om)
+    compare(gpu_grad(f, yl, yh, 6, Wt), oracle_grad(p, 6, om, Wt), 2e-3, 1e-5)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_checkpoint_segments_bitwise(dtype):
+    # recomputation from saved segment states reproduces the taped run exactly
+    p = problem()
+    om = weights64(p)
+    Wt = np.random.default_rng(10).standard_normal((p.L_s, p.H, p.W))
+    out = []
+    for seg in (0, 2, 3):
+        f, yl, yh = context(p, dtype, dtype, om, opts=((FUSE_OPT_GRAD_SEGMENT, seg),))
+        out.append(gpu_grad(f, yl, yh, 7, Wt))
+    for o in out[1:]:
+        for a, b in zip(o[:3], out[0][:3]):
+            assert np.array_equal(a, b)
+        assert o[3] == out[0][3]
+
+
+def test_zbar_path():
+    p = problem()
+    om = weights64(p)
+    rng = np.random.default_rng(11)
+    Wx = rng.standard_normal((p.L_s, p.H, p.W))
+    Wz = rng.standard_normal((p.L_l, p.H, p.W))
+    f, yl, yh = context(p, "f64", "f64", om)
+    f.grad_forward(yl, yh, 5)
+    gl, gh, pr = f.grad_backward(Xbar=torch.tensor(Wx, device="cuda"), Zbar=torch.tensor(Wz, device="cuda"))
+    # Z = X E  =>  dL/dX = Wx + Wz E^T
+    Wt = Wx + np.einsum("lhw,cl->chw", Wz, p.E)
+    _, glo, gho, go = oracle_grad(p, 5, om, Wt)
+    assert rel(gl.cpu().numpy(), glo) <= 1e-9
+    assert rel(gh.cpu().numpy(), gho) <= 1e-9
+    assert abs(pr["rho"] - go["rho"]) <= 1e-9 * abs(go["rho"])
+
+
+def test_repeated_backward_is_linear():
+    p = problem()
+    om = weights64(p)
+    rng = np.random.default_rng(12)
+    A = torch.tensor(rng.standard_normal((p.L_s, p.H, p.W)), device="cuda")
+    B = torch.tensor(rng.standard_normal((p.L_s, p.H, p.W)), device="cuda")
+    f, yl, yh = context(p, "f64", "f64", om)
+    f.grad_forward(yl, yh, 5)
+    ga = f.grad_backward(Xbar=A)
+    gb = f.grad_backward(Xbar=B)
+    gab = f.grad_backward(Xbar=A + B)
+    for q in range(2):
+        assert rel((ga[q] + gb[q]).cpu().numpy(), gab[q].cpu().numpy()) <= 1e-12
+    for k in ("lam1", "lam2", "rho"):
+        assert abs(ga[2][k] + gb[2][k] - gab[2][k]) <= 1e-10 * max(1.0, abs(gab[2][k]))
+
+
+def test_autograd_function():
+    p = problem()
+    om = weights64(p)
+    Wt = torch.tensor(np.random.default_rng(13).standard_normal((p.L_s, p.H, p.W)), device="cuda")
+    f, yl, yh = context(p, "f64", "f64", om)
+    yl.requires_grad_(True)
+    yh.requires_grad_(True)
+    params = f.params().requires_grad_(True)
+    X = f.unrolled(yl, yh, 5, params)
+    loss = (X * Wt).sum()
+    loss.backward()
+    f2, yl2, yh2 = context(p, "f64", "f64", om)
+    X2 = f2.grad_forward(yl2, yh2, 5)
+    gl, gh, pr = f2.grad_backward(Xbar=Wt)
+    assert torch.equal(X.detach(), X2)
+    assert torch.equal(yl.grad, gl) and torch.equal(yh.grad, gh)
+    assert params.grad.tolist() == [pr["lam1"], pr["lam2"], pr["rho"]]
+    with pytest.raises(ValueError):
+        f.unrolled(yl, yh, 5, params.detach() * 1.5)
+
+
+def test_one_iteration_has_zero_gradient():
+    # X of the first iteration solves A X = 0 from the zero state
+    p = problem()
+    om = weights64(p)
+    Wt = np.ones((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f64", "f64", om)
+    X, gl, gh, pr = gpu_grad(f, yl, yh, 1, Wt)
+    assert not X.any() and not gl.any() and not gh.any()
+    assert pr == dict(lam1=0.0, lam2=0.0, rho=0.0)
+
+
+def test_central_differences_of_the_gpu_forward():
+    # independent of the oracle: FP64 GPU solves at perturbed inputs and parameters
+    p = problem(seed=synth.SEED_BASE + 13, H=24, W=24, d=2, S=1)
+    om = weights64(p)
+    iters = 6
+    rng = np.random.default_rng(14)
+    Wt = rng.standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f64", "f64", om)
+    _, gl, gh, pr = gpu_grad(f, yl, yh, iters, Wt)
+
+    def loss(q, dyl=0.0, dyh=0.0):
+        g, a, b = context(q, "f64", "f64", om)
+        X, _ = g.solve(a + dyl, b + dyh, iters)
+        return float((X.cpu().numpy() * Wt).sum())
+
+    # a step small enough that no clamp decision flips inside it on these seeds (C-16 reading)
+    h = 1e-8
+    for key, grad in (("Yl", gl), ("Yh", gh)):
+        d = rng.standard_normal(grad.shape)
+        dt = torch.tensor(h * d, device="cuda")
+        fd = (loss(p, **{("dyl" if key == "Yl" else "dyh"): dt}) -
+              loss(p, **{("dyl" if key == "Yl" else "dyh"): -dt})) / (2 * h)
+        an = float((grad * d).sum())
+        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (key, fd, an)
+    import dataclasses
+    for key in ("lam1", "lam2", "rho"):
+        v = getattr(p, key)
+        hp = 1e-6 * v
+        fd = (loss(dataclasses.replace(p, **{key: v + hp})) - loss(dataclasses.replace(p, **{key: v - hp}))) / (2 * hp)
+        assert abs(fd - pr[key]) <= 1e-5 * max(1e-3, abs(pr[key])), (key, fd, pr[key])
+
+
+def test_errors():
+    p = problem()
+    om = weights64(p)
+    f, yl, yh = context(p, "f64", "f64", om)
+    xb = torch.zeros((p.L_s, p.H, p.W), dtype=torch.float64, device="cuda")
+    with pytest.raises(FuseError) as e:
+        f.grad_backward(Xbar=xb)
+    assert e.value.status == FUSE_ESTATE
+    fuse_reset_error(f.ctx)                 # errors are sticky until reset
+    f.grad_forward(yl, yh, 3)
+    with pytest.raises(FuseError) as e:
+        f.grad_backward()
+    assert e.value.status == FUSE_EINVAL
+    fuse_reset_error(f.ctx)
+    f.solve(yl, yh, 2)                      # changes the state: the checkpoints are stale
+    with pytest.raises(FuseError) as e:
+        f.grad_backward(Xbar=xb)
+    assert e.value.status == FUSE_ESTATE
+    fuse_reset_error(f.ctx)
+    f.grad_forward(yl, yh, 3)
+    f.grad_backward(Xbar=xb)
+
+
+def test_unrolled_workload_full_size():
+    # the unrolled-forward workload (256 x 256, L_s 8, 20 iterations) in its benchmark precision
+    p, meta = synth.workload("unrolled_256")
+    from oracle import cloops
+    om = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    om32 = om.astype(np.float32).astype(np.float64)
+    Wt = np.random.default_rng(15).standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, meta["dtype"], meta["wdtype"], om32)
+    compare(gpu_grad(f, yl, yh, p.iters, Wt), oracle_grad(p, p.iters, om32, Wt), 2e-3, 1e-5)
