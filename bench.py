@@ -32,9 +32,9 @@ METRIC = "ADMM throughput (megapixel*band*iter/s)"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch, from the
 # ncu capture summarised in profiles/latent_tma_kernel_hsms128.md (128x128 case, the same kernel
-# and launch shape), scaled to the workload by its pixel count (the traffic is proportional to
-# it).  Must be re-measured whenever the latent kernel changes.
-LATENT_TRAFFIC_PER_PIXEL = {}
+# and launch shape), per pixel; scaled to the workload by its pixel count (the traffic is
+# proportional to it).  Must be re-measured whenever the latent kernel changes.
+LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.676864e6 + 739.627264e6) / (128 * 128)}
 UNIT = "Mpx*band*iter/s"
 
 
@@ -49,6 +49,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-FP32 comparison")
+    ap.add_argument("--no-grad", action="store_true", help="skip the reverse-pass measurement")
+    ap.add_argument("--grad-only", action="store_true", help="only the reverse-pass measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -389,6 +392,80 @@ def run_batch(a, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def grad_bench(a, rank):
+    """Forward with checkpoints and reverse pass (fuse_grad_forward / fuse_grad_backward) of the
+    unrolled-forward workload (256 x 256, 31 bands, L_s 8, 3x3 patches, 3x3 search, 20
+    iterations, FP32), loss <Wt, X_K> with a seeded Wt; against a plain fuse_solve of the same
+    iterations and the oracle's FP64 reverse pass timed on a 32 x 32 crop."""
+    import torch
+    from oracle import grad as ograd, nlpr
+    from paper_2210_04184_gb300 import synth
+    from paper_2210_04184_gb300.fuse import Fusion, fuse_grad_bytes
+    p, meta = _workload("unrolled_256", rank, None)
+    td = torch.float32
+    f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
+    yl = torch.tensor(p.Yl, dtype=td, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=td, device="cuda")
+    Wt = torch.tensor(np.random.default_rng(17).standard_normal((p.L_s, p.H, p.W)), dtype=td, device="cuda")
+    f.weights(yh)
+    st = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(max(3, a.warmup)):
+        f.grad_forward(yl, yh, p.iters)
+        f.grad_backward(Xbar=Wt)
+        f.solve(yl, yh, p.iters, want_X=False)
+    torch.cuda.synchronize()
+    fwd, bwd, plain = [], [], []
+    for _ in range(max(1, a.steps)):
+        e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
+        e0.record(st)
+        f.grad_forward(yl, yh, p.iters)
+        e1.record(st)
+        f.grad_backward(Xbar=Wt)            # includes the host read of the parameter sums
+        e2.record(st)
+        e3.record(st)
+        f.solve(yl, yh, p.iters, want_X=False)
+        e4.record(st)
+        torch.cuda.synchronize()
+        fwd.append(e0.elapsed_time(e1)); bwd.append(e1.elapsed_time(e2)); plain.append(e3.elapsed_time(e4))
+    fm, bm, pm = statistics.median(fwd), statistics.median(bwd), statistics.median(plain)
+    units = p.H * p.W / 1e6 * p.L_s * p.iters
+    out = {"workload": "unrolled_256", "H": p.H, "W": p.W, "bands": p.L_l, "L_s": p.L_s,
+           "patch": f"{2 * p.K + 1}x{2 * p.K + 1}", "search": f"{2 * p.S + 1}x{2 * p.S + 1}",
+           "iters": p.iters, "dtype": "f32", "weights": meta["wdtype"],
+           "ms_forward_with_tape": fm, "ms_backward": bm, "ms_plain_forward": pm,
+           "value_forward_backward": units / ((fm + bm) / 1e3), "unit": UNIT,
+           "backward_over_plain_forward": bm / pm, "workspace_bytes": fuse_grad_bytes(f.ctx, p.iters)}
+    f.close()
+    if rank == 0 and not a.no_cpu_baseline:
+        # the oracle as it stands, the workload's 20 iterations on a square crop: 64 x 64, or
+        # 128 x 128 when the 64 x 64 run took under 3 s (a sample of several seconds)
+        spec = dict(synth.WORKLOADS["unrolled_256"])
+        for k in ("dtype", "wdtype", "cfg", "iters", "H", "W"):
+            spec.pop(k)
+        iters = p.iters
+
+        def run(crop):
+            q = synth.make_problem(H=crop, W=crop, seed=1, **spec)
+            om = nlpr.weights(nlpr.to_hwl(q.Yh), q.K, q.S, q.h)
+            Wq = np.random.default_rng(0).standard_normal((crop, crop, q.L_s))
+            t0 = time.perf_counter()
+            ograd.unrolled_grad(nlpr.to_hwl(q.Yl), nlpr.to_hwl(q.Yh), q.blur, q.d, q.R, q.E, q.K, q.S, q.lam1,
+                                q.lam2, q.rho, om, iters, lambda X: Wq)
+            return time.perf_counter() - t0, q
+
+        crop = 64
+        dt, q = run(crop)
+        if dt < 3.0:
+            crop = 128
+            dt, q = run(crop)
+        out["cpu_baseline"] = {"value": crop * crop / 1e6 * q.L_s * iters / dt, "unit": UNIT, "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{crop}x{crop} crop, forward tape + reverse pass of {iters} "
+                                         f"iterations, FP64 NumPy, {dt:.1f}s"}
+    return out
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -412,7 +489,15 @@ def run_ours(a, rank, world, local_rank):
     from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream
     fuse_set_stream(f.ctx, stream.cuda_stream)
     fuse_weights(f.ctx, yh.data_ptr())
-    tuned = f.autotune(yl, yh, iters=2)            # launch shapes only; results are unchanged
+    if a.no_autotune:
+        from paper_2210_04184_gb300.fuse import (fuse_get_option, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES,
+                                                 FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS)
+        tuned = {k: fuse_get_option(f.ctx, v) for k, v in
+                 (("latent_threads", FUSE_OPT_LATENT_THREADS), ("latent_stages", FUSE_OPT_LATENT_STAGES),
+                  ("latent_bands", FUSE_OPT_LATENT_BANDS), ("fft_rows", FUSE_OPT_FFT_ROWS),
+                  ("fft_cols", FUSE_OPT_FFT_COLS))}
+    else:
+        tuned = f.autotune(yl, yh, iters=2)        # launch shapes only; results are unchanged
 
     def step():
         fuse_weights(f.ctx, yh.data_ptr())
@@ -477,6 +562,9 @@ def run_ours(a, rank, world, local_rank):
     fp64 = None
     if not a.no_fp64 and meta["dtype"] == "f32":
         fp64 = fp64_compare(p, meta, f, yl, yh, Z)
+    grad = None
+    if not a.no_grad and rank == 0 and a.workload == "hsms_256":
+        grad = grad_bench(a, rank)
 
     if rank != 0:
         if dist:
@@ -506,6 +594,7 @@ def run_ours(a, rank, world, local_rank):
         "clocks": clk,
         "e2e": e2e,
         "fp64_compare": fp64,
+        "grad": grad,
     }
     if not a.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(p)
@@ -522,6 +611,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+    elif a.grad_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_2210_04184_gb300 import build as _build
+        _build.build()
+        out = grad_bench(a, rank)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
     elif a.workload == "batch64":
         run_batch(a, rank, world, local_rank)
     else:

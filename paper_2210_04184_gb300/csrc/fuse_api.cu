@@ -93,7 +93,15 @@ struct fuse_ctx {
     long long epoch = 0;
     // host FP64 copies of (E E^T + rho I)^{-1}, F and E R, for the parameter derivatives
     std::vector<double> hM1, hF, hER;
+    // latent state read / written by the next latent launch (NULL = Sig, in place); set only
+    // around directly launched iterations of the taped forward, never while capturing
+    void *lat_in = nullptr, *lat_out = nullptr;
 };
+
+namespace {
+inline void* lat_src(const fuse_ctx* c) { return c->lat_in ? c->lat_in : c->Sig; }
+inline void* lat_dst(const fuse_ctx* c) { return c->lat_out ? c->lat_out : c->Sig; }
+}  // namespace
 
 namespace {
 
@@ -363,7 +371,8 @@ struct Impl {
     }
     template <typename WT>
     static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb) {
-        return LatentArgs<T, WT>{(const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W,
+        return LatentArgs<T, WT>{(const T*)c->X, (const WT*)c->omega, (const T*)lat_src(c), (T*)lat_dst(c),
+                                 (T*)c->planes, c->H, c->W,
                                  c->Ls, c->S, Ty, ncons, D, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit,
                                  c->half, bpb};
     }
@@ -457,7 +466,7 @@ struct Impl {
         dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
         with_k(c->K, [&](auto k) {
             latent_kernel<T, WT, decltype(k)::value, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
-                (const T*)c->X, (const WT*)c->omega, (T*)c->Sig, (T*)c->planes, c->H, c->W, c->Ls, c->S,
+                (const T*)c->X, (const WT*)c->omega, (const T*)lat_src(c), (T*)lat_dst(c), (T*)c->planes, c->H, c->W, c->Ls, c->S,
                 c->lat_Ty, (T)(c->lam2 / c->rho), c->half);
         });
     }

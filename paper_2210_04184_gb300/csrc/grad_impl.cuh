@@ -305,17 +305,23 @@ struct GradImpl {
     }
 };
 
-// One forward iteration with the tape slot filled: the entering Lambda1, Lambda2, Sigma before,
-// X after.
-fuse_status taped_iteration(fuse_ctx* c, int slot) {
+// One directly launched forward iteration in tape slot `slot` of a segment of `len` iterations.
+// The entering Lambda1, Lambda2 are copied to the slot and X after the iteration; the latent
+// pass reads Sigma from the slot and writes the next slot (the context's state after the
+// segment's last iteration), so taping Sigma costs no extra pass over it.
+fuse_status taped_iteration(fuse_ctx* c, int slot, int len) {
     GradWork* g = c->gw;
     const size_t img = c->n * c->Ls * c->esz;
     CK(c, cudaMemcpyAsync((char*)g->tL1 + (size_t)slot * img, c->Lam1, img, cudaMemcpyDeviceToDevice, c->stream));
     CK(c, cudaMemcpyAsync((char*)g->tL2 + (size_t)slot * img, c->Lam2, img, cudaMemcpyDeviceToDevice, c->stream));
-    CK(c, cudaMemcpyAsync((char*)g->tSig + (size_t)slot * c->sig_bytes, c->Sig, c->sig_bytes,
-                          cudaMemcpyDeviceToDevice, c->stream));
-    fuse_status st = run_iterations(c, 1);
+    c->lat_in = (char*)g->tSig + (size_t)slot * c->sig_bytes;
+    c->lat_out = slot + 1 < len ? (char*)g->tSig + (size_t)(slot + 1) * c->sig_bytes : c->Sig;
+    fuse_status st = c->dtype == FUSE_F64 ? Impl<double>::iterate(c, c->stream, false)
+                                          : Impl<float>::iterate(c, c->stream, false);
+    c->lat_in = c->lat_out = nullptr;
     if (st != FUSE_OK) return st;
+    c->launches_all += 7;
+    c->launches_latent += 1;
     CK(c, cudaMemcpyAsync((char*)g->tX + (size_t)slot * img, c->X, img, cudaMemcpyDeviceToDevice, c->stream));
     return FUSE_OK;
 }
@@ -334,6 +340,26 @@ fuse_status checkpoint_copy(fuse_ctx* c, int j, bool save) {
     return FUSE_OK;
 }
 
+// Runs segment j from the context's current state (which must be the state entering it),
+// filling the tape; `save` also stores that state as the segment's checkpoint.
+fuse_status run_segment(fuse_ctx* c, int j, bool save) {
+    GradWork* g = c->gw;
+    const int s0 = j * g->seg;
+    const int len = std::min(g->seg, g->iters - s0);
+    fuse_status st;
+    if (save && j > 0) {
+        st = checkpoint_copy(c, j, true);
+        if (st != FUSE_OK) return st;
+    }
+    if (j == 0) CK(c, cudaMemsetAsync(g->tSig, 0, c->sig_bytes, c->stream));
+    else CK(c, cudaMemcpyAsync(g->tSig, c->Sig, c->sig_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 0; k < len; ++k) {
+        st = taped_iteration(c, k, len);
+        if (st != FUSE_OK) return st;
+    }
+    return FUSE_OK;
+}
+
 fuse_status grad_forward_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, void* Xo) {
     fuse_status st = grad_prepare(c, iters);
     if (st != FUSE_OK) return st;
@@ -341,12 +367,8 @@ fuse_status grad_forward_impl(fuse_ctx* c, const void* Yl, const void* Yh, int i
     st = solve_impl(c, Yl, Yh, 0, 0, nullptr, nullptr);
     if (st != FUSE_OK) return st;
     GradWork* g = c->gw;
-    for (int t = 0; t < iters; ++t) {
-        if (t > 0 && t % g->seg == 0) {
-            st = checkpoint_copy(c, t / g->seg, true);
-            if (st != FUSE_OK) return st;
-        }
-        st = taped_iteration(c, t % g->seg);
+    for (int j = 0; j < g->nseg && iters > 0; ++j) {
+        st = run_segment(c, j, true);
         if (st != FUSE_OK) return st;
     }
     c->have_x = true;
@@ -393,10 +415,8 @@ fuse_status grad_backward_t(fuse_ctx* c, const void* Xbar, const void* Zbar, voi
             if (j == 0) st = zero_state(c, s);
             else st = checkpoint_copy(c, j, false);
             if (st != FUSE_OK) return st;
-            for (int t = s0; t < e0; ++t) {
-                st = taped_iteration(c, t - s0);
-                if (st != FUSE_OK) return st;
-            }
+            st = run_segment(c, j, false);
+            if (st != FUSE_OK) return st;
             recomputed = true;
         }
         for (int t = e0 - 1; t >= s0; --t) {

@@ -72,9 +72,10 @@ latent_bwd_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T
         Rm[j] = active ? Rc[(size_t)y * W + x0 + j] : T(0);
         A[j] = T(0);
     }
-    double smu = 0.0;
+    double smu = 0.0;                                 // FP64 only across offsets (few adds)
     for (int jt = 0; jt < nt2; ++jt) {
         const int t2 = tm.t2_of(t1, jt);
+        T smu_t = T(0);
         T Hacc[VEC];
 #pragma unroll
         for (int j = 0; j < VEC; ++j) Hacc[j] = T(0);
@@ -97,27 +98,33 @@ latent_bwd_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T
                 T w[VEC + 2 * K];
 #pragma unroll
                 for (int j = 0; j < VEC + 2 * K; ++j) w[j] = (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W));
+                // issue the 2(2K+1) state loads of this patch row before any arithmetic or store
+                vecT<T, VEC> s_in[PS], s_b[PS];
+                const size_t row0 = (size_t)((k1 + K) * PS) * vstride;
 #pragma unroll
                 for (int k2 = 0; k2 < PS; ++k2) {
-                    const size_t off = (size_t)((k1 + K) * PS + k2) * vstride;
-                    const vecT<T, VEC> s_in = si[off];
-                    vecT<T, VEC> s_b = sb[off];
+                    s_in[k2] = ld_stream(si + row0 + (size_t)k2 * vstride);
+                    s_b[k2] = ld_stream(sb + row0 + (size_t)k2 * vstride);
+                }
+#pragma unroll
+                for (int k2 = 0; k2 < PS; ++k2) {
 #pragma unroll
                     for (int j = 0; j < VEC; ++j) {
-                        const T v = delta[j] - s_in.v[j];
+                        const T v = delta[j] - s_in[k2].v[j];
                         const T wt = w[j + k2];
                         const bool inside = (v < T(0) ? -v : v) < coef * wt;
-                        const T vb = inside ? -(gb[j] + s_b.v[j]) : gb[j];
+                        const T vb = inside ? -(gb[j] + s_b[k2].v[j]) : gb[j];
                         if (!inside && v != T(0)) {
-                            const T mb = -(s_b.v[j] + T(2) * gb[j]);
-                            smu += (double)(v > T(0) ? mb * wt : -mb * wt);
+                            const T mb = -(s_b[k2].v[j] + T(2) * gb[j]);
+                            smu_t += v > T(0) ? mb * wt : -mb * wt;
                         }
                         Hacc[j] += vb;
-                        s_b.v[j] = -vb;
+                        s_b[k2].v[j] = -vb;
                     }
-                    sb[off] = s_b;
+                    st_stream(sb + row0 + (size_t)k2 * vstride, s_b[k2]);
                 }
             }
+            smu += (double)smu_t;
         }
         if (valid) {
 #pragma unroll
@@ -182,6 +189,7 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double q[3] = {0.0, 0.0, 0.0};
     if (p < n) {
+        T q0 = T(0), q1 = T(0), q2 = T(0);            // per pixel in T, FP64 across pixels
         T pb[MAXLS], a[MAXLS], wb[MAXLS];
 #pragma unroll
         for (int j = 0; j < MAXLS; ++j) {
@@ -205,9 +213,9 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
                     }
                 }
                 const T d9b = g.D9b[(size_t)i * n + p];
-                q[0] += (double)(a[i] * kr);
-                q[1] += (double)(a[i] * kl);
-                q[2] += (double)(ab * d9b);
+                q0 += a[i] * kr;
+                q1 += a[i] * kl;
+                q2 += ab * d9b;
                 const T w2b = wb[i] + ab;
                 g.Xp[(size_t)i * n + p] = w2b;
                 g.L2b[(size_t)i * n + p] = -w2b;
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
                         }
                     }
                     const T a1 = g.rho * a[i] + g.D9a[(size_t)i * nl + pl];
-                    q[0] += (double)(a1 * km) + (double)(ab * a[i]);
+                    q0 += a1 * km + ab * a[i];
                     const T w1b = wb[i] + g.rho * ab;
                     g.BXb[(size_t)i * n + p] = w1b;
                     g.L1b[(size_t)i * n + p] = -w1b;
@@ -256,6 +264,9 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
                 }
             }
         }
+        q[0] = (double)q0;
+        q[1] = (double)q1;
+        q[2] = (double)q2;
     }
     block_sum<3, true>(q, g.part + (size_t)blockIdx.x * 3);
 }

@@ -36,7 +36,7 @@ namespace fuse {
 
 template <typename T, typename WT, int K, int VEC>
 __global__ void __launch_bounds__(256)
-latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restrict__ Sig,
+latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* Sig, T* Sout,
               T* __restrict__ planes, int H, int W, int Ls, int S, int Ty, T coef, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Hs = reinterpret_cast<T*>(smem_raw);           // [(2S+1)][Ty][W]
@@ -73,8 +73,9 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
 #pragma unroll
             for (int j = 0; j < VEC; ++j) delta[j] = Xm[j] - Xc[(size_t)ys * W + wrap1(x0 + j - t2, W)];
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
-            vecT<T, VEC>* sp = reinterpret_cast<vecT<T, VEC>*>(
-                Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0);
+            const size_t soff = ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + (size_t)y * W + x0;
+            const vecT<T, VEC>* sp = reinterpret_cast<const vecT<T, VEC>*>(Sig + soff);
+            vecT<T, VEC>* so = reinterpret_cast<vecT<T, VEC>*>(Sout + soff);
             const size_t vstride = kstride / VEC;
 #pragma unroll
             for (int k1 = -K; k1 <= K; ++k1) {
@@ -98,9 +99,10 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, T* __restri
                         Hacc[j] += T(2) * s2 - u;                  // G = v + 2 Sigma'
                         s[k2].v[j] = s2;
                     }
-                    st_stream(sp + (size_t)k2 * vstride, s[k2]);
+                    st_stream(so + (size_t)k2 * vstride, s[k2]);
                 }
                 sp += (size_t)PS * vstride;
+                so += (size_t)PS * vstride;
             }
         }
 #pragma unroll
@@ -149,7 +151,8 @@ template <typename T, typename WT>
 struct LatentArgs {
     const T* X;
     const WT* omega;
-    T* Sig;
+    const T* Sig;       // state read (bulk copies)
+    T* Sout;            // state written: Sig itself, or another buffer of the same layout
     T* planes;
     int H, W, Ls, S, Ty, ncons, D;
     T coef;
@@ -172,7 +175,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                                                 unsigned char* smem_tma) {
     const T* __restrict__ X = args.X;
     const WT* __restrict__ omega = args.omega;
-    T* __restrict__ Sig = args.Sig;
+    const T* Sig = args.Sig;
+    T* Sout = args.Sout;
     T* __restrict__ planes = args.planes;
     const int H = args.H, W = args.W, Ls = args.Ls, S = args.S, Ty = args.Ty, ncons = args.ncons, D = args.D;
     const T coef = args.coef;
@@ -281,7 +285,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 delta[j] = active ? Xm[j] - Xc[xsrow + wrap1(x0 + j - t2, W)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
-            T* gp = Sig + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
+            T* gp = Sout + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
 #pragma unroll
             for (int k1 = 0; k1 < PS; ++k1) {
                 T mu[VEC + 2 * K];
