@@ -1,8 +1,8 @@
 """FP64 reverse pass of K unrolled ADMM iterations (TEST INFRASTRUCTURE ONLY; see nlpr.py).
 
 Given dL/dX for the X of the last iteration, returns the gradients of L with respect to Y_l,
-Y_h, lambda1, lambda2 and rho through the whole unrolled ADMM of Sec. IV from zero
-initialisation.  Written on the oracle's own variables (P1, Lambda1, P2, Lambda2, Q, Sigma):
+Y_h, lambda1, lambda2, rho and the weights omega through the whole unrolled ADMM of Sec. IV from
+zero initialisation; weights_vjp carries dL/domega back to the guide through eq. wts.  Written on the oracle's own variables (P1, Lambda1, P2, Lambda2, Q, Sigma):
 each update of Sec. IV is differentiated as printed, in reverse order:
 
   Sigma' = Sigma - (D X - Q')          (eq. dualvar3_main)
@@ -56,6 +56,7 @@ def backward(tape, su: nlpr.Setup, Yl, Yh, Xbar_last):
     M1b = np.zeros((Ls, Ls))
     rho_b = 0.0
     S_mu = 0.0                                   # sum mubar * omega
+    omega_b = np.zeros_like(su.omega)            # dL/domega (mu = lambda2 omega / rho)
     last = len(tape) - 1
     for t in range(last, -1, -1):
         st, X = tape[t]
@@ -87,6 +88,7 @@ def backward(tape, su: nlpr.Setup, Yl, Yh, Xbar_last):
                     vb = Qpb[ti, ki] * outside
                     mub = (-Qpb[ti, ki] * np.sign(v) * outside).sum(axis=2)
                     S_mu += float((mub * su.omega[ti]).sum())
+                    omega_b[ti] += mub * (lam2 / rho)
                     Xb += nlpr.diff_op_t(vb, tau, k)
                     Sig_in_b[ti, ki] -= vb
             # P2' = a2 F
@@ -138,7 +140,22 @@ def backward(tape, su: nlpr.Setup, Yl, Yh, Xbar_last):
     g["lam1"] = lam1_b
     g["Yh"] = (lam1 / rho) * nlpr.img(nlpr.mat(D9bb) @ G, H, W)           # (H, W, L_h)
     g["Yl"] = nlpr.img(nlpr.mat(nlpr.decimate(D9ab, su.d)) @ su.E, H // su.d, W // su.d)
+    g["omega"] = omega_b                                                     # (|W|, H, W)
     return g
+
+
+def weights_vjp(G, K, S, h, omega_bar):
+    """dL/dG (H, W, L_guide) for a loss that depends on the guide G only through
+    omega = nlpr.weights(G, K, S, h) (eq. wts), given dL/domega (|W|, H, W):
+      omega_tau(i) = exp(-dist_tau(i) / h^2),  dist_tau(i) = sum_k ||D_{tau k} G(i)||^2,
+      dL/dG = sum_tau sum_k D_{tau k}^T ( -2/h^2 omega_bar_tau omega_tau  D_{tau k} G )."""
+    omega = nlpr.weights(G, K, S, h)
+    Gb = np.zeros_like(G)
+    for t, tau in enumerate(nlpr.search_offsets(S)):
+        a = (-2.0 / (h * h)) * omega_bar[t] * omega[t]
+        for k in nlpr.patch_offsets(K):
+            Gb += nlpr.diff_op_t(a[:, :, None] * nlpr.diff_op(G, tau, k), tau, k)
+    return Gb
 
 
 def unrolled_grad(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, Xbar_fn):

@@ -70,3 +70,46 @@ def test_reverse_pass_with_identity_subspace_and_no_decimation():
             an = g[key]
         fd = (_loss(qp, Wt, iters) - _loss(qm, Wt, iters)) / (2 * h)
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (key, fd, an)
+
+
+def test_weight_and_guide_gradients_match_central_differences():
+    # omega enters only through mu = lambda2 omega / rho; the guide only through omega (eq. wts)
+    p = _tiny(45)
+    rng = np.random.default_rng(46)
+    Wt = rng.standard_normal((6, 8, 2))
+    iters = 4
+    G = rng.random((6, 8, 2))                       # a guide other than Y_h
+    h_w = 0.5
+    p["omega"] = nlpr.weights(G, p["K"], p["S"], h_w)
+    X, g = grad.unrolled_grad(p["Yl"], p["Yh"], p["kern"], p["d"], p["R"], p["E"], p["K"], p["S"], p["lam1"],
+                              p["lam2"], p["rho"], p["omega"], iters, lambda X: Wt)
+    h = 1e-6
+    d_om = rng.standard_normal(p["omega"].shape)
+    qp = dict(p); qp["omega"] = p["omega"] + h * d_om
+    qm = dict(p); qm["omega"] = p["omega"] - h * d_om
+    fd = (_loss(qp, Wt, iters) - _loss(qm, Wt, iters)) / (2 * h)
+    an = float((g["omega"] * d_om).sum())
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+    # <omega_bar, omega> = lambda2 dL/dlambda2 (mu depends on lambda2 omega only)
+    assert abs(float((g["omega"] * p["omega"]).sum()) - p["lam2"] * g["lam2"]) <= 1e-9 * max(1.0, abs(an))
+    Gb = grad.weights_vjp(G, p["K"], p["S"], h_w, g["omega"])
+    d_g = rng.standard_normal(G.shape)
+    qp = dict(p); qp["omega"] = nlpr.weights(G + h * d_g, p["K"], p["S"], h_w)
+    qm = dict(p); qm["omega"] = nlpr.weights(G - h * d_g, p["K"], p["S"], h_w)
+    fd = (_loss(qp, Wt, iters) - _loss(qm, Wt, iters)) / (2 * h)
+    an = float((Gb * d_g).sum())
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+def test_weights_vjp_matches_central_differences_of_the_weights():
+    # the guide step alone: L = <V, omega(G)> for a random V
+    rng = np.random.default_rng(47)
+    G = rng.random((7, 9, 2))
+    K, S, hw = 1, 2, 0.7
+    V = rng.standard_normal((len(nlpr.search_offsets(S)), 7, 9))
+    Gb = grad.weights_vjp(G, K, S, hw, V)
+    d = rng.standard_normal(G.shape)
+    e = 1e-6
+    fd = (float((V * nlpr.weights(G + e * d, K, S, hw)).sum()) -
+          float((V * nlpr.weights(G - e * d, K, S, hw)).sum())) / (2 * e)
+    assert abs(fd - float((Gb * d).sum())) <= 1e-7 * max(1.0, abs(fd))
