@@ -83,8 +83,11 @@ enum {
                                     2 in batches) */
     FUSE_OPT_FFT_ROWS = 9,       /* rows per block of the row FFT passes: 1, 2, 4 or 8 */
     FUSE_OPT_FFT_COLS = 10,      /* columns per block of the column FFT pass: power of 2 <= 32 */
-    FUSE_OPT_GRAD_SEGMENT = 11   /* iterations per checkpointed segment of fuse_grad_forward
+    FUSE_OPT_GRAD_SEGMENT = 11,  /* iterations per checkpointed segment of fuse_grad_forward
                                     (default 0: one segment, every iteration taped) */
+    FUSE_OPT_GRAD_WEIGHTS = 12   /* 1: fuse_grad_backward also accumulates dL/domega for
+                                    fuse_grad_weights (one more read of the state per reverse
+                                    iteration); default 0 */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -226,12 +229,13 @@ fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev, int H, int
 
 /* ---- Reverse pass (differentiation of K unrolled iterations) -----------------------------
  * The ADMM of Sec. IV run for a fixed number K of iterations from zero state is a
- * differentiable map (Y_l, Y_h, lambda1, lambda2, rho) -> X_K; the paper does not
- * differentiate it, these entry points do, by the exact adjoint of every update in reverse
- * order: the soft threshold of eq. Qj_main (derivative taken as 0 at |v| = mu), the closed
- * forms of eqs. Qm_update and Qh_update, the dual updates, and the X update of eq. inv (A is
- * symmetric, so its adjoint is the same per-frequency division).  The weights omega are held
- * fixed.
+ * differentiable map (Y_l, Y_h, lambda1, lambda2, rho, omega) -> X_K, with omega itself a
+ * function of the guide (eq. wts); the paper does not differentiate it, these entry points
+ * do, by the exact adjoint of every update in reverse order: the soft threshold of eq. Qj_main
+ * (derivative taken as 0 at |v| = mu), the closed forms of eqs. Qm_update and Qh_update, the
+ * dual updates, and the X update of eq. inv (A is symmetric, so its adjoint is the same
+ * per-frequency division).  fuse_grad_backward returns the data-path gradients;
+ * fuse_grad_weights the weight and guide gradients.
  *
  * Checkpointing: the forward keeps, for each of its iterations, X and the entering Lambda1,
  * Lambda2 and Sigma (the tape).  With FUSE_OPT_GRAD_SEGMENT = s > 0 the iterations are grouped
@@ -264,6 +268,23 @@ fuse_status fuse_grad_forward(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_
  * FUSE_ENONFINITE, FUSE_ECUDA. */
 fuse_status fuse_grad_backward(fuse_ctx* ctx, const void* Xbar_dev, const void* Zbar_dev,
                                void* Yl_bar_dev, void* Yh_bar_dev, double* param_bar);
+
+/* Weight and guide gradients of the last fuse_grad_backward, which must have run with
+ * FUSE_OPT_GRAD_WEIGHTS = 1 (else FUSE_ESTATE).  The weights enter the iterations only through
+ * the thresholds mu = lambda2 omega / rho (eq. Qj_main).
+ *   omega_bar_dev  nullable, device [|W|][H][W] of dtype: dL/domega for the weight array the
+ *                  context holds (fuse_weights / fuse_set_weights layout).  In half-window mode
+ *                  the solver reads only the kept offsets, whose weights also threshold their
+ *                  mirrors: their entries carry both, and the other offsets' entries are 0.
+ *   guide_dev      the guide given to fuse_weights, device [L_guide][H][W] of dtype (needed
+ *                  for guide_bar_dev only)
+ *   guide_bar_dev  nullable, device [L_guide][H][W] of dtype: dL/dguide through eq. wts,
+ *                  dL/dG = sum_tau sum_k D_{tau k}^T (-2/h^2 omega_bar omega D_{tau k} G).
+ *                  When the guide is Y_h, the full dL/dY_h is this plus fuse_grad_backward's
+ *                  Yh_bar (the data path).
+ * Asynchronous.  Errors: FUSE_ESTATE, FUSE_EINVAL (guide_bar without guide), FUSE_ENOMEM. */
+fuse_status fuse_grad_weights(fuse_ctx* ctx, void* omega_bar_dev, const void* guide_dev,
+                              void* guide_bar_dev);
 
 /* fuse_grad_forward followed by fuse_grad_backward. */
 fuse_status fuse_grad(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters,

@@ -89,7 +89,7 @@ struct fuse_ctx {
     // reverse pass: workspace, iterations per checkpointed segment (0 = one segment), a counter
     // bumped by every call that changes inputs or state (a taped forward is valid while unchanged)
     GradWork* gw = nullptr;
-    int grad_seg = 0;
+    int grad_seg = 0, grad_weights = 0;
     long long epoch = 0;
     // host FP64 copies of (E E^T + rho I)^{-1}, F and E R, for the parameter derivatives
     std::vector<double> hM1, hF, hER;
@@ -1330,6 +1330,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             if (value < 0 || value > (1 << 30)) return fail(c, FUSE_EINVAL, "iterations per segment must be >= 0");
             c->grad_seg = (int)value;
             return FUSE_OK;
+        case FUSE_OPT_GRAD_WEIGHTS: c->grad_weights = value != 0; return FUSE_OK;
         case FUSE_OPT_LATENT_BANDS:
             if (value < 1 || value > 64) return fail(c, FUSE_EINVAL, "bands per latent block must be in [1, 64]");
             c->lat_bpb = (int)value;
@@ -1521,6 +1522,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_FFT_ROWS: *value = c->fr_rpb; return FUSE_OK;
         case FUSE_OPT_FFT_COLS: *value = c->fc_cw; return FUSE_OK;
         case FUSE_OPT_GRAD_SEGMENT: *value = c->grad_seg; return FUSE_OK;
+        case FUSE_OPT_GRAD_WEIGHTS: *value = c->grad_weights; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }
@@ -1792,6 +1794,12 @@ fuse_status fuse_grad_backward(fuse_ctx* c, const void* Xbar, const void* Zbar, 
     if (st != FUSE_OK) return st;
     if (!Xbar && !Zbar) return fail(c, FUSE_EINVAL, "both dL/dX and dL/dZ are NULL");
     return grad_backward_impl(c, Xbar, Zbar, Yl_bar, Yh_bar, param_bar);
+}
+
+fuse_status fuse_grad_weights(fuse_ctx* c, void* omega_bar, const void* guide, void* guide_bar) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    return grad_weights_impl(c, omega_bar, guide, guide_bar);
 }
 
 fuse_status fuse_grad(fuse_ctx* c, const void* Yl, const void* Yh, int iters, const void* Xbar, const void* Zbar,

@@ -26,6 +26,10 @@ struct GradWork {
     void *Krho = nullptr, *Klam = nullptr, *Kmu = nullptr, *MhT = nullptr;
     double *lat_part = nullptr, *px_part = nullptr;
     size_t n_lat_part = 0, n_px_part = 0;
+    // dL/domega [|W|][H][W] (allocated when FUSE_OPT_GRAD_WEIGHTS is on) and the guide step's
+    // box sums; omb_valid: the last reverse pass accumulated omb
+    void *omb = nullptr, *Abox = nullptr;
+    bool omb_valid = false;
     std::vector<void*> allocs;
 };
 
@@ -246,6 +250,32 @@ struct GradImpl {
         });
     }
 
+    template <typename WT>
+    static void omega_bwd(fuse_ctx* c, cudaStream_t s, const void* Xt, const void* Sin) {
+        GradWork* g = c->gw;
+        const unsigned kept = (unsigned)(c->half ? c->nW / 2 : c->nW);
+        dim3 grid((unsigned)((c->n + 255) / 256), kept);
+        const T coef = (T)(c->lam2 / c->rho);
+        const T scale = (T)((c->half ? 2.0 : 1.0) * c->lam2 / c->rho);
+        with_k(c->K, [&](auto k) {
+            omega_bwd_kernel<T, WT, decltype(k)::value><<<grid, 256, 0, s>>>(
+                (const T*)Xt, (const WT*)c->omega, (const T*)Sin, (const T*)g->Sb, (const T*)g->Cb, (T*)g->omb,
+                c->H, c->W, c->Ls, c->S, coef, scale, c->half);
+        });
+    }
+
+    static fuse_status omega_bwd_any(fuse_ctx* c, cudaStream_t s, const void* Xt, const void* Sin) {
+        if constexpr (sizeof(T) == 8) {
+            omega_bwd<double>(c, s, Xt, Sin);
+        } else {
+            if (c->wdtype == FUSE_BF16) omega_bwd<__nv_bfloat16>(c, s, Xt, Sin);
+            else omega_bwd<float>(c, s, Xt, Sin);
+        }
+        c->launches_all++;
+        CKL(c, "omega_bwd_kernel");
+        return FUSE_OK;
+    }
+
     static fuse_status latent_bwd_any(fuse_ctx* c, cudaStream_t s, const void* Xt, const void* Sin) {
         if constexpr (sizeof(T) == 8) {
             latent_bwd<double>(c, s, Xt, Sin);
@@ -285,7 +315,12 @@ struct GradImpl {
         if (!last) {
             // X_0 = 0 and Sigma_0 = 0, so the first latent pass has v = 0 and no threshold term
             if (t > 0) {
-                st = latent_bwd_any(c, s, Xt, (const char*)g->tSig + (size_t)slot * c->sig_bytes);
+                const char* Sin = (const char*)g->tSig + (size_t)slot * c->sig_bytes;
+                if (c->grad_weights) {
+                    st = omega_bwd_any(c, s, Xt, Sin);          // reads Sigmabar' before it is overwritten
+                    if (st != FUSE_OK) return st;
+                }
+                st = latent_bwd_any(c, s, Xt, Sin);
                 if (st != FUSE_OK) return st;
             }
             st = stencil<0>(c, s, Xt, g->BXt, c->tapsB, nullptr, nullptr);
@@ -392,6 +427,14 @@ fuse_status grad_backward_t(fuse_ctx* c, const void* Xbar, const void* Zbar, voi
     CK(c, cudaMemsetAsync(g->Sb, 0, c->sig_bytes, s));
     CK(c, cudaMemsetAsync(g->L1b, 0, img, s));
     CK(c, cudaMemsetAsync(g->L2b, 0, img, s));
+    g->omb_valid = false;
+    if (c->grad_weights) {
+        if (!g->omb) {
+            st = galloc(c, g, &g->omb, (size_t)c->nW * c->n * c->esz);
+            if (st != FUSE_OK) return st;
+        }
+        CK(c, cudaMemsetAsync(g->omb, 0, (size_t)c->nW * c->n * c->esz, s));
+    }
     // dL/dX of the last iteration: Xbar + Zbar E^T (Z = X E)
     if (Zbar) {
         st = Impl<T>::band_mix(c, s, Zbar, g->Xb, c->Et, c->n, c->Ll, c->Ls);
@@ -424,6 +467,7 @@ fuse_status grad_backward_t(fuse_ctx* c, const void* Xbar, const void* Zbar, voi
             if (st != FUSE_OK) return st;
         }
     }
+    g->omb_valid = c->grad_weights != 0;
     if (recomputed) {
         // the context's state is now that of an earlier iteration
         c->have_state = false;
@@ -465,10 +509,61 @@ fuse_status grad_backward_impl(fuse_ctx* c, const void* Xbar, const void* Zbar, 
         if (Ylb) CK(c, cudaMemsetAsync(Ylb, 0, c->nl * c->Ll * c->esz, c->stream));
         if (Yhb) CK(c, cudaMemsetAsync(Yhb, 0, c->n * c->Lh * c->esz, c->stream));
         if (pbar) pbar[0] = pbar[1] = pbar[2] = 0.0;
+        g->omb_valid = false;
+        if (c->grad_weights) {
+            if (!g->omb) {
+                fuse_status st = galloc(c, g, &g->omb, (size_t)c->nW * c->n * c->esz);
+                if (st != FUSE_OK) return st;
+            }
+            CK(c, cudaMemsetAsync(g->omb, 0, (size_t)c->nW * c->n * c->esz, c->stream));
+            g->omb_valid = true;
+        }
         return FUSE_OK;
     }
     return c->dtype == FUSE_F64 ? grad_backward_t<double>(c, Xbar, Zbar, Ylb, Yhb, pbar)
                                 : grad_backward_t<float>(c, Xbar, Zbar, Ylb, Yhb, pbar);
+}
+
+template <typename T>
+fuse_status guide_grad_t(fuse_ctx* c, const void* G, void* Gb) {
+    GradWork* g = c->gw;
+    cudaStream_t s = c->stream;
+    if (!g->Abox) {
+        fuse_status st = galloc(c, g, &g->Abox, (size_t)c->nW * c->n * c->esz);
+        if (st != FUSE_OK) return st;
+    }
+    const unsigned nb = (unsigned)((c->n + 255) / 256);
+    const T c2 = (T)(-2.0 / (c->h * c->h));
+    if constexpr (sizeof(T) == 8) {
+        guide_box_kernel<T, double><<<dim3(nb, (unsigned)c->nW), 256, 0, s>>>(
+            (const T*)g->omb, (const double*)c->omega, (T*)g->Abox, c->H, c->W, c->K, c2);
+    } else {
+        if (c->wdtype == FUSE_BF16)
+            guide_box_kernel<T, __nv_bfloat16><<<dim3(nb, (unsigned)c->nW), 256, 0, s>>>(
+                (const T*)g->omb, (const __nv_bfloat16*)c->omega, (T*)g->Abox, c->H, c->W, c->K, c2);
+        else
+            guide_box_kernel<T, float><<<dim3(nb, (unsigned)c->nW), 256, 0, s>>>(
+                (const T*)g->omb, (const float*)c->omega, (T*)g->Abox, c->H, c->W, c->K, c2);
+    }
+    CKL(c, "guide_box_kernel");
+    guide_bwd_kernel<T><<<dim3(nb, (unsigned)c->Lg), 256, 0, s>>>((const T*)G, (const T*)g->Abox, (T*)Gb, c->H,
+                                                                  c->W, c->S);
+    CKL(c, "guide_bwd_kernel");
+    c->launches_all += 2;
+    return FUSE_OK;
+}
+
+fuse_status grad_weights_impl(fuse_ctx* c, void* omega_bar, const void* G, void* Gb) {
+    GradWork* g = c->gw;
+    if (!g || !g->omb_valid) return fail(c, FUSE_ESTATE, "no reverse pass with FUSE_OPT_GRAD_WEIGHTS on");
+    if (omega_bar)
+        CK(c, cudaMemcpyAsync(omega_bar, g->omb, (size_t)c->nW * c->n * c->esz, cudaMemcpyDeviceToDevice,
+                              c->stream));
+    if (Gb) {
+        if (!G) return fail(c, FUSE_EINVAL, "the guide is needed for its gradient");
+        return c->dtype == FUSE_F64 ? guide_grad_t<double>(c, G, Gb) : guide_grad_t<float>(c, G, Gb);
+    }
+    return FUSE_OK;
 }
 
 }  // namespace

@@ -278,4 +278,115 @@ __global__ void __launch_bounds__(256) axpy_kernel(T* __restrict__ y, const T* _
         y[i] += x[i];
 }
 
+// Kept offset q (the state's offset index) -> (tau1, tau2): inverse of TauMap::s_index.
+__device__ __forceinline__ void tau_of_state_index(int q, int S, int half, int* t1, int* t2) {
+    const int side = 2 * S + 1;
+    if (half) {
+        if (q < S) { *t1 = 0; *t2 = q + 1; return; }
+        const int r = q - S;
+        *t1 = r / side + 1;
+        *t2 = r % side - S;
+        return;
+    }
+    const int cell = q >= (side * side) / 2 ? q + 1 : q;
+    *t1 = cell / side - S;
+    *t2 = cell % side - S;
+}
+
+// dL/domega of one reverse iteration, run before the latent reverse pass overwrites the state
+// adjoint.  mu = coef omega with coef = lambda2/rho, so for the output pixel i and offset tau
+//   omega_bar_tau(i) += scale sum_{k, c} mubar_{tau k c}(i),  scale = coef (x2 in half-window mode:
+//   the stored weight of a kept offset also thresholds its mirror),
+//   mubar = -(Sigmabar' + 2 Gbar) sign(v) outside the dead zone, 0 inside,
+// with v, Gbar as in the latent reverse pass, read at the re-indexed pixel m = i - k.
+// One thread per output pixel (coalesced over m for every (k, c)); grid (ceil(n/256), kept offsets).
+template <typename T, typename WT, int K>
+__global__ void __launch_bounds__(256)
+omega_bwd_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* __restrict__ Sin,
+                 const T* __restrict__ Sb, const T* __restrict__ Rb, T* __restrict__ omega_bar,
+                 int H, int W, int Ls, int S, T coef, T scale, int half) {
+    constexpr int PS = 2 * K + 1;
+    constexpr int NP = PS * PS;
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int q = blockIdx.y;
+    int t1, t2;
+    tau_of_state_index(q, S, half, &t1, &t2);
+    const TauMap tm{S, half};
+    const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+    const int wi = tm.w_index(t1, t2);
+    const T mu = coef * (T)wload(omega + (size_t)wi * n + p);
+    T acc = T(0);
+#pragma unroll
+    for (int k1 = -K; k1 <= K; ++k1) {
+        const int my = wrapn(y - k1, H);
+        const int sy = wrapn(my - t1, H);
+#pragma unroll
+        for (int k2 = -K; k2 <= K; ++k2) {
+            const int mx = wrapn(x - k2, W);
+            const int sx = wrapn(mx - t2, W);
+            const size_t m = (size_t)my * W + mx, ms = (size_t)sy * W + sx;
+            const size_t base = ((size_t)q * NP + (k1 + K) * PS + (k2 + K)) * Ls * n + m;
+            for (int c = 0; c < Ls; ++c) {
+                const size_t cn = (size_t)c * n;
+                const T v = X[cn + m] - X[cn + ms] - Sin[base + cn];
+                if ((v < T(0) ? -v : v) < mu || v == T(0)) continue;
+                const T mb = -(Sb[base + cn] + T(2) * (Rb[cn + m] - Rb[cn + ms]));
+                acc += v > T(0) ? mb : -mb;
+            }
+        }
+    }
+    omega_bar[(size_t)wi * n + p] += scale * acc;
+}
+
+// Guide gradient through the weights (eq. wts), step 1: for every stored offset tau
+//   A_tau(m) = sum_{k in [-K,K]^2} a_tau(m + k),  a_tau = c2 omega_bar_tau omega_tau, c2 = -2/h^2.
+// One thread per pixel; grid (ceil(n/256), |W|).
+template <typename T, typename WT>
+__global__ void __launch_bounds__(256)
+guide_box_kernel(const T* __restrict__ omega_bar, const WT* __restrict__ omega, T* __restrict__ A,
+                 int H, int W, int K, T c2) {
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const size_t off = (size_t)blockIdx.y * n;
+    const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+    T acc = T(0);
+    for (int k1 = -K; k1 <= K; ++k1) {
+        const size_t row = (size_t)wrapn(y + k1, H) * W;
+        for (int k2 = -K; k2 <= K; ++k2) {
+            const size_t j = row + wrapn(x + k2, W);
+            acc += omega_bar[off + j] * (T)wload(omega + off + j);
+        }
+    }
+    A[off + p] = c2 * acc;
+}
+
+// Step 2: dL/dG_c(j) = sum_tau [A_tau(j) (G_c(j) - G_c(j - tau)) - A_tau(j + tau) (G_c(j + tau) - G_c(j))]
+// (the adjoint of the patch differences D_{tau k} G summed over k).  One thread per pixel;
+// grid (ceil(n/256), L_guide).
+template <typename T>
+__global__ void __launch_bounds__(256)
+guide_bwd_kernel(const T* __restrict__ G, const T* __restrict__ A, T* __restrict__ Gb, int H, int W, int S) {
+    const size_t n = (size_t)H * W;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int side = 2 * S + 1;
+    const int nW = side * side - 1;
+    const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
+    const T* Gc = G + (size_t)blockIdx.y * n;
+    const T g0 = Gc[p];
+    T acc = T(0);
+    for (int t = 0; t < nW; ++t) {
+        const int cell = t >= nW / 2 ? t + 1 : t;
+        const int t1 = cell / side - S, t2 = cell % side - S;
+        const size_t jm = (size_t)wrapn(y - t1, H) * W + wrapn(x - t2, W);
+        const size_t jp = (size_t)wrapn(y + t1, H) * W + wrapn(x + t2, W);
+        const T* At = A + (size_t)t * n;
+        acc += At[p] * (g0 - Gc[jm]) - At[jp] * (Gc[jp] - g0);
+    }
+    Gb[(size_t)blockIdx.y * n + p] = acc;
+}
+
 }  // namespace fuse

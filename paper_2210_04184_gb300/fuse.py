@@ -23,7 +23,7 @@ FUSE_F32, FUSE_F64, FUSE_BF16 = 0, 1, 2
 FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
 FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
 FUSE_OPT_HALF_WINDOW, FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS = 7, 8, 9, 10
-FUSE_OPT_GRAD_SEGMENT = 11
+FUSE_OPT_GRAD_SEGMENT, FUSE_OPT_GRAD_WEIGHTS = 11, 12
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -85,6 +85,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_grad_forward": (_ST, [_VP, _VP, _VP, _I, _VP]),
         "fuse_grad_backward": (_ST, [_VP, _VP, _VP, _VP, _VP, _D]),
         "fuse_grad": (_ST, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _D]),
+        "fuse_grad_weights": (_ST, [_VP, _VP, _VP, _VP]),
         "fuse_phi_static": (_ST, [_VP, _VP, _I, _I, _I, _I, _I, _I, _I, _VP, _VP]),
         "fuse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
         "fuse_batch_solve": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP),
@@ -257,6 +258,11 @@ def fuse_grad_backward(ctx, Xbar_dev: int | None, Zbar_dev: int | None, Yl_bar: 
     _check(load().fuse_grad_backward(ctx, _VP(Xbar_dev or None), _VP(Zbar_dev or None), _VP(Yl_bar or None),
                                      _VP(Yh_bar or None), pb if want_params else None), ctx)
     return (pb[0], pb[1], pb[2]) if want_params else None
+
+
+def fuse_grad_weights(ctx, omega_bar: int | None, guide_dev: int | None, guide_bar: int | None):
+    _check(load().fuse_grad_weights(ctx, _VP(omega_bar or None), _VP(guide_dev or None), _VP(guide_bar or None)),
+           ctx)
 
 
 def fuse_grad(ctx, Yl_dev: int, Yh_dev: int, iters: int, Xbar_dev: int | None, Zbar_dev: int | None,
@@ -471,16 +477,31 @@ class Fusion:
                                zb.data_ptr() if zb is not None else None, gl.data_ptr(), gh.data_ptr())
         return gl, gh, dict(lam1=p[0], lam2=p[1], rho=p[2])
 
+    def grad_weights(self, guide=None):
+        """dL/domega of the last grad_backward (run with FUSE_OPT_GRAD_WEIGHTS = 1) and, when the
+        guide that produced the weights is given, dL/dguide through eq. wts."""
+        t = self.torch
+        ob = t.empty((self.nW, self.H, self.W), dtype=self.tdtype, device="cuda")
+        g = self._t(guide, (self.geom.L_guide, self.H, self.W)) if guide is not None else None
+        gb = t.empty((self.geom.L_guide, self.H, self.W), dtype=self.tdtype, device="cuda") if g is not None else None
+        self._sync_stream()
+        fuse_grad_weights(self.ctx, ob.data_ptr(), g.data_ptr() if g is not None else None,
+                          gb.data_ptr() if gb is not None else None)
+        return ob, gb
+
     def params(self):
         """(lambda1, lambda2, rho) of the context as a float64 CPU tensor, for unrolled()."""
         return self.torch.tensor([self._lam1, self._lam2, self._rho], dtype=self.torch.float64)
 
-    def unrolled(self, Yl, Yh, iters, params=None):
-        """X after `iters` iterations from zero state as a differentiable function of Y_l, Y_h and
-        params = (lambda1, lambda2, rho) (a tensor equal to the context's values, see params())."""
+    def unrolled(self, Yl, Yh, iters, params=None, guide=None):
+        """X after `iters` iterations from zero state as a differentiable function of Y_l, Y_h,
+        params = (lambda1, lambda2, rho) (a tensor equal to the context's values, see params())
+        and, when given, the guide: the weights are then computed from it (fuse_weights) and
+        differentiated through; without a guide the context's current weights are constants.
+        Passing Y_h itself as the guide gives it both gradient paths (torch adds them)."""
         if params is None:
             params = self.params()
-        return UnrolledADMM.apply(Yl, Yh, params, self, iters)
+        return UnrolledADMM.apply(Yl, Yh, params, guide, self, iters)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -547,7 +568,7 @@ def _unrolled_function():
         (fuse_grad_backward).  The weights omega are constants of the map."""
 
         @staticmethod
-        def forward(ctx, Yl, Yh, params, fusion, iters):
+        def forward(ctx, Yl, Yh, params, guide, fusion, iters):
             p = [float(v) for v in params.detach().cpu().tolist()]
             ref = (fusion._lam1, fusion._lam2, fusion._rho)
             if any(abs(a - b) > 1e-12 * max(1.0, abs(b)) for a, b in zip(p, ref)):
@@ -555,6 +576,10 @@ def _unrolled_function():
             ctx.fusion = fusion
             ctx.pdev = params.device
             ctx.pdtype = params.dtype
+            ctx.guide = guide.detach() if guide is not None else None
+            if guide is not None:
+                fusion.weights(ctx.guide)
+            fusion.set_option(FUSE_OPT_GRAD_WEIGHTS, int(guide is not None and guide.requires_grad))
             return fusion.grad_forward(Yl.detach(), Yh.detach(), iters)
 
         @staticmethod
@@ -562,7 +587,10 @@ def _unrolled_function():
             f = ctx.fusion
             gl, gh, p = f.grad_backward(Xbar=Xbar.contiguous())
             gp = torch.tensor([p["lam1"], p["lam2"], p["rho"]], dtype=ctx.pdtype, device=ctx.pdev)
-            return gl, gh, gp, None, None
+            gg = None
+            if ctx.guide is not None and ctx.needs_input_grad[3]:
+                _, gg = f.grad_weights(ctx.guide)
+            return gl, gh, gp, gg, None, None
 
     return _Unrolled
 

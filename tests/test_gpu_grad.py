@@ -4,7 +4,9 @@ pass (oracle/grad.py) and against central differences of the GPU's own FP64 forw
 The loss is L = <Wt, X_K> for a fixed seeded Wt, so dL/dX_K = Wt.  Tolerances: FP64 within
 1e-9 relative (both sides take the same clamp decisions up to rounding); FP32 within 2e-3
 relative (a clamp decision taken on an FP32 v within rounding of mu flips that entry's
-adjoint, so FP32 gradients carry a small decision noise on top of rounding)."""
+adjoint, so FP32 gradients carry a small decision noise on top of rounding; the local
+dL/domega within 1e-2).  Central differences use directions whose clamp decisions are stable
+within the step (the map is piecewise smooth, reading C-16)."""
 import numpy as np
 import pytest
 
@@ -59,6 +61,20 @@ def oracle_grad(p, iters, omega, Wt_lhw):
     X, g = ograd.unrolled_grad(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S,
                                p.lam1, p.lam2, p.rho, omega, iters, lambda X: nlpr.to_hwl(Wt_lhw))
     return nlpr.to_lhw(X), nlpr.to_lhw(g["Yl"]), nlpr.to_lhw(g["Yh"]), g
+
+
+def stable_fd(loss, shape, rng, tries=6, h=1e-6):
+    """Central difference of loss(t) (t: step along a random direction) at a direction whose
+    clamp decisions do not flip within the step: steps h and h/10 must agree to 1e-7 relative
+    (the unrolled map is piecewise smooth; a kink inside the step biases the difference).
+    Returns (direction, derivative)."""
+    for _ in range(tries):
+        d = rng.standard_normal(shape)
+        f1 = (loss(h * d) - loss(-h * d)) / (2 * h)
+        f2 = (loss(0.1 * h * d) - loss(-0.1 * h * d)) / (0.2 * h)
+        if abs(f1 - f2) <= 1e-7 * max(1.0, abs(f1)):
+            return d, f1
+    raise AssertionError("no direction with a stable clamp mask")
 
 
 def weights64(p):
@@ -198,15 +214,11 @@ def test_central_differences_of_the_gpu_forward():
         X, _ = g.solve(a + dyl, b + dyh, iters)
         return float((X.cpu().numpy() * Wt).sum())
 
-    # a step small enough that no clamp decision flips inside it on these seeds (C-16 reading)
-    h = 1e-8
     for key, grad in (("Yl", gl), ("Yh", gh)):
-        d = rng.standard_normal(grad.shape)
-        dt = torch.tensor(h * d, device="cuda")
-        fd = (loss(p, **{("dyl" if key == "Yl" else "dyh"): dt}) -
-              loss(p, **{("dyl" if key == "Yl" else "dyh"): -dt})) / (2 * h)
+        kw = "dyl" if key == "Yl" else "dyh"
+        d, fd = stable_fd(lambda e: loss(p, **{kw: torch.tensor(e, device="cuda")}), grad.shape, rng)
         an = float((grad * d).sum())
-        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (key, fd, an)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (key, fd, an)
     import dataclasses
     for key in ("lam1", "lam2", "rho"):
         v = getattr(p, key)
@@ -247,3 +259,105 @@ def test_unrolled_workload_full_size():
     Wt = np.random.default_rng(15).standard_normal((p.L_s, p.H, p.W))
     f, yl, yh = context(p, meta["dtype"], meta["wdtype"], om32)
     compare(gpu_grad(f, yl, yh, p.iters, Wt), oracle_grad(p, p.iters, om32, Wt), 2e-3, 1e-5)
+
+
+# ---- weight and guide gradients (fuse_grad_weights) ----------------------------------------
+
+def _mirror_sum(om_bar, S):
+    """Oracle dL/domega (every offset) mapped onto the half-window solver's stored weights: the
+    stored weight of a kept offset tau at pixel j also serves the mirror (-tau) at pixel j - tau."""
+    offs = nlpr.search_offsets(S)
+    idx = {t: i for i, t in enumerate(offs)}
+    out = np.zeros_like(om_bar)
+    for i, t in enumerate(offs):
+        if t[0] > 0 or (t[0] == 0 and t[1] > 0):
+            m = idx[(-t[0], -t[1])]
+            out[i] = om_bar[i] + np.roll(om_bar[m], shift=t, axis=(0, 1))
+    return out
+
+
+@pytest.mark.parametrize("half", [1, 0])
+def test_weight_and_guide_gradients_match_oracle_fp64(half):
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_GRAD_WEIGHTS
+    p = problem()
+    Wt = np.random.default_rng(21).standard_normal((p.L_s, p.H, p.W))
+    f = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    f.set_option(FUSE_OPT_HALF_WINDOW, half)
+    f.set_option(FUSE_OPT_GRAD_WEIGHTS, 1)
+    yl = torch.tensor(p.Yl, device="cuda")
+    yh = torch.tensor(p.Yh, device="cuda")
+    f.weights(yh)                                     # guide = Y_h
+    f.grad_forward(yl, yh, 6)
+    _, _, pr = f.grad_backward(Xbar=torch.tensor(Wt, device="cuda"))
+    ob, gb = f.grad_weights(yh)
+    om_gpu = f.get_weights().cpu().numpy()
+    ob, gb = ob.cpu().numpy(), gb.cpu().numpy()
+    om = weights64(p)
+    assert np.abs(om_gpu - om).max() <= 1e-13
+    _, _, _, go = oracle_grad(p, 6, om, Wt)
+    want = _mirror_sum(go["omega"], p.S) if half else go["omega"]
+    assert rel(ob, want) <= 1e-9
+    # <omega_bar, omega> = lambda2 dL/dlambda2 on the GPU's own outputs
+    assert abs(float((ob * om_gpu).sum()) - p.lam2 * pr["lam2"]) <= 1e-9 * abs(p.lam2 * pr["lam2"])
+    gbo = nlpr.to_lhw(ograd.weights_vjp(nlpr.to_hwl(p.Yh), p.K, p.S, p.h, go["omega"]))
+    assert rel(gb, gbo) <= 1e-9
+
+
+def test_weight_gradient_fp32():
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_GRAD_WEIGHTS
+    p = problem()
+    om = weights64(p).astype(np.float32).astype(np.float64)
+    Wt = np.random.default_rng(22).standard_normal((p.L_s, p.H, p.W))
+    f, yl, yh = context(p, "f32", "f32", om, opts=((FUSE_OPT_GRAD_WEIGHTS, 1),))
+    f.grad_forward(yl, yh, 6)
+    f.grad_backward(Xbar=torch.tensor(Wt, dtype=torch.float32, device="cuda"))
+    ob, _ = f.grad_weights()
+    _, _, _, go = oracle_grad(p, 6, om, Wt)
+    # dL/domega is local: an FP32 clamp decision that differs from the FP64 one changes that
+    # entry by O(1), so the FP32 bound is looser than for the summed gradients (measured 4.3e-3)
+    assert rel(ob.double().cpu().numpy(), _mirror_sum(go["omega"], p.S)) <= 1e-2
+
+
+def test_guide_gradient_central_differences_and_autograd():
+    # the guide is Y_h: the autograd function adds the data and weight paths; checked against
+    # central differences of the GPU's FP64 forward with weights recomputed from Y_h + h d
+    p = problem(seed=synth.SEED_BASE + 14, H=24, W=24, d=2, S=1)
+    iters = 6
+    rng = np.random.default_rng(23)
+    Wt = torch.tensor(rng.standard_normal((p.L_s, p.H, p.W)), device="cuda")
+    f = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    yl = torch.tensor(p.Yl, device="cuda")
+    yh = torch.tensor(p.Yh, device="cuda").requires_grad_(True)
+    X = f.unrolled(yl, yh, iters, guide=yh)
+    (X * Wt).sum().backward()
+
+    def loss(y):
+        g = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+        g.weights(y)
+        Xs, _ = g.solve(yl, y, iters)
+        return float((Xs * Wt).sum())
+
+    d, fd = stable_fd(lambda e: loss(yh.detach() + torch.tensor(e, device="cuda")), tuple(yh.shape), rng)
+    an = float((yh.grad.cpu().numpy() * d).sum())
+    assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+    # the two paths separately, through the C entry points
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_GRAD_WEIGHTS
+    f2 = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    f2.set_option(FUSE_OPT_GRAD_WEIGHTS, 1)
+    y2 = yh.detach().clone()
+    f2.weights(y2)
+    f2.grad_forward(yl, y2, iters)
+    _, gh, _ = f2.grad_backward(Xbar=Wt)
+    _, gg = f2.grad_weights(y2)
+    assert torch.allclose(yh.grad, gh + gg, rtol=1e-12, atol=1e-14)
+
+
+def test_weight_gradient_needs_the_option():
+    p = problem()
+    f, yl, yh = context(p, "f64", "f64", weights64(p))
+    f.grad_forward(yl, yh, 3)
+    f.grad_backward(Xbar=torch.zeros((p.L_s, p.H, p.W), dtype=torch.float64, device="cuda"))
+    with pytest.raises(FuseError) as e:
+        f.grad_weights()
+    assert e.value.status == FUSE_ESTATE
+    fuse_reset_error(f.ctx)
