@@ -403,14 +403,32 @@ def admm_step(st: State, su: Setup, x_solver=None, latent_fn=None, dtsum_fn=None
     return State(P1, P2, Lam1, Lam2, Q, Sig, X, st.t + 1)
 
 
+def quantize_state(Sig: np.ndarray, omega: np.ndarray, lam2: float, rho: float, levels: int) -> np.ndarray:
+    """Sigma as stored in `levels`-step fixed point relative to its own threshold.
+
+    After any update Sigma_{tau k}(i) = -clamp(v, -mu, mu) with mu = lambda2 omega_{i tau}/rho
+    (eqs. Qj_main, dualvar3_main), so |Sigma| <= mu and the code rint(Sigma levels / mu) lies in
+    [-levels, levels]; the stored value is code mu / levels (0 where mu = 0).  This storage is
+    not the paper's: it is the reduced-precision state option of the solver."""
+    out = np.zeros_like(Sig)
+    for t in range(Sig.shape[0]):
+        mu = (lam2 * omega[t] / rho)[None, :, :, None]
+        safe = np.where(mu > 0, mu, 1.0)
+        code = np.where(mu > 0, np.clip(np.rint(Sig[t] / safe * levels), -levels, levels), 0.0)
+        out[t] = code * mu / levels
+    return out
+
+
 def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
-         x_solver=None, fast=False, callback=None, inplace=False):
+         x_solver=None, fast=False, callback=None, inplace=False, state_levels=None):
     """Run `iters` ADMM iterations from `state` (zero initialisation by default).
 
     Images in (H, W, L) layout.  fast=True uses the C loops of oracle/loops.c for the
     Q/Sigma updates and the D^T sum (same arithmetic, explicit loops); with inplace=True those
     loops overwrite Q and Sigma in place (the old values are not needed once C is formed),
     so large problems hold one copy of the latent variables.
+    state_levels: Sigma enters the Q and Sigma updates as stored in fixed point
+    (quantize_state); the right-hand side still sums the exact Q + Sigma of the last update.
     Returns (X, state, setup)."""
     su = setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega)
     if state is not None:
@@ -422,6 +440,15 @@ def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
         from . import cloops
         latent_fn = cloops.latent_update_inplace if inplace else cloops.latent_update
         dtsum_fn = cloops.dt_sum
+    if state_levels:
+        exact_fn = latent_fn
+
+        def latent_fn(X, s, u):
+            sq = dataclasses.replace(s, Sig=quantize_state(s.Sig, u.omega, u.lam2, u.rho, state_levels))
+            if exact_fn is not None:
+                return exact_fn(X, sq, u)
+            Q = update_q(X, sq, u)
+            return Q, update_sigma(X, Q, sq, u)
     for _ in range(iters):
         st = admm_step(st, su, x_solver, latent_fn, dtsum_fn)
         if callback is not None:

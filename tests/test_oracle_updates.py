@@ -187,3 +187,34 @@ def test_inplace_latent_loops_match():
     st2 = st.copy()
     Qb, Sb = cloops.latent_update_inplace(X, st2, su)
     assert np.array_equal(Qa, Qb) and np.array_equal(Sa, Sb) and Sb is st2.Sig
+
+
+def test_fixed_point_state_storage():
+    # codes are integers in [-levels, levels], |Sigma| <= mu is kept, mu = 0 stores 0, and with
+    # very fine steps the fixed-point run equals the exact one
+    rng = np.random.default_rng(61)
+    H, W, L, K, S = 6, 8, 2, 1, 1
+    nW, nP = len(nlpr.search_offsets(S)), len(nlpr.patch_offsets(K))
+    om = rng.random((nW, H, W))
+    om[0, 0, 0] = 0.0
+    lam2, rho, lev = 0.3, 0.5, 32767
+    mu = lam2 * om / rho
+    Sig = -np.clip(rng.standard_normal((nW, nP, H, W, L)), -mu[:, None, :, :, None], mu[:, None, :, :, None])
+    q = nlpr.quantize_state(Sig, om, lam2, rho, lev)
+    codes = np.divide(q * lev, mu[:, None, :, :, None], out=np.zeros_like(q), where=mu[:, None, :, :, None] > 0)
+    assert np.allclose(codes, np.rint(codes), atol=1e-6) and np.abs(np.rint(codes)).max() <= lev
+    assert np.all(np.abs(q - Sig) <= mu[:, None, :, :, None] / (2 * lev) * (1 + 1e-12))
+    assert np.all(q[0, :, 0, 0, :] == 0.0)
+    assert np.array_equal(nlpr.quantize_state(q, om, lam2, rho, lev), q) or \
+        np.abs(nlpr.quantize_state(q, om, lam2, rho, lev) - q).max() <= 1e-15
+    Yl = rng.random((3, 4, 3)); Yh = rng.random((H, W, 1))
+    E = np.linalg.qr(rng.standard_normal((3, L)))[0].T
+    R = rng.random((3, 1)); R /= R.sum()
+    kern = np.ones((3, 3)) / 9.0
+    omega = nlpr.weights(Yh, K, S, 0.5)
+    args = (Yl, Yh, kern, 2, R, E, K, S, 0.8, 0.05, 0.3, omega, 6)
+    X0, _, _ = nlpr.admm(*args)
+    X1, _, _ = nlpr.admm(*args, state_levels=2 ** 40)
+    X2, _, _ = nlpr.admm(*args, state_levels=lev)
+    assert np.abs(X1 - X0).max() <= 1e-11
+    assert 0 < np.abs(X2 - X0).max() <= 1e-4 * np.abs(X0).max()
