@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-FP32 comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the reverse-pass measurement")
     ap.add_argument("--grad-only", action="store_true", help="only the reverse-pass measurement")
+    ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-point state measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
@@ -136,15 +137,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def latent_bytes(p, esz, wsz, half=True):
+def latent_bytes(p, esz, wsz, half=True, ssz=None):
     """Algorithmic bytes of one latent-pass launch: state read + write over the kept offsets
-    (half of the window in half-window mode), their weights, X, and the adjoint planes."""
+    (half of the window in half-window mode; ssz bytes per stored entry, default esz), their
+    weights, X, and the adjoint planes."""
     n = p.H * p.W
     nW = (2 * p.S + 1) ** 2 - 1
     nK = nW // 2 if half else nW
     rows = p.S + 1 if half else 2 * p.S + 1
     nP = (2 * p.K + 1) ** 2
-    return (2 * nK * nP * p.L_s * n * esz + nK * n * wsz + p.L_s * n * esz
+    ssz = ssz or esz
+    return (2 * nK * nP * p.L_s * n * ssz + nK * n * wsz + p.L_s * n * esz
             + 2 * rows * p.L_s * n * esz)
 
 
@@ -240,7 +243,57 @@ def fp64_compare(p, meta, f32ctx, yl, yh, Z32):
         fw.close()
         out["rel_err_Z_fp32_f32weights_vs_fp64"] = float(torch.linalg.norm(Zw.double() - Z64) / nz)
     out["equal_error_1e-4"] = out.get("rel_err_Z_fp32_f32weights_vs_fp64", err32) <= 1e-4
-    return out
+    return out, Z64
+
+
+def fixed_point_bench(a, p, meta, yl, yh, Z64):
+    """The same workload with the latent state stored in 16-bit fixed point relative to its
+    threshold (FUSE_OPT_STATE_FORMAT = 1): throughput, the latent pass against the roofline
+    (2-byte state entries), and the relative error of Z against the FP64 GPU run."""
+    import torch
+    from paper_2210_04184_gb300.fuse import (Fusion, FUSE_OPT_PROFILE, FUSE_K_LATENT, FUSE_OPT_STATE_FORMAT,
+                                             fuse_solve, fuse_weights, fuse_set_stream)
+    f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
+    f.set_option(FUSE_OPT_STATE_FORMAT, 1)
+    st = torch.cuda.current_stream()
+    fuse_set_stream(f.ctx, st.cuda_stream)
+    fuse_weights(f.ctx, yh.data_ptr())
+    tuned = f.autotune(yl, yh, iters=2)
+    Z = torch.empty((p.L_l, p.H, p.W), dtype=yl.dtype, device="cuda")
+
+    def step():
+        fuse_weights(f.ctx, yh.data_ptr())
+        fuse_solve(f.ctx, yl.data_ptr(), yh.data_ptr(), p.iters, 0, None, Z.data_ptr())
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    f.set_option(FUSE_OPT_PROFILE, 1)
+    f.profile(FUSE_K_LATENT, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat_ms, lat_n = f.profile(FUSE_K_LATENT)
+    f.set_option(FUSE_OPT_PROFILE, 0)
+    f.close()
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    wsz = {"bf16": 2, "f32": 4, "f64": 8}[meta["wdtype"]]
+    lb = latent_bytes(p, 4, wsz, ssz=2)
+    per = lat_ms / max(lat_n, 1)
+    err = float(torch.linalg.norm(Z.double() - Z64) / torch.linalg.norm(Z64)) if Z64 is not None else None
+    return {"state": "int16 fixed point relative to mu",
+            "value": p.H * p.W / 1e6 * p.L_s * p.iters * a.steps / (ms / 1e3),
+            "unit": UNIT, "ms_per_step": ms / a.steps, "launch_shapes": tuned,
+            "roofline": {"bound": "hbm", "achieved": lb / (per / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": lb / (per / 1e3) / 1e9 / hbm, "kernel": "latent_tma_kernel<int16 state>",
+                         "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per, "launches": lat_n,
+                         "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
+            "rel_err_Z_vs_fp64": err, "equal_error_1e-4": err is not None and err <= 1e-4}
 
 
 def run_batch(a, rank, world, local_rank):
@@ -560,8 +613,12 @@ def run_ours(a, rank, world, local_rank):
                "d2h_bytes_per_step": hz.numel() * hz.element_size()}
 
     fp64 = None
+    Z64 = None
     if not a.no_fp64 and meta["dtype"] == "f32":
-        fp64 = fp64_compare(p, meta, f, yl, yh, Z)
+        fp64, Z64 = fp64_compare(p, meta, f, yl, yh, Z)
+    fixed = None
+    if not a.no_fixed and rank == 0 and meta["dtype"] == "f32" and p.W % 8 == 0:
+        fixed = fixed_point_bench(a, p, meta, yl, yh, Z64)
     grad = None
     if not a.no_grad and rank == 0 and a.workload == "hsms_256":
         grad = grad_bench(a, rank)
@@ -594,6 +651,7 @@ def run_ours(a, rank, world, local_rank):
         "clocks": clk,
         "e2e": e2e,
         "fp64_compare": fp64,
+        "fixed_point_state": fixed,
         "grad": grad,
     }
     if not a.no_cpu_baseline and world == 1:

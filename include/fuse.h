@@ -85,9 +85,17 @@ enum {
     FUSE_OPT_FFT_COLS = 10,      /* columns per block of the column FFT pass: power of 2 <= 32 */
     FUSE_OPT_GRAD_SEGMENT = 11,  /* iterations per checkpointed segment of fuse_grad_forward
                                     (default 0: one segment, every iteration taped) */
-    FUSE_OPT_GRAD_WEIGHTS = 12   /* 1: fuse_grad_backward also accumulates dL/domega for
+    FUSE_OPT_GRAD_WEIGHTS = 12,  /* 1: fuse_grad_backward also accumulates dL/domega for
                                     fuse_grad_weights (one more read of the state per reverse
                                     iteration); default 0 */
+    FUSE_OPT_STATE_FORMAT = 13   /* storage of the latent state: 0 (default) the iterate type;
+                                    1 = 16-bit fixed point relative to each entry's threshold
+                                    (|Sigma'| <= mu always, so q = rint(32767 Sigma'/mu) stands
+                                    for q mu / 32767; absolute error <= mu/65534 per entry, half
+                                    the state bytes).  F32 contexts with the bulk-copy latent
+                                    pass (W % 8 == 0) only; not with the reverse pass.  Switching
+                                    reallocates the state and clears it.  A batch takes the
+                                    format of its contexts (all the same). */
 };
 
 /* Kernel groups for fuse_profile. */

@@ -96,6 +96,53 @@ __device__ __forceinline__ void vstore_stream(T* p, const T (&v)[VEC]) {
     }
 }
 
+// Storage of the latent state.  Either the iterate type, or 16-bit fixed point relative to the
+// entry's own threshold: |Sigma'| <= mu always (Sigma' = -clamp(v, -mu, mu)), so the code
+// q = rint(Sigma' 32767 / mu) in [-32767, 32767] stands for q mu / 32767 (an absolute error of at
+// most mu / 65534 plus the rounding of the quotient; mu = 0 stores 0).  mu[j] are the thresholds
+// of the VEC entries.
+template <typename T, typename ST, int VEC>
+struct StateIO {
+    static __device__ __forceinline__ void load(const ST* p, T (&v)[VEC], const T*) { vload<T, VEC>(p, v); }
+    static __device__ __forceinline__ void store(ST* p, const T (&v)[VEC], const T*) {
+        vstore_stream<T, VEC>(p, v);
+    }
+};
+template <int VEC>
+struct StateIO<float, int16_t, VEC> {
+    static_assert(VEC % 8 == 0, "16-bit state moves in 16-byte groups of 8");
+    static constexpr float kScale = 1.0f / 32767.0f;
+    static __device__ __forceinline__ int code(float v, float m) {
+        return m > 0.0f ? max(-32767, min(32767, __float2int_rn(__fdividef(v, m) * 32767.0f))) : 0;
+    }
+    static __device__ __forceinline__ void load(const int16_t* p, float (&v)[VEC], const float* mu) {
+#pragma unroll
+        for (int g = 0; g < VEC / 8; ++g) {
+            const int4 w = reinterpret_cast<const int4*>(p)[g];
+            const int32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int lo = (int)(int16_t)(wd[h] & 0xffff), hi = wd[h] >> 16;
+                v[g * 8 + 2 * h] = (float)lo * (mu[g * 8 + 2 * h] * kScale);
+                v[g * 8 + 2 * h + 1] = (float)hi * (mu[g * 8 + 2 * h + 1] * kScale);
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(int16_t* p, const float (&v)[VEC], const float* mu) {
+#pragma unroll
+        for (int g = 0; g < VEC / 8; ++g) {
+            int32_t wd[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int a = code(v[g * 8 + 2 * h], mu[g * 8 + 2 * h]);
+                const int b = code(v[g * 8 + 2 * h + 1], mu[g * 8 + 2 * h + 1]);
+                wd[h] = (int32_t)(((uint32_t)(uint16_t)(int16_t)a) | ((uint32_t)(uint16_t)(int16_t)b << 16));
+            }
+            __stcs(reinterpret_cast<int4*>(p) + g, make_int4(wd[0], wd[1], wd[2], wd[3]));
+        }
+    }
+};
+
 // Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1
 // (blockIdx.z).  Full mode: tau1 in [-S, S], all tau2 (skipping (0,0)); state index =
 // row-major index in W.

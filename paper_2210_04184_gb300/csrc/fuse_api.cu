@@ -86,6 +86,8 @@ struct fuse_ctx {
     unsigned wait_limit = 1u << 22;
     // half-window latent state (one offset of each +-tau pair); 0 = full window
     int half = 1;
+    // latent state storage: 0 = the iterate type, 1 = 16-bit fixed point relative to mu
+    int sfmt = 0;
     // reverse pass: workspace, iterations per checkpointed segment (0 = one segment), a counter
     // bumped by every call that changes inputs or state (a taped forward is valid while unchanged)
     GradWork* gw = nullptr;
@@ -296,7 +298,9 @@ bool latent_tma_shape(fuse_ctx* c) {
     while (Ty > 1 && ((tpr * Ty + 31) / 32) * 32 + 32 > 288) --Ty;
     const int ncons = ((tpr * Ty + 31) / 32) * 32;
     if (ncons + 32 > 288) return false;
-    const size_t smem = (size_t)(c->lat_stages + 2 * c->S + 1) * Ty * c->W * c->esz + 2 * (size_t)c->lat_stages * 8;
+    const size_t ssz = c->sfmt ? 2 : c->esz;     // bytes of one stored state element
+    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz + (size_t)(2 * c->S + 1) * Ty * c->W * c->esz +
+                        2 * (size_t)c->lat_stages * 8;
     if (smem > (size_t)kMaxSmem || c->lat_stages < 1) return false;
     c->lt_Ty = Ty;
     c->lt_ncons = ncons;
@@ -405,6 +409,10 @@ struct Impl {
             constexpr int K = decltype(k)::value;
             if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_kernel<T, WT, K, VEC>, A, kMaxSmem);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, K, TVEC>, A, kMaxSmem);
+            if constexpr (sizeof(T) == 4) {
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, K, TVEC, int16_t>, A, kMaxSmem);
+            }
         });
         CK(c, e);
         return FUSE_OK;
@@ -459,7 +467,14 @@ struct Impl {
                       rowsW);
             const LatentArgs<T, WT> a = lat_args<WT>(c, c->lt_Ty, c->lt_ncons, c->lat_stages, c->lat_bpb);
             with_k(c->K, [&](auto k) {
-                latent_tma_kernel<T, WT, decltype(k)::value, TVEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
+                constexpr int K = decltype(k)::value;
+                if constexpr (sizeof(T) == 4) {
+                    if (c->sfmt == 1) {
+                        latent_tma_kernel<T, WT, K, TVEC, int16_t><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
+                        return;
+                    }
+                }
+                latent_tma_kernel<T, WT, K, TVEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
             });
             return;
         }
@@ -652,6 +667,28 @@ fuse_status weights_impl(fuse_ctx* c, const void* G) {
 
 void grad_free(GradWork* g);
 
+// Reallocates the latent state for half-window mode `h` and storage format `f`; clears the
+// ADMM state (the next solve starts from zero) and the captured iteration graph.
+fuse_status realloc_state(fuse_ctx* c, int h, int f) {
+    const size_t nWs = h ? (size_t)c->nW / 2 : (size_t)c->nW;
+    const size_t bytes = nWs * c->nP * c->Ls * c->n * (f ? 2 : c->esz);
+    for (auto& p : c->allocs)
+        if (p == c->Sig) { CK(c, cudaStreamSynchronize(c->stream)); cudaFree(p); p = nullptr; }
+    c->Sig = nullptr;
+    fuse_status s2 = dalloc(c, &c->Sig, bytes);
+    if (s2 != FUSE_OK) return s2;
+    c->sig_bytes = bytes;
+    c->half = h;
+    c->sfmt = f;
+    latent_tma_shape(c);
+    ++c->epoch;
+    c->have_state = false;
+    c->have_x = false;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    return FUSE_OK;
+}
+
 void release(fuse_ctx* c) {
     grad_free(c->gw);
     c->gw = nullptr;
@@ -689,7 +726,7 @@ struct fuse_batch {
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     int device = 0;
     fuse_dtype dtype = FUSE_F32, wdtype = FUSE_F32;
-    int K = 0, S = 0, Ls = 0, bh = 1, bw = 1, half = 1;
+    int K = 0, S = 0, Ls = 0, bh = 1, bw = 1, half = 1, sfmt = 0;
     // launch shapes shared by all problems
     int lat_target = 256, lat_stages = 6, lat_ncons = 0, lat_bpb = 2;
     size_t lat_smem = 0, st_smem = 0, fr_smem = 0, fc_smem = 0, px_smem = 0;
@@ -777,7 +814,9 @@ struct BatchImpl {
         for (int i = 0; i < n; ++i) {
             fuse_ctx* c = b->ctx[i];
             la[i] = Impl<T>::template lat_args<WT>(c, Ty[i], b->lat_ncons, b->lat_stages, b->lat_bpb);
-            const size_t sm = (size_t)(b->lat_stages + side) * Ty[i] * c->W * esz + 2 * (size_t)b->lat_stages * 8;
+            const size_t ssz = b->sfmt ? 2 : esz;
+            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz + (size_t)side * Ty[i] * c->W * esz +
+                              2 * (size_t)b->lat_stages * 8;
             if (sm > b->lat_smem) b->lat_smem = sm;
         }
         if (b->lat_smem > (size_t)kMaxSmem) return bfail(b, FUSE_EUNSUPPORTED, "batched latent ring exceeds shared memory");
@@ -854,6 +893,11 @@ struct BatchImpl {
         cudaError_t e = cudaSuccess;
         with_k(b->K, [&](auto k) {
             e = cudaFuncSetAttribute(latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC>, A, kMaxSmem);
+            if constexpr (sizeof(T) == 4) {
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC, int16_t>, A,
+                                             kMaxSmem);
+            }
         });
         BCK(b, e);
         with_bh(b->bh, [&](auto bh) {
@@ -901,7 +945,15 @@ struct BatchImpl {
             BCK(b, cudaEventRecord(e0, s));
         }
         with_k(b->K, [&](auto k) {
-            latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
+            constexpr int K = decltype(k)::value;
+            if constexpr (sizeof(T) == 4) {
+                if (b->sfmt) {
+                    latent_tma_batch_kernel<T, WT, K, VEC, int16_t><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
+                        (const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg);
+                    return;
+                }
+            }
+            latent_tma_batch_kernel<T, WT, K, VEC><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
                 (const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg);
         });
         if (timed) BCK(b, cudaEventRecord(e1, s));
@@ -1340,6 +1392,8 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
         case FUSE_OPT_LATENT_IMPL:
         case FUSE_OPT_LATENT_THREADS:
         case FUSE_OPT_LATENT_STAGES: {
+            if (option == FUSE_OPT_LATENT_IMPL && !value && c->sfmt)
+                return fail(c, FUSE_EUNSUPPORTED, "the fixed-point state needs the bulk-copy latent pass");
             const int old_impl = c->lat_impl, old_t = c->lat_target, old_d = c->lat_stages;
             if (option == FUSE_OPT_LATENT_IMPL) c->lat_impl = value ? 1 : 0;
             if (option == FUSE_OPT_LATENT_THREADS) c->lat_target = (int)value;
@@ -1381,21 +1435,25 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
         case FUSE_OPT_HALF_WINDOW: {
             const int h = value ? 1 : 0;
             if (h == c->half) return FUSE_OK;
-            const size_t nWs = h ? (size_t)c->nW / 2 : (size_t)c->nW;
-            const size_t bytes = nWs * c->nP * c->Ls * c->n * c->esz;
-            for (auto& p : c->allocs)
-                if (p == c->Sig) { CK(c, cudaStreamSynchronize(c->stream)); cudaFree(p); p = nullptr; }
-            c->Sig = nullptr;
-            fuse_status s2 = dalloc(c, &c->Sig, bytes);
-            if (s2 != FUSE_OK) return s2;
-            c->sig_bytes = bytes;
-            c->half = h;
-            ++c->epoch;
-            c->have_state = false;
-            c->have_x = false;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-            return FUSE_OK;
+            return realloc_state(c, h, c->sfmt);
+        }
+        case FUSE_OPT_STATE_FORMAT: {
+            const int f = value ? 1 : 0;
+            if (f == c->sfmt) return FUSE_OK;
+            if (f == 1) {
+                if (c->dtype != FUSE_F32) return fail(c, FUSE_EUNSUPPORTED, "fixed-point state needs an F32 context");
+                const int old_impl = c->lat_impl;
+                c->sfmt = 1;
+                c->lat_impl = 1;
+                if (!latent_tma_shape(c)) {
+                    c->sfmt = 0;
+                    c->lat_impl = old_impl;
+                    latent_tma_shape(c);
+                    return fail(c, FUSE_EUNSUPPORTED, "fixed-point state needs the bulk-copy latent pass (W % 8 == 0)");
+                }
+                c->sfmt = 0;
+            }
+            return realloc_state(c, c->half, f);
         }
         case FUSE_OPT_WAIT_LIMIT:
             if (value < 1) return fail(c, FUSE_EINVAL, "wait limit must be positive");
@@ -1518,6 +1576,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_LATENT_STAGES: *value = c->lat_stages; return FUSE_OK;
         case FUSE_OPT_WAIT_LIMIT: *value = c->wait_limit; return FUSE_OK;
         case FUSE_OPT_HALF_WINDOW: *value = c->half; return FUSE_OK;
+        case FUSE_OPT_STATE_FORMAT: *value = c->sfmt; return FUSE_OK;
         case FUSE_OPT_LATENT_BANDS: *value = c->lat_bpb; return FUSE_OK;
         case FUSE_OPT_FFT_ROWS: *value = c->fr_rpb; return FUSE_OK;
         case FUSE_OPT_FFT_COLS: *value = c->fc_cw; return FUSE_OK;
@@ -1568,7 +1627,8 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
         fuse_ctx* c = ctxs[i];
         if (!c || c->sticky != FUSE_OK) return FUSE_EINVAL;
         if (c->dtype != c0->dtype || c->wdtype != c0->wdtype || c->K != c0->K || c->S != c0->S ||
-            c->Ls != c0->Ls || c->bh != c0->bh || c->bw != c0->bw || c->half != c0->half || c->device != c0->device)
+            c->Ls != c0->Ls || c->bh != c0->bh || c->bw != c0->bw || c->half != c0->half || c->device != c0->device ||
+            c->sfmt != c0->sfmt)
             return FUSE_EINVAL;
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return FUSE_EINVAL;
@@ -1581,6 +1641,7 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
     b->device = c0->device;
     b->dtype = c0->dtype; b->wdtype = c0->wdtype;
     b->K = c0->K; b->S = c0->S; b->Ls = c0->Ls; b->bh = c0->bh; b->bw = c0->bw; b->half = c0->half;
+    b->sfmt = c0->sfmt;
     b->fc_cw = c0->dtype == FUSE_F64 ? 4 : 8;
     if (cudaSetDevice(b->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1785,6 +1846,7 @@ fuse_status fuse_grad_forward(fuse_ctx* c, const void* Yl, const void* Yh, int i
     if (iters < 0) return fail(c, FUSE_EINVAL, "iters must be >= 0");
     if (!c->have_weights) return FUSE_ESTATE;
     if (pixel_bucket(c->Ls) == 0) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass supports L_s <= 32");
+    if (c->sfmt) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass needs the state in the iterate type");
     return grad_forward_impl(c, Yl, Yh, iters, X_out);
 }
 

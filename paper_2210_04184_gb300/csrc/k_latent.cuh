@@ -151,8 +151,8 @@ template <typename T, typename WT>
 struct LatentArgs {
     const T* X;
     const WT* omega;
-    const T* Sig;       // state read (bulk copies)
-    T* Sout;            // state written: Sig itself, or another buffer of the same layout
+    const void* Sig;    // state read (bulk copies), elements of the storage type
+    void* Sout;         // state written: Sig itself, or another buffer of the same layout
     T* planes;
     int H, W, Ls, S, Ty, ncons, D;
     T coef;
@@ -170,13 +170,13 @@ __device__ __forceinline__ void consumer_barrier(int ncons) {
 // tau1 row `row`.  The bands are processed one after the other while the producer keeps the
 // ring full; between bands the consumers meet at a named barrier (the producer never waits on
 // it) to form and store that band's adjoint partial sums.
-template <typename T, typename WT, int K, int VEC>
+template <typename T, typename WT, int K, int VEC, typename ST>
 __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, int bx, int g, int row,
                                                 unsigned char* smem_tma) {
     const T* __restrict__ X = args.X;
     const WT* __restrict__ omega = args.omega;
-    const T* Sig = args.Sig;
-    T* Sout = args.Sout;
+    const ST* Sig = static_cast<const ST*>(args.Sig);
+    ST* Sout = static_cast<ST*>(args.Sout);
     T* __restrict__ planes = args.planes;
     const int H = args.H, W = args.W, Ls = args.Ls, S = args.S, Ty = args.Ty, ncons = args.ncons, D = args.D;
     const T coef = args.coef;
@@ -187,8 +187,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     constexpr int NP = PS * PS;
     const int side = 2 * S + 1;
     const int tile = Ty * W;
-    T* ring = reinterpret_cast<T*>(smem_tma);                 // [D][Ty][W]
-    T* Hs = ring + (size_t)D * tile;                          // [(2S+1)][Ty][W]
+    ST* ring = reinterpret_cast<ST*>(smem_tma);               // [D][Ty][W] of the storage type
+    T* Hs = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [(2S+1)][Ty][W]
     uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)side * tile);
     uint64_t* empty = full + D;
     __shared__ volatile int s_abort;
@@ -205,7 +205,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int nb = min(args.bpb, Ls - c0);
     const int per_band = nt2 * NP;
     const int nq = nb * per_band;
-    const unsigned bytes = (unsigned)(rows * W * (int)sizeof(T));
+    const unsigned bytes = (unsigned)(rows * W * (int)sizeof(ST));
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) {
@@ -232,7 +232,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 const int item = q / per_band, rem = q - item * per_band;
                 const int j = rem / NP, kidx = rem - j * NP;
                 const int t2 = tm.t2_of(t1, j);
-                const T* src = Sig + ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + (c0 + item)) * n +
+                const ST* src = Sig + ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + (c0 + item)) * n +
                                (size_t)y0 * W;
                 mbar_arrive_expect_tx(&full[slot], bytes);
                 tma_load_1d(ring + (size_t)slot * tile, src, bytes, &full[slot], pol);
@@ -285,7 +285,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 delta[j] = active ? Xm[j] - Xc[xsrow + wrap1(x0 + j - t2, W)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
-            T* gp = Sout + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
+            ST* gp = Sout + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
 #pragma unroll
             for (int k1 = 0; k1 < PS; ++k1) {
                 T mu[VEC + 2 * K];
@@ -298,7 +298,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                     if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
                     if (active) {
                         T sv[VEC];
-                        vload<T, VEC>(ring + (size_t)slot * tile + (size_t)r * W + x0, sv);
+                        StateIO<T, ST, VEC>::load(ring + (size_t)slot * tile + (size_t)r * W + x0, sv, mu + k2);
 #pragma unroll
                         for (int j = 0; j < VEC; ++j) {
                             const T u = sv[j] - delta[j];
@@ -307,7 +307,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                             Hacc[j] += T(2) * s2 - u;
                             sv[j] = s2;
                         }
-                        vstore_stream<T, VEC>(gp, sv);
+                        StateIO<T, ST, VEC>::store(gp, sv, mu + k2);
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&empty[slot]);
@@ -341,23 +341,23 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     }
 }
 
-template <typename T, typename WT, int K, int VEC>
+template <typename T, typename WT, int K, int VEC, typename ST = T>
 __global__ void __launch_bounds__(288, 2) latent_tma_kernel(LatentArgs<T, WT> args) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
-    latent_tma_body<T, WT, K, VEC>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
+    latent_tma_body<T, WT, K, VEC, ST>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
 }
 
 // One launch over many problems (batched uneven sizes): blocks are mapped to (problem, block)
 // by the segment table; every problem's launch shape fits the common block size and shared
 // memory size of the launch.
-template <typename T, typename WT, int K, int VEC>
+template <typename T, typename WT, int K, int VEC, typename ST = T>
 __global__ void __launch_bounds__(288, 2)
 latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     int prob, bx, by, bz;
     segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
     const LatentArgs<T, WT> a = args[prob];
-    latent_tma_body<T, WT, K, VEC>(a, bx, by, bz, smem_tma);
+    latent_tma_body<T, WT, K, VEC, ST>(a, bx, by, bz, smem_tma);
 }
 
 }  // namespace fuse
