@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--no-grad", action="store_true", help="skip the reverse-pass measurement")
     ap.add_argument("--grad-only", action="store_true", help="only the reverse-pass measurement")
     ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-point state measurement")
+    ap.add_argument("--fixed-state", action="store_true",
+                    help="run the main measurement with the 16-bit fixed-point latent state")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
@@ -534,6 +536,9 @@ def run_ours(a, rank, world, local_rank):
     esz = 8 if meta["dtype"] == "f64" else 4
     wsz = {"bf16": 2, "f32": 4, "f64": 8}[meta["wdtype"]]
     f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
+    if a.fixed_state:
+        from paper_2210_04184_gb300.fuse import FUSE_OPT_STATE_FORMAT
+        f.set_option(FUSE_OPT_STATE_FORMAT, 1)
     yl = torch.tensor(p.Yl, dtype=td, device="cuda")
     yh = torch.tensor(p.Yh, dtype=td, device="cuda")
     Z = torch.empty((p.L_l, p.H, p.W), dtype=td, device="cuda")
@@ -635,7 +640,9 @@ def run_ours(a, rank, world, local_rank):
     traffic = None
     if a.workload.startswith("hsms") and meta["wdtype"] == "bf16" and "hsms" in LATENT_TRAFFIC_PER_PIXEL:
         traffic = LATENT_TRAFFIC_PER_PIXEL["hsms"] * p.H * p.W
-    lb = latent_bytes(p, esz, wsz)
+    lb = latent_bytes(p, esz, wsz, ssz=2 if a.fixed_state else None)
+    if a.fixed_state:
+        traffic = None
     achieved = lb / (per_launch_ms / 1e3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,

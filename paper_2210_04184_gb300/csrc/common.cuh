@@ -99,8 +99,9 @@ __device__ __forceinline__ void vstore_stream(T* p, const T (&v)[VEC]) {
 // Storage of the latent state.  Either the iterate type, or 16-bit fixed point relative to the
 // entry's own threshold: |Sigma'| <= mu always (Sigma' = -clamp(v, -mu, mu)), so the code
 // q = rint(Sigma' 32767 / mu) in [-32767, 32767] stands for q mu / 32767 (an absolute error of at
-// most mu / 65534 plus the rounding of the quotient; mu = 0 stores 0).  mu[j] are the thresholds
-// of the VEC entries.
+// most mu / 65534 plus the rounding of the quotient; mu = 0 stores 0; |Sigma'| <= mu keeps
+// |Sigma' 32767 / mu| below 32767.5, so the code never leaves the range).  mu[j] are the
+// thresholds of the VEC entries.
 template <typename T, typename ST, int VEC>
 struct StateIO {
     static __device__ __forceinline__ void load(const ST* p, T (&v)[VEC], const T*) { vload<T, VEC>(p, v); }
@@ -108,37 +109,48 @@ struct StateIO {
         vstore_stream<T, VEC>(p, v);
     }
 };
+// The codes are converted without conversion instructions: with q stored in two's complement,
+// flipping the 16-bit sign bit gives q + 2^15 in [1, 65535]; placed under the exponent of 2^23
+// (byte permute) it forms the float 2^23 + 2^15 + q, so subtracting 2^23 + 2^15 yields q exactly.
+// Encoding adds 2^23 + 2^15 to Sigma' 32767/mu in one fused multiply-add, whose rounding to the
+// float grid of spacing 1 there is rint (ties to even); the low 16 bits of the result are
+// q + 2^15.
 template <int VEC>
 struct StateIO<float, int16_t, VEC> {
     static_assert(VEC % 8 == 0, "16-bit state moves in 16-byte groups of 8");
     static constexpr float kScale = 1.0f / 32767.0f;
-    static __device__ __forceinline__ int code(float v, float m) {
-        return m > 0.0f ? max(-32767, min(32767, __float2int_rn(__fdividef(v, m) * 32767.0f))) : 0;
+    static constexpr float kBias = 8421376.0f;           // 2^23 + 2^15
+    static __device__ __forceinline__ float decode(uint32_t w, uint32_t sel, float m) {
+        return (__uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - kBias) * (m * kScale);
+    }
+    static __device__ __forceinline__ uint32_t encode(float v, float m) {
+        const float inv = m > 0.0f ? __fdividef(32767.0f, m) : 0.0f;
+        return __float_as_uint(__fmaf_rn(v, inv, kBias));
     }
     static __device__ __forceinline__ void load(const int16_t* p, float (&v)[VEC], const float* mu) {
 #pragma unroll
         for (int g = 0; g < VEC / 8; ++g) {
             const int4 w = reinterpret_cast<const int4*>(p)[g];
-            const int32_t wd[4] = {w.x, w.y, w.z, w.w};
+            const uint32_t wd[4] = {(uint32_t)w.x ^ 0x80008000u, (uint32_t)w.y ^ 0x80008000u,
+                                    (uint32_t)w.z ^ 0x80008000u, (uint32_t)w.w ^ 0x80008000u};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const int lo = (int)(int16_t)(wd[h] & 0xffff), hi = wd[h] >> 16;
-                v[g * 8 + 2 * h] = (float)lo * (mu[g * 8 + 2 * h] * kScale);
-                v[g * 8 + 2 * h + 1] = (float)hi * (mu[g * 8 + 2 * h + 1] * kScale);
+                v[g * 8 + 2 * h] = decode(wd[h], 0x7610u, mu[g * 8 + 2 * h]);
+                v[g * 8 + 2 * h + 1] = decode(wd[h], 0x7632u, mu[g * 8 + 2 * h + 1]);
             }
         }
     }
     static __device__ __forceinline__ void store(int16_t* p, const float (&v)[VEC], const float* mu) {
 #pragma unroll
         for (int g = 0; g < VEC / 8; ++g) {
-            int32_t wd[4];
+            uint32_t wd[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const int a = code(v[g * 8 + 2 * h], mu[g * 8 + 2 * h]);
-                const int b = code(v[g * 8 + 2 * h + 1], mu[g * 8 + 2 * h + 1]);
-                wd[h] = (int32_t)(((uint32_t)(uint16_t)(int16_t)a) | ((uint32_t)(uint16_t)(int16_t)b << 16));
+                const uint32_t a = encode(v[g * 8 + 2 * h], mu[g * 8 + 2 * h]);
+                const uint32_t b = encode(v[g * 8 + 2 * h + 1], mu[g * 8 + 2 * h + 1]);
+                wd[h] = __byte_perm(a, b, 0x5410u) ^ 0x80008000u;
             }
-            __stcs(reinterpret_cast<int4*>(p) + g, make_int4(wd[0], wd[1], wd[2], wd[3]));
+            __stcs(reinterpret_cast<int4*>(p) + g, make_int4((int)wd[0], (int)wd[1], (int)wd[2], (int)wd[3]));
         }
     }
 };
