@@ -96,62 +96,30 @@ __device__ __forceinline__ void vstore_stream(T* p, const T (&v)[VEC]) {
     }
 }
 
-// Storage of the latent state.  Either the iterate type, or 16-bit fixed point relative to the
-// entry's own threshold: |Sigma'| <= mu always (Sigma' = -clamp(v, -mu, mu)), so the code
-// q = rint(Sigma' 32767 / mu) in [-32767, 32767] stands for q mu / 32767 (an absolute error of at
-// most mu / 65534 plus the rounding of the quotient; mu = 0 stores 0; |Sigma'| <= mu keeps
-// |Sigma' 32767 / mu| below 32767.5, so the code never leaves the range).  mu[j] are the
-// thresholds of the VEC entries.
-template <typename T, typename ST, int VEC>
-struct StateIO {
-    static __device__ __forceinline__ void load(const ST* p, T (&v)[VEC], const T*) { vload<T, VEC>(p, v); }
-    static __device__ __forceinline__ void store(ST* p, const T (&v)[VEC], const T*) {
-        vstore_stream<T, VEC>(p, v);
-    }
-};
-// The codes are converted without conversion instructions: with q stored in two's complement,
-// flipping the 16-bit sign bit gives q + 2^15 in [1, 65535]; placed under the exponent of 2^23
-// (byte permute) it forms the float 2^23 + 2^15 + q, so subtracting 2^23 + 2^15 yields q exactly.
-// Encoding adds 2^23 + 2^15 to Sigma' 32767/mu in one fused multiply-add, whose rounding to the
-// float grid of spacing 1 there is rint (ties to even); the low 16 bits of the result are
-// q + 2^15.
-template <int VEC>
-struct StateIO<float, int16_t, VEC> {
-    static_assert(VEC % 8 == 0, "16-bit state moves in 16-byte groups of 8");
-    static constexpr float kScale = 1.0f / 32767.0f;
+// 16-bit fixed-point storage of the latent state relative to the entry's own threshold.
+// |Sigma'| <= mu always (Sigma' = -clamp(v, -mu, mu)), so the code q = rint(Sigma' 32767 / mu)
+// in [-32767, 32767] stands for q mu / 32767 (absolute error at most mu / 65534).  Thresholds
+// below kMinMu act as kMinMu, so that the code arithmetic stays finite where mu = 0 (there the
+// stored value is at most kMinMu instead of 0).  Codes are stored in two's complement and
+// converted without conversion instructions: flipping the 16-bit sign bit gives q + 2^15 in
+// [1, 65535], which placed under the exponent of 2^23 (byte permute) forms the float
+// 2^23 + 2^15 + q; subtracting kBias yields q.  Adding kBias to a value in [-32767, 32767]
+// rounds it to the nearest integer (ties to even: the float spacing there is 1) and leaves
+// q + 2^15 in the low 16 bits.
+struct FixedCode {
+    static constexpr float kLevels = 32767.0f;
+    static constexpr float kStep = 1.0f / 32767.0f;
     static constexpr float kBias = 8421376.0f;           // 2^23 + 2^15
-    static __device__ __forceinline__ float decode(uint32_t w, uint32_t sel, float m) {
-        return (__uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - kBias) * (m * kScale);
+    static constexpr float kMinMu = 1e-20f;
+    // code e (0: low half, 1: high half) of the word w as a float
+    static __device__ __forceinline__ float decode(uint32_t w, int e) {
+        return __uint_as_float(__byte_perm(w ^ 0x80008000u, 0x4B000000u, e ? 0x7632u : 0x7610u)) - kBias;
     }
-    static __device__ __forceinline__ uint32_t encode(float v, float m) {
-        const float inv = m > 0.0f ? __fdividef(32767.0f, m) : 0.0f;
-        return __float_as_uint(__fmaf_rn(v, inv, kBias));
-    }
-    static __device__ __forceinline__ void load(const int16_t* p, float (&v)[VEC], const float* mu) {
-#pragma unroll
-        for (int g = 0; g < VEC / 8; ++g) {
-            const int4 w = reinterpret_cast<const int4*>(p)[g];
-            const uint32_t wd[4] = {(uint32_t)w.x ^ 0x80008000u, (uint32_t)w.y ^ 0x80008000u,
-                                    (uint32_t)w.z ^ 0x80008000u, (uint32_t)w.w ^ 0x80008000u};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                v[g * 8 + 2 * h] = decode(wd[h], 0x7610u, mu[g * 8 + 2 * h]);
-                v[g * 8 + 2 * h + 1] = decode(wd[h], 0x7632u, mu[g * 8 + 2 * h + 1]);
-            }
-        }
-    }
-    static __device__ __forceinline__ void store(int16_t* p, const float (&v)[VEC], const float* mu) {
-#pragma unroll
-        for (int g = 0; g < VEC / 8; ++g) {
-            uint32_t wd[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const uint32_t a = encode(v[g * 8 + 2 * h], mu[g * 8 + 2 * h]);
-                const uint32_t b = encode(v[g * 8 + 2 * h + 1], mu[g * 8 + 2 * h + 1]);
-                wd[h] = __byte_perm(a, b, 0x5410u) ^ 0x80008000u;
-            }
-            __stcs(reinterpret_cast<int4*>(p) + g, make_int4((int)wd[0], (int)wd[1], (int)wd[2], (int)wd[3]));
-        }
+    // float bits whose low 16 bits are rint(c) + 2^15, for c in [-32767, 32767]
+    static __device__ __forceinline__ uint32_t round_bits(float c) { return __float_as_uint(c + kBias); }
+    // two codes from round_bits into one word (low half first), back in two's complement
+    static __device__ __forceinline__ uint32_t pack(uint32_t lo, uint32_t hi) {
+        return __byte_perm(lo, hi, 0x5410u) ^ 0x80008000u;
     }
 };
 

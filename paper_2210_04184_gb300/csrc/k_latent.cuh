@@ -254,13 +254,6 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int y = y0 + r;
     const bool owner = tid < tpr * Ty;
     const bool active = owner && r < rows;
-    // circular indices that do not depend on the offset or the band, computed once
-    int wcol[VEC + 2 * K];                     // weight columns x0 - K + j
-#pragma unroll
-    for (int j = 0; j < VEC + 2 * K; ++j) wcol[j] = wrap1(x0 - K + j, W);
-    size_t wrow[PS];                           // weight rows y + k1
-#pragma unroll
-    for (int k1 = -K; k1 <= K; ++k1) wrow[k1 + K] = (size_t)wrap1(y + k1, H) * W;
     const size_t xsrow = (size_t)wrap1(y - t1, H) * W;   // row of X(m - tau)
     const size_t pix = (size_t)y * W + x0;
     const size_t kstride = (size_t)Ls * n;
@@ -269,13 +262,11 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     for (int item = 0; item < nb; ++item) {
         const int c = c0 + item;
         const T* Xc = X + (size_t)c * n;
-        T Xm[VEC], A[VEC];
+        T Xm[VEC];
         if (active) vload<T, VEC>(Xc + pix, Xm);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
+        for (int j = 0; j < VEC; ++j)
             if (!active) Xm[j] = T(0);
-            A[j] = T(0);
-        }
         for (int jt = 0; jt < nt2; ++jt) {
             const int t2 = tm.t2_of(t1, jt);
             T Hacc[VEC], delta[VEC];
@@ -288,51 +279,95 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             ST* gp = Sout + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
 #pragma unroll
             for (int k1 = 0; k1 < PS; ++k1) {
-                T mu[VEC + 2 * K];
-                const WT* orow = om + wrow[k1];
+                const WT* orow = om + (size_t)wrap1(y + k1 - K, H) * W;     // weight row y + k1
+                if constexpr (std::is_same<ST, T>::value) {
+                    T mu[VEC + 2 * K];
 #pragma unroll
-                for (int j = 0; j < VEC + 2 * K; ++j) mu[j] = active ? coef * (T)wload(orow + wcol[j]) : T(0);
+                    for (int j = 0; j < VEC + 2 * K; ++j)
+                        mu[j] = active ? coef * (T)wload(orow + wrap1(x0 - K + j, W)) : T(0);
 #pragma unroll
-                for (int k2 = 0; k2 < PS; ++k2) {
-                    const unsigned lim = s_abort ? 64u : limit;
-                    if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
-                    if (active) {
-                        T sv[VEC];
-                        StateIO<T, ST, VEC>::load(ring + (size_t)slot * tile + (size_t)r * W + x0, sv, mu + k2);
+                    for (int k2 = 0; k2 < PS; ++k2) {
+                        const unsigned lim = s_abort ? 64u : limit;
+                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (active) {
+                            T sv[VEC];
+                            vload<T, VEC>(ring + (size_t)slot * tile + (size_t)r * W + x0, sv);
 #pragma unroll
-                        for (int j = 0; j < VEC; ++j) {
-                            const T u = sv[j] - delta[j];
-                            const T m = mu[j + k2];
-                            const T s2 = tmin(tmax(u, -m), m);
-                            Hacc[j] += T(2) * s2 - u;
-                            sv[j] = s2;
+                            for (int j = 0; j < VEC; ++j) {
+                                const T u = sv[j] - delta[j];
+                                const T m = mu[j + k2];
+                                const T s2 = tmin(tmax(u, -m), m);
+                                Hacc[j] += T(2) * s2 - u;
+                                sv[j] = s2;
+                            }
+                            vstore_stream<T, VEC>(gp, sv);
                         }
-                        StateIO<T, ST, VEC>::store(gp, sv, mu + k2);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        gp += kstride;
+                        if (++slot == D) { slot = 0; par ^= 1u; }
                     }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty[slot]);
-                    gp += kstride;
-                    if (++slot == D) { slot = 0; par ^= 1u; }
+                } else {
+                    // 16-bit fixed point (see FixedCode): the update runs in code units of mu/32767,
+                    // where the clamp bounds are +-32767 and the new code is the clamped value
+                    // rounded by one addition; G returns to real units through mu/32767.
+                    static_assert(VEC == 8, "one 16-byte group of codes per thread and chunk");
+                    float mu[VEC + 2 * K];
+#pragma unroll
+                    for (int j = 0; j < VEC + 2 * K; ++j) {
+                        const float w = active ? (float)wload(orow + wrap1(x0 - K + j, W)) : 0.0f;
+                        mu[j] = fmaxf(coef * w, FixedCode::kMinMu);
+                    }
+#pragma unroll
+                    for (int k2 = 0; k2 < PS; ++k2) {
+                        const unsigned lim = s_abort ? 64u : limit;
+                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (active) {
+                            const int4 w = *reinterpret_cast<const int4*>(ring + (size_t)slot * tile + (size_t)r * W + x0);
+                            const uint32_t wd[4] = {(uint32_t)w.x, (uint32_t)w.y, (uint32_t)w.z, (uint32_t)w.w};
+                            uint32_t out[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                uint32_t t[2];
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    const int j = 2 * h + e;
+                                    const float m = mu[j + k2];
+                                    const float q = FixedCode::decode(wd[h], e);
+                                    const float uc = fmaf(-delta[j], __fdividef(FixedCode::kLevels, m), q);  // Sigma - D X
+                                    const float s2c = fminf(fmaxf(uc, -FixedCode::kLevels), FixedCode::kLevels);
+                                    Hacc[j] = fmaf(fmaf(2.0f, s2c, -uc), m * FixedCode::kStep, Hacc[j]);
+                                    t[e] = FixedCode::round_bits(s2c);
+                                }
+                                out[h] = FixedCode::pack(t[0], t[1]);
+                            }
+                            __stcs(reinterpret_cast<int4*>(gp), make_int4((int)out[0], (int)out[1], (int)out[2], (int)out[3]));
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        gp += kstride;
+                        if (++slot == D) { slot = 0; par ^= 1u; }
+                    }
                 }
             }
             if (owner) {
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    A[j] += Hacc[j];
-                    Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
-                }
+                for (int j = 0; j < VEC; ++j) Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
             }
         }
         consumer_barrier(ncons);                 // every H_tau of this band is in Hs
         if (active) {
-            T V[VEC];
+            T A[VEC], V[VEC];
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) V[j] = T(0);
+            for (int j = 0; j < VEC; ++j) { A[j] = T(0); V[j] = T(0); }
             for (int jt = 0; jt < nt2; ++jt) {
                 const int t2 = tm.t2_of(t1, jt);
                 const T* hrow = Hs + ((size_t)(t2 + S) * Ty + r) * W;
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) V[j] += hrow[wrap1(x0 + j + t2, W)];
+                for (int j = 0; j < VEC; ++j) {
+                    A[j] += hrow[x0 + j];
+                    V[j] += hrow[wrap1(x0 + j + t2, W)];
+                }
             }
             vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
             vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
