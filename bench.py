@@ -544,7 +544,7 @@ def run_ours(a, rank, world, local_rank):
     Z = torch.empty((p.L_l, p.H, p.W), dtype=td, device="cuda")
     stream = torch.cuda.current_stream()
 
-    from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream
+    from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream, fuse_conditioning
     fuse_set_stream(f.ctx, stream.cuda_stream)
     fuse_weights(f.ctx, yh.data_ptr())
     if a.no_autotune:
@@ -658,6 +658,7 @@ def run_ours(a, rank, world, local_rank):
         "clocks": clk,
         "e2e": e2e,
         "fp64_compare": fp64,
+        "conditioning": dict(zip(("A_x_update", "EEt_plus_rho", "F_inverse"), fuse_conditioning(f.ctx))),
         "fixed_point_state": fixed,
         "grad": grad,
     }

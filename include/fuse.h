@@ -179,6 +179,16 @@ fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_hos
  * Errors: FUSE_ESTATE (no solve yet), FUSE_ENONFINITE (a term is not finite). */
 fuse_status fuse_objective(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, double out[4]);
 
+/* Spectral condition numbers of the linear systems the iterations solve, computed in FP64 at
+ * fuse_init (host only, no device work):
+ *   out[0]  A = I + B^T B + sum_{tau,k} D_{tau k}^T D_{tau k} (eq. x_linear_system_main),
+ *           diagonal in the DFT basis: max/min of its eigenvalues 1 + |b^|^2 + |P| sum (2 - 2cos)
+ *   out[1]  E E^T + rho I (eq. Qh_update)
+ *   out[2]  I + lambda1/rho E R R^T E^T, the inverse of F (eq. Qm_update)
+ * The iterate-type arithmetic needs condition numbers far below 1/eps of that type (eps = 6e-8
+ * for FP32) for the inverses to keep their accuracy.  Errors: FUSE_EINVAL (NULL). */
+fuse_status fuse_conditioning(fuse_ctx* ctx, double out[3]);
+
 /* Size in bytes of the resumable ADMM state (Lambda1, U1 = P1 + Lambda1, Lambda2,
  * U2 = P2 + Lambda2, X, Sigma, the adjoint partial sums), in that order; Sigma is stored as
  * Sig'[tau][k][c][m] = Sigma_{tau k}(m + k) over the kept offsets (all of W, or W+ in

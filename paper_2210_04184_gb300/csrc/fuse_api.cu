@@ -2,6 +2,7 @@
 // The contract of every entry point is in include/fuse.h.
 #include "fuse.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -95,6 +96,8 @@ struct fuse_ctx {
     long long epoch = 0;
     // host FP64 copies of (E E^T + rho I)^{-1}, F and E R, for the parameter derivatives
     std::vector<double> hM1, hF, hER;
+    // spectral condition numbers of A (eq. inv), E E^T + rho I and F^{-1} (fuse_conditioning)
+    double cond[3] = {0.0, 0.0, 0.0};
     // latent state read / written by the next latent launch (NULL = Sig, in place); set only
     // around directly launched iterations of the taped forward, never while capturing
     void *lat_in = nullptr, *lat_out = nullptr;
@@ -159,6 +162,43 @@ bool plan_fft(int N, FFTPlan* P) {
 }
 
 // In-place inverse of an n x n row-major matrix (Gauss-Jordan, partial pivoting, FP64).
+// Extreme eigenvalues of the symmetric n x n matrix A (cyclic Jacobi rotations until the
+// off-diagonal part is negligible).
+void sym_eig_range(std::vector<double> A, int n, double* lo, double* hi) {
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        }
+        if (off <= 1e-30 * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double th = 0.5 * (aqq - app) / apq;
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {                       // columns p, q
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = cs * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {                       // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = cs * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + cs * aqk;
+                }
+            }
+    }
+    *lo = *hi = A[0];
+    for (int i = 1; i < n; ++i) {
+        *lo = std::min(*lo, A[(size_t)i * n + i]);
+        *hi = std::max(*hi, A[(size_t)i * n + i]);
+    }
+}
+
 bool invert(std::vector<double>& A, int n) {
     std::vector<double> I(n * (size_t)n, 0.0);
     for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
@@ -1173,6 +1213,18 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
             M1[(size_t)i * Ls + j] = s + (i == j ? rho : 0.0);
             Fm[(size_t)i * Ls + j] = cr * t + (i == j ? 1.0 : 0.0);
         }
+    {
+        // conditioning (before inversion): E E^T + rho I and F^{-1} = I + lambda1/rho E R R^T E^T;
+        // A = I + B^T B + sum D^T D is diagonal in the DFT basis with eigenvalues 1/(HW f)
+        double lo, hi;
+        sym_eig_range(M1, Ls, &lo, &hi);
+        c->cond[1] = hi / lo;
+        sym_eig_range(Fm, Ls, &lo, &hi);
+        c->cond[2] = hi / lo;
+        double fmin = fh[0], fmax = fh[0];
+        for (double v : fh) { fmin = std::min(fmin, v); fmax = std::max(fmax, v); }
+        c->cond[0] = fmax / fmin;
+    }
     if (!invert(M1, Ls) || !invert(Fm, Ls)) return bail(FUSE_EINVAL);
     c->hM1 = M1;
     c->hF = Fm;
@@ -1830,6 +1882,12 @@ fuse_status fuse_reset_error(fuse_ctx* c) {
     if (!c) return FUSE_EINVAL;
     c->sticky = FUSE_OK;
     c->err.clear();
+    return FUSE_OK;
+}
+
+fuse_status fuse_conditioning(fuse_ctx* c, double out[3]) {
+    if (!c || !out) return FUSE_EINVAL;
+    for (int q = 0; q < 3; ++q) out[q] = c->cond[q];
     return FUSE_OK;
 }
 

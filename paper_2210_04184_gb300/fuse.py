@@ -82,6 +82,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_batch_autotune": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I]),
         "fuse_selftest": (_ST, [_VP, _I]),
         "fuse_grad_bytes": (_ST, [_VP, _I, ctypes.POINTER(ctypes.c_size_t)]),
+        "fuse_conditioning": (_ST, [_VP, _D]),
         "fuse_grad_forward": (_ST, [_VP, _VP, _VP, _I, _VP]),
         "fuse_grad_backward": (_ST, [_VP, _VP, _VP, _VP, _VP, _D]),
         "fuse_grad": (_ST, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _D]),
@@ -239,6 +240,12 @@ def fuse_phi_static(X_dev: int, omega_dev: int, H: int, W: int, L_s: int, K: int
                     dtype: int, wdtype: int, phi_dev: int, stream: int = 0):
     _check(load().fuse_phi_static(_VP(X_dev), _VP(omega_dev), H, W, L_s, K, S, dtype, wdtype,
                                   _VP(phi_dev), _VP(stream or None)))
+
+
+def fuse_conditioning(ctx) -> tuple[float, float, float]:
+    out = (ctypes.c_double * 3)()
+    _check(load().fuse_conditioning(ctx, out), ctx)
+    return out[0], out[1], out[2]
 
 
 def fuse_grad_bytes(ctx, iters: int) -> int:
