@@ -26,9 +26,9 @@ import numpy as np
 from . import nlpr
 
 
-def forward_tape(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters):
+def forward_tape(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, mask=None):
     """Forward ADMM from zero state keeping every input state and X (images (H, W, L))."""
-    su = nlpr.setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega)
+    su = nlpr.setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, mask)
     st = nlpr.State.zeros(su.H, su.W, su.L_s, K, S)
     tape = []
     for _ in range(iters):
@@ -158,9 +158,9 @@ def weights_vjp(G, K, S, h, omega_bar):
     return Gb
 
 
-def unrolled_grad(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, Xbar_fn):
+def unrolled_grad(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, Xbar_fn, mask=None):
     """Runs the forward tape and the reverse pass; Xbar_fn(X_last) gives dL/dX_last.
     Returns (X_last, grads)."""
-    tape, su, _ = forward_tape(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters)
+    tape, su, _ = forward_tape(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, mask)
     X_last = tape[-1][1]
     return X_last, backward(tape, su, Yl, Yh, Xbar_fn(X_last))

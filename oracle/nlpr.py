@@ -193,12 +193,17 @@ def nlpr(X: np.ndarray, omega: np.ndarray, K: int, S: int) -> float:
     return total
 
 
-def objective(X, Yl, Yh, kern, d, R, E, omega, K, S, lam1, lam2) -> float:
+def objective(X, Yl, Yh, kern, d, R, E, omega, K, S, lam1, lam2, mask=None) -> float:
     """l(X) + lambda2 phi(X), with l(X) = 1/2||Yl - SBXE||^2 + lambda1/2 ||Yh - XER||^2
-    (eq. mainoptim)."""
+    (eq. mainoptim).  mask (H, W) 0/1 with d = 1: S keeps the pixels where mask is 1 and Yl is
+    given at full resolution (its values elsewhere do not enter)."""
     H, W, _ = X.shape
-    SBXE = mat(decimate(blur(X, kern), d)) @ E
-    r1 = mat(Yl) - SBXE
+    if mask is not None:
+        m = mat(mask[:, :, None].astype(float))
+        r1 = m * (mat(Yl) - mat(blur(X, kern)) @ E)
+    else:
+        SBXE = mat(decimate(blur(X, kern), d)) @ E
+        r1 = mat(Yl) - SBXE
     r2 = mat(Yh) - mat(X) @ E @ R
     return 0.5 * float((r1 * r1).sum()) + 0.5 * lam1 * float((r2 * r2).sum()) \
         + lam2 * nlpr(X, omega, K, S)
@@ -325,17 +330,27 @@ class Setup:
     mask: np.ndarray        # diag(S^T S) as (H, W)
 
 
-def setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega) -> Setup:
-    """Yl: (H/d, W/d, L_l), Yh: (H, W, L_h), E: (L_s, L_l), R: (L_l, L_h)."""
+def setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, mask=None) -> Setup:
+    """Yl: (H/d, W/d, L_l), Yh: (H, W, L_h), E: (L_s, L_l), R: (L_l, L_h).
+
+    mask: optional (H, W) 0/1 array with d = 1 for a general sampling operator S that keeps the
+    pixels where mask is 1 (for example a random inpainting mask); Yl is then (H, W, L_l) and
+    S^T S = diag(mask), S^T Y_l = mask * Y_l.  Eq. Qh_update holds for any such S."""
     H, W = Yh.shape[:2]
     L_s = E.shape[0]
     inv_p1 = np.linalg.inv(E @ E.T + rho * np.eye(L_s))
     F = np.linalg.inv(np.eye(L_s) + (lam1 / rho) * (E @ R @ R.T @ E.T))
-    SYlEt = decimate_t(img(mat(Yl) @ E.T, H // d, W // d), d, H, W)
+    if mask is not None:
+        if d != 1:
+            raise ValueError("a sampling mask needs d = 1")
+        smask = np.asarray(mask, dtype=float)
+        SYlEt = smask[:, :, None] * img(mat(Yl) @ E.T, H, W)
+    else:
+        smask = sampling_mask(H, W, d)
+        SYlEt = decimate_t(img(mat(Yl) @ E.T, H // d, W // d), d, H, W)
     YhRtEt = img(mat(Yh) @ R.T @ E.T, H, W)
     return Setup(H, W, L_s, d, K, S, lam1, lam2, rho, kern, E, R, omega,
-                 x_denominator(H, W, kern, K, S), inv_p1, F, SYlEt, YhRtEt,
-                 sampling_mask(H, W, d))
+                 x_denominator(H, W, kern, K, S), inv_p1, F, SYlEt, YhRtEt, smask)
 
 
 def dt_sum(Q: np.ndarray, Sig: np.ndarray, K: int, S: int) -> np.ndarray:
@@ -420,7 +435,7 @@ def quantize_state(Sig: np.ndarray, omega: np.ndarray, lam2: float, rho: float, 
 
 
 def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
-         x_solver=None, fast=False, callback=None, inplace=False, state_levels=None):
+         x_solver=None, fast=False, callback=None, inplace=False, state_levels=None, mask=None):
     """Run `iters` ADMM iterations from `state` (zero initialisation by default).
 
     Images in (H, W, L) layout.  fast=True uses the C loops of oracle/loops.c for the
@@ -429,8 +444,9 @@ def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
     so large problems hold one copy of the latent variables.
     state_levels: Sigma enters the Q and Sigma updates as stored in fixed point
     (quantize_state); the right-hand side still sums the exact Q + Sigma of the last update.
+    mask: general sampling operator (see setup).
     Returns (X, state, setup)."""
-    su = setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega)
+    su = setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, mask)
     if state is not None:
         st = state if inplace else state.copy()
     else:

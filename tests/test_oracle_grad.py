@@ -113,3 +113,35 @@ def test_weights_vjp_matches_central_differences_of_the_weights():
     fd = (float((V * nlpr.weights(G + e * d, K, S, hw)).sum()) -
           float((V * nlpr.weights(G - e * d, K, S, hw)).sum())) / (2 * e)
     assert abs(fd - float((Gb * d).sum())) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_reverse_pass_with_a_sampling_mask():
+    # a random sampling mask (d = 1): dL/dY_l vanishes off the mask and matches central differences
+    p = _tiny(48, d=1)
+    rng = np.random.default_rng(49)
+    mask = (rng.random((6, 8)) < 0.4).astype(float)
+    p["Yl"] = rng.random((6, 8, 3))
+    Wt = rng.standard_normal((6, 8, 2))
+    iters = 4
+
+    def loss(q):
+        X, _, _ = nlpr.admm(q["Yl"], q["Yh"], q["kern"], 1, q["R"], q["E"], q["K"], q["S"], q["lam1"],
+                            q["lam2"], q["rho"], q["omega"], iters, mask=mask)
+        return float((Wt * X).sum())
+
+    X, g = grad.unrolled_grad(p["Yl"], p["Yh"], p["kern"], 1, p["R"], p["E"], p["K"], p["S"], p["lam1"],
+                              p["lam2"], p["rho"], p["omega"], iters, lambda X: Wt, mask=mask)
+    assert not g["Yl"][mask == 0].any()
+    h = 1e-6
+    for key in ("Yl", "Yh", "rho"):
+        if key == "rho":
+            qp = dict(p); qp[key] = p[key] + h
+            qm = dict(p); qm[key] = p[key] - h
+            an = g[key]
+        else:
+            dirn = rng.standard_normal(p[key].shape)
+            qp = dict(p); qp[key] = p[key] + h * dirn
+            qm = dict(p); qm[key] = p[key] - h * dirn
+            an = float((g[key] * dirn).sum())
+        fd = (loss(qp) - loss(qm)) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (key, fd, an)

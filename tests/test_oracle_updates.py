@@ -218,3 +218,47 @@ def test_fixed_point_state_storage():
     X2, _, _ = nlpr.admm(*args, state_levels=lev)
     assert np.abs(X1 - X0).max() <= 1e-11
     assert 0 < np.abs(X2 - X0).max() <= 1e-4 * np.abs(X0).max()
+
+
+def test_sampling_mask_generalises_the_lattice():
+    # S given as a 0/1 mask (d = 1, Y_l at full resolution): the lattice pattern of d = 2 with
+    # Y_l placed on it reproduces the regular d = 2 run exactly, and an all-ones mask the d = 1 run
+    rng = _rng(71)
+    H, W, d = 8, 12, 2
+    E, R, Yl, Yh = _problem(rng, H, W, d=d)
+    kern = _kernel(rng)
+    om = nlpr.weights(Yh, 1, 1, 0.5)
+    args = (kern, d, R, E, 1, 1, 0.8, 0.05, 0.3, om, 5)
+    X_reg, _, _ = nlpr.admm(Yl, Yh, *args)
+    mask = nlpr.sampling_mask(H, W, d)
+    Yl_full = nlpr.decimate_t(Yl, d, H, W) + 7.0 * (1.0 - mask)[:, :, None]   # off-mask values unused
+    X_mask, _, _ = nlpr.admm(Yl_full, Yh, kern, 1, R, E, 1, 1, 0.8, 0.05, 0.3, om, 5, mask=mask)
+    assert np.abs(X_mask - X_reg).max() <= 1e-12 * np.abs(X_reg).max()
+    Yl1 = rng.random((H, W, Yl.shape[2]))
+    X1, _, _ = nlpr.admm(Yl1, Yh, kern, 1, R, E, 1, 1, 0.8, 0.05, 0.3, om, 4)
+    X1m, _, _ = nlpr.admm(Yl1, Yh, kern, 1, R, E, 1, 1, 0.8, 0.05, 0.3, om, 4, mask=np.ones((H, W)))
+    assert np.abs(X1m - X1).max() <= 1e-12 * np.abs(X1).max()
+
+
+def test_p1_update_with_a_random_mask_solves_its_subproblem():
+    # eq. P1_update_problem with S = the rows of I at a random set of pixels
+    rng = _rng(72)
+    H, W, rho = 8, 8, 0.37
+    E, R, _, Yh = _problem(rng, H, W, d=1)
+    L_s = E.shape[0]
+    kern = _kernel(rng)
+    mask = (rng.random((H, W)) < 0.3).astype(float)
+    Yl = rng.random((H, W, E.shape[1]))
+    su = nlpr.setup(Yl, Yh, kern, 1, R, E, 1, 1, 0.8, 0.1, rho, rng.random((8, H, W)), mask)
+    st = nlpr.State.zeros(H, W, L_s, 1, 1)
+    st.Lam1 = rng.standard_normal((H, W, L_s))
+    X = rng.standard_normal((H, W, L_s))
+    P1, _ = nlpr.update_p1(X, st, su)
+    keep = mask.reshape(-1) > 0
+    A = _vec_map(lambda P: nlpr.mat(P)[keep] @ E, (H, W, L_s))
+    n = A.shape[1]
+    lhs = np.vstack([A, np.sqrt(rho) * np.eye(n)])
+    V = nlpr.blur(X, kern) - st.Lam1
+    rhs = np.concatenate([nlpr.mat(Yl)[keep].reshape(-1), np.sqrt(rho) * V.reshape(-1)])
+    ref = np.linalg.lstsq(lhs, rhs, rcond=None)[0].reshape(H, W, L_s)
+    assert np.abs(P1 - ref).max() <= 1e-10 * np.abs(ref).max()
