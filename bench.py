@@ -231,6 +231,8 @@ def fp64_compare(p, meta, f32ctx, yl, yh, Z32):
     yl64, yh64 = yl.double(), yh.double()
     Z64 = torch.empty((p.L_l, p.H, p.W), dtype=torch.float64, device="cuda")
     f64 = Fusion.from_problem(p, dtype="f64", wdtype="f64")
+    if "mask" in meta:
+        f64.set_mask(meta["mask"])
     it64 = timed(f64, yl64, yh64, Z64)
     f64.close()
     it32 = timed(f32ctx, yl, yh, Z32)
@@ -240,6 +242,8 @@ def fp64_compare(p, meta, f32ctx, yl, yh, Z32):
            "rel_err_Z_fp32_vs_fp64": err32, "fp32_weights": meta["wdtype"]}
     if meta["wdtype"] != "f32":
         fw = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+        if "mask" in meta:
+            fw.set_mask(meta["mask"])
         Zw = torch.empty_like(Z32)
         timed(fw, yl, yh, Zw)
         fw.close()
@@ -257,6 +261,8 @@ def fixed_point_bench(a, p, meta, yl, yh, Z64):
                                              fuse_solve, fuse_weights, fuse_set_stream)
     f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
     f.set_option(FUSE_OPT_STATE_FORMAT, 1)
+    if "mask" in meta:
+        f.set_mask(meta["mask"])
     st = torch.cuda.current_stream()
     fuse_set_stream(f.ctx, st.cuda_stream)
     fuse_weights(f.ctx, yh.data_ptr())
@@ -539,6 +545,8 @@ def run_ours(a, rank, world, local_rank):
     if a.fixed_state:
         from paper_2210_04184_gb300.fuse import FUSE_OPT_STATE_FORMAT
         f.set_option(FUSE_OPT_STATE_FORMAT, 1)
+    if "mask" in meta:
+        f.set_mask(meta["mask"])            # random sampling operator (inpainting workload)
     yl = torch.tensor(p.Yl, dtype=td, device="cuda")
     yh = torch.tensor(p.Yh, dtype=td, device="cuda")
     Z = torch.empty((p.L_l, p.H, p.W), dtype=td, device="cuda")

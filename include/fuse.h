@@ -179,6 +179,16 @@ fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_hos
  * Errors: FUSE_ESTATE (no solve yet), FUSE_ENONFINITE (a term is not finite). */
 fuse_status fuse_objective(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, double out[4]);
 
+/* General sampling operator: S keeps the pixels where mask is nonzero instead of the regular
+ * lattice (for example a random inpainting mask).  Needs ratio 1 (FUSE_EINVAL otherwise); Y_l
+ * is then given at full resolution [L_l][H][W] and its values off the mask do not enter.  S^T S
+ * is diagonal either way, so eq. Qh_update and the X update of eq. inv are unchanged; the
+ * objective's data term and the reverse pass use the same S.
+ *   mask  [H][W] uint8 (host or device; copied, cudaMemcpyDefault), NULL = back to the lattice.
+ * Asynchronous on the context stream.  A batch takes its contexts' masks when it is created.
+ * Errors: FUSE_EINVAL, FUSE_ENOMEM, FUSE_ECUDA. */
+fuse_status fuse_set_mask(fuse_ctx* ctx, const void* mask);
+
 /* Spectral condition numbers of the linear systems the iterations solve, computed in FP64 at
  * fuse_init (host only, no device work):
  *   out[0]  A = I + B^T B + sum_{tau,k} D_{tau k}^T D_{tau k} (eq. x_linear_system_main),

@@ -123,6 +123,13 @@ struct FixedCode {
     }
 };
 
+// The pixels kept by the sampling operator S: the lattice i1 = i2 = 0 (mod d), or, when a mask
+// is given (then d = 1), the pixels where the mask is nonzero (for example a random inpainting
+// mask); S^T S is diagonal either way, which is all eq. Qh_update needs.
+__device__ __forceinline__ bool sampled_pixel(const uint8_t* mask, size_t p, int y, int x, int d) {
+    return mask ? mask[p] != 0 : ((y % d) == 0 && (x % d) == 0);
+}
+
 // Offsets of the search window W = [-S, S]^2 \ {0} handled by one latent block row tau1
 // (blockIdx.z).  Full mode: tau1 in [-S, S], all tau2 (skipping (0,0)); state index =
 // row-major index in W.

@@ -89,6 +89,10 @@ struct fuse_ctx {
     int half = 1;
     // latent state storage: 0 = the iterate type, 1 = 16-bit fixed point relative to mu
     int sfmt = 0;
+    // sampling mask [H][W] (uint8, ratio 1) replacing the regular lattice; NULL = lattice.
+    // The buffer (mask_buf) is kept once allocated, so launch arguments taken earlier (a batch)
+    // never point to freed memory.
+    void *mask = nullptr, *mask_buf = nullptr;
     // reverse pass: workspace, iterations per checkpointed segment (0 = one segment), a counter
     // bumped by every call that changes inputs or state (a taped forward is valid while unchanged)
     GradWork* gw = nullptr;
@@ -411,7 +415,7 @@ struct Impl {
     static PixelArgs<T> px_args(fuse_ctx* c) {
         return PixelArgs<T>{(const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2,
                             (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1, (const T*)c->F,
-                            c->H, c->W, c->Ls, c->d, (T)c->rho};
+                            c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask};
     }
     template <typename WT>
     static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb) {
@@ -583,7 +587,7 @@ fuse_status Impl<T>::objective(fuse_ctx* c, const void* Yl, const void* Yh, doub
     const unsigned nb = (unsigned)((n + 255) / 256);
     obj_data_kernel<T><<<nb, 256, 0, c->stream>>>((const T*)c->X, (const T*)c->BX, (const T*)Yl, (const T*)Yh,
                                                    c->objE, c->objER, c->H, c->W, c->d, c->Ls, c->Ll, c->Lh,
-                                                   c->partial);
+                                                   c->partial, (const uint8_t*)c->mask);
     double* phi_part = c->partial + (size_t)nb * 3;
     dim3 pgrid(nb, (unsigned)c->nW);
     if constexpr (sizeof(T) == 8) {
@@ -1882,6 +1886,24 @@ fuse_status fuse_reset_error(fuse_ctx* c) {
     if (!c) return FUSE_EINVAL;
     c->sticky = FUSE_OK;
     c->err.clear();
+    return FUSE_OK;
+}
+
+fuse_status fuse_set_mask(fuse_ctx* c, const void* mask) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (mask && c->d != 1) return fail(c, FUSE_EINVAL, "a sampling mask needs ratio 1");
+    if (!mask) {
+        c->mask = nullptr;
+    } else {
+        if (!c->mask_buf && (st = dalloc(c, &c->mask_buf, c->n)) != FUSE_OK) return st;
+        CK(c, cudaMemcpyAsync(c->mask_buf, mask, c->n, cudaMemcpyDefault, c->stream));
+        c->mask = c->mask_buf;
+    }
+    // the pixel launches carry the mask pointer: drop the captured iteration graph
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    ++c->epoch;
     return FUSE_OK;
 }
 

@@ -294,7 +294,7 @@ struct GradImpl {
                                 (const T*)g->U1b, (const T*)g->Cb, (T*)g->L1b, (T*)g->L2b, (T*)g->Xp, (T*)g->BXb,
                                 (T*)g->D9ab, (T*)g->D9bb, (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1,
                                 (const T*)c->F, (const T*)g->Krho, (const T*)g->Klam, (const T*)g->Kmu,
-                                g->px_part, c->H, c->W, c->Ls, c->d, (T)c->rho};
+                                g->px_part, c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask};
         const unsigned blocks = (unsigned)((c->n + 127) / 128);
         with_maxls(c->Ls, [&](auto m) {
             constexpr int M = decltype(m)::value;

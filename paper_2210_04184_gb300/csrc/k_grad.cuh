@@ -176,6 +176,7 @@ struct PixelBwdArgs {
     double* part;      // [blocks][3] += see pixel_bwd_kernel
     int H, W, Ls, d;
     T rho;
+    const uint8_t* mask;   // sampling mask [H][W] (d = 1) or NULL for the lattice of ratio d
 };
 
 // One thread per pixel, band vectors in registers (MAXLS >= L_s).  Per block, part[3 b + q] +=
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
                 a[j] = g.BX[(size_t)j * n + p] - g.Lam1[(size_t)j * n + p];      // w1
             }
         }
-        if ((y % d) == 0 && (x % d) == 0) {
+        if (sampled_pixel(g.mask, p, y, x, d)) {
             const size_t nl = (size_t)(H / d) * (W / d);
             const size_t pl = (size_t)(y / d) * (W / d) + x / d;
 #pragma unroll

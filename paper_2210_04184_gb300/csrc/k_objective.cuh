@@ -34,12 +34,14 @@ __device__ void block_sum(double (&v)[NV], double* out) {
     }
 }
 
-// partial[blockIdx.x * 3 + {0,1,2}] = sums of (Y_l - S B X E)^2, (Y_h - X E R)^2, X^2.
+// partial[blockIdx.x * 3 + {0,1,2}] = sums of (Y_l - S B X E)^2, (Y_h - X E R)^2, X^2 (with a
+// sampling mask, Y_l is full resolution and only the masked pixels enter).
 template <typename T>
 __global__ void __launch_bounds__(256)
 obj_data_kernel(const T* __restrict__ X, const T* __restrict__ BX, const T* __restrict__ Yl,
                 const T* __restrict__ Yh, const double* __restrict__ E, const double* __restrict__ ER,
-                int H, int W, int d, int Ls, int Ll, int Lh, double* __restrict__ partial) {
+                int H, int W, int d, int Ls, int Ll, int Lh, double* __restrict__ partial,
+                const uint8_t* __restrict__ mask) {
     const size_t n = (size_t)H * W;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v[3] = {0.0, 0.0, 0.0};
@@ -51,7 +53,7 @@ obj_data_kernel(const T* __restrict__ X, const T* __restrict__ BX, const T* __re
             for (int c = 0; c < Ls; ++c) r -= (double)X[c * n + p] * ER[c * Lh + h];
             v[1] += r * r;
         }
-        if ((y % d) == 0 && (x % d) == 0) {
+        if (sampled_pixel(mask, p, y, x, d)) {
             const size_t nl = (size_t)(H / d) * (W / d);
             const size_t pl = (size_t)(y / d) * (W / d) + x / d;
             for (int l = 0; l < Ll; ++l) {

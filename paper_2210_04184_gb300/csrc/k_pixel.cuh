@@ -28,6 +28,7 @@ struct PixelArgs {
     const T* F;
     int H, W, Ls, d;
     T rho;
+    const uint8_t* mask;   // sampling mask [H][W] (d = 1) or NULL for the lattice of ratio d
 };
 
 template <typename T, int MAXLS>
@@ -76,7 +77,7 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
     for (int j = 0; j < MAXLS; ++j)
         if (j < Ls) w[j] = BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p];
     const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
-    if ((y % d) == 0 && (x % d) == 0) {
+    if (sampled_pixel(args.mask, p, y, x, d)) {
         const size_t nl = (size_t)(H / d) * (W / d);
         const size_t pl = (size_t)(y / d) * (W / d) + x / d;
 #pragma unroll
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(128) pixel_kernel_wide(PixelArgs<T> args) {
         U2[c * n + p] = acc + l2;
     }
     const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
-    if ((y % d) == 0 && (x % d) == 0) {
+    if (sampled_pixel(args.mask, p, y, x, d)) {
         const size_t nl = (size_t)(H / d) * (W / d);
         const size_t pl = (size_t)(y / d) * (W / d) + x / d;
         for (int j = 0; j < Ls; ++j) a[j * nb + tid] = rho * (BX[j * n + p] - Lam1[j * n + p]) + D9a[j * nl + pl];

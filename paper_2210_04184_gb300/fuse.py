@@ -83,6 +83,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_selftest": (_ST, [_VP, _I]),
         "fuse_grad_bytes": (_ST, [_VP, _I, ctypes.POINTER(ctypes.c_size_t)]),
         "fuse_conditioning": (_ST, [_VP, _D]),
+        "fuse_set_mask": (_ST, [_VP, _VP]),
         "fuse_grad_forward": (_ST, [_VP, _VP, _VP, _I, _VP]),
         "fuse_grad_backward": (_ST, [_VP, _VP, _VP, _VP, _VP, _D]),
         "fuse_grad": (_ST, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _D]),
@@ -240,6 +241,10 @@ def fuse_phi_static(X_dev: int, omega_dev: int, H: int, W: int, L_s: int, K: int
                     dtype: int, wdtype: int, phi_dev: int, stream: int = 0):
     _check(load().fuse_phi_static(_VP(X_dev), _VP(omega_dev), H, W, L_s, K, S, dtype, wdtype,
                                   _VP(phi_dev), _VP(stream or None)))
+
+
+def fuse_set_mask(ctx, mask_ptr: int | None):
+    _check(load().fuse_set_mask(ctx, _VP(mask_ptr or None)), ctx)
 
 
 def fuse_conditioning(ctx) -> tuple[float, float, float]:
@@ -495,6 +500,21 @@ class Fusion:
         fuse_grad_weights(self.ctx, ob.data_ptr(), g.data_ptr() if g is not None else None,
                           gb.data_ptr() if gb is not None else None)
         return ob, gb
+
+    def set_mask(self, mask):
+        """Sampling mask (H, W) of 0/1 (any integer or bool array or tensor; ratio 1), or None for
+        the regular lattice; Y_l is then given at full resolution."""
+        if mask is None:
+            fuse_set_mask(self.ctx, None)
+            return
+        t = self.torch
+        m = t.as_tensor(np.asarray(mask.cpu() if isinstance(mask, t.Tensor) else mask) != 0,
+                        dtype=t.uint8).contiguous()
+        if tuple(m.shape) != (self.H, self.W):
+            raise ValueError(f"expected a mask of shape {(self.H, self.W)}")
+        self._sync_stream()
+        fuse_set_mask(self.ctx, m.data_ptr())
+        self.sync()                     # the host copy is read by the asynchronous copy
 
     def params(self):
         """(lambda1, lambda2, rho) of the context as a float64 CPU tensor, for unrolled()."""

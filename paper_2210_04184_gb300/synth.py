@@ -210,7 +210,19 @@ WORKLOADS = {
     "unrolled_256": dict(H=256, W=256, L_l=31, L_h=3, L_s=8, d=4, blur_size=9, blur_sigma=1.5,
                          snr_l=35.0, snr_h=35.0, K=1, S=1, iters=20, kind="hsms",
                          dtype="f32", wdtype="f32", cfg=3),
+    # Guided inpainting (a variant of the same ADMM): Z 256x256x31, 20% of the pixels observed at
+    # random (S a random mask, no blur), an MS guide of 3 bands, patch 3x3, search 7x7, 100
+    # iterations, L_s = 8, BF16 weights.
+    "inpaint_256": dict(H=256, W=256, L_l=31, L_h=3, L_s=8, d=1, blur_size=1, blur_sigma=1.0,
+                        snr_l=35.0, snr_h=35.0, K=1, S=3, iters=100, kind="hsms",
+                        dtype="f32", wdtype="bf16", cfg=5, mask_fraction=0.2),
 }
+
+
+def sampling_mask(H: int, W: int, fraction: float, seed: int) -> np.ndarray:
+    """A seeded random 0/1 mask (uint8, H x W) keeping about `fraction` of the pixels."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((H, W)) < fraction).astype(np.uint8)
 
 
 def workload(name: str, **override) -> tuple[Problem, dict]:
@@ -219,8 +231,12 @@ def workload(name: str, **override) -> tuple[Problem, dict]:
     spec.update(override)
     dtype = spec.pop("dtype"); wdtype = spec.pop("wdtype"); cfg = spec.pop("cfg")
     seed = spec.pop("seed", SEED_BASE + cfg)
+    frac = spec.pop("mask_fraction", None)
     p = make_problem(seed=seed, name=name, **spec)
-    return p, dict(dtype=dtype, wdtype=wdtype, seed=seed)
+    meta = dict(dtype=dtype, wdtype=wdtype, seed=seed)
+    if frac is not None:
+        meta["mask"] = sampling_mask(p.H, p.W, frac, seed + 1)
+    return p, meta
 
 
 def batch_sizes(n: int = 64, seed: int = SEED_BASE + 4) -> list[int]:
