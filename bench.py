@@ -34,7 +34,7 @@ METRIC = "ADMM throughput (megapixel*band*iter/s)"
 # ncu capture summarised in profiles/latent_tma_kernel_hsms128.md (128x128 case, the same kernel
 # and launch shape), per pixel; scaled to the workload by its pixel count (the traffic is
 # proportional to it).  Must be re-measured whenever the latent kernel changes.
-LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.676864e6 + 739.627264e6) / (128 * 128)}
+LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.702720e6 + 738.255872e6) / (128 * 128)}
 UNIT = "Mpx*band*iter/s"
 
 
