@@ -139,6 +139,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of a host float over all ranks (the max-over-ranks timing of a weak-
+    scaling run: every rank solves its own problems, and no collective touches the data path)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def latent_bytes(p, esz, wsz, half=True, ssz=None):
     """Algorithmic bytes of one latent-pass launch: state read + write over the kept offsets
     (half of the window in half-window mode; ssz bytes per stored entry, default esz), their
@@ -360,14 +376,11 @@ def run_batch(a, rank, world, local_rank):
     _, launches = batch.profile(FUSE_K_ALL)
     batch.set_option(FUSE_OPT_PROFILE, 0)
     batch.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     px = sum(p.H * p.W for p in ps)
     Ls = ps[0].L_s
     units = px / 1e6 * Ls * iters * a.steps * world
-    value = units / (ms / 1e3)
+    value = job_value(units / world, world, ms / 1e3)
 
     # end to end: pinned host inputs copied in, Z of every problem read back, each step
     e2e = None
@@ -387,10 +400,12 @@ def run_batch(a, rank, world, local_rank):
             torch.cuda.synchronize()
 
         e2e_step()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             e2e_step()
-        dt = time.perf_counter() - t0
+        dt = max_over_ranks(time.perf_counter() - t0, dist)
         e2e = {"value": units / dt, "unit": UNIT,
                "h2d_bytes_per_step": sum(h.numel() * 4 for h in hyl) + sum(h.numel() * 4 for h in hyh),
                "d2h_bytes_per_step": sum(h.numel() * 4 for h in hz)}
@@ -593,12 +608,9 @@ def run_ours(a, rank, world, local_rank):
     lat_ms, lat_n = f.profile(FUSE_K_LATENT)
     _, launches = f.profile(FUSE_K_ALL)
     f.set_option(FUSE_OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     units = p.H * p.W / 1e6 * p.L_s * p.iters * a.steps * world
-    value = units / (ms / 1e3)
+    value = job_value(units / world, world, ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned inputs, Z read back each step)
     e2e = None
@@ -617,10 +629,7 @@ def run_ours(a, rank, world, local_rank):
         for _ in range(a.steps):
             fuse_run_host(f.ctx, hyl.data_ptr(), hyh.data_ptr(), None, p.iters, None, hz.data_ptr())
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist)
         e2e = {"value": units / dt, "unit": UNIT,
                "h2d_bytes_per_step": hyl.numel() * hyl.element_size() + hyh.numel() * hyh.element_size(),
                "d2h_bytes_per_step": hz.numel() * hz.element_size()}
