@@ -117,3 +117,32 @@ def test_batch_autotune_keeps_results():
     batch.sync()
     for a, b in zip(ref, got):
         assert torch.equal(a, b)
+
+
+def test_batch64_full_size_sampled():
+    # the batched workload at its full size (64 problems of 96..384 pixels a side, 100
+    # iterations, BF16 weights) in the bench's launch configuration: every problem finite,
+    # sampled problems equal to their single-problem solves bit for bit, and the smallest
+    # against the oracle (with the GPU's BF16 weights)
+    ps = synth.batch_workload(64)
+    iters = ps[0].iters
+    fs, yl, yh = _contexts(ps, "f32", "bf16")
+    batch = FusionBatch(fs)
+    batch.autotune(yl, yh, iters=1)
+    Xs, _ = batch.solve(yl, yh, iters)
+    batch.sync()
+    for X in Xs:
+        assert bool(torch.isfinite(X).all())
+    order = sorted(range(len(ps)), key=lambda i: ps[i].H)
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        X, _ = fs[i].solve(yl[i], yh[i], iters)
+        fs[i].sync()
+        assert torch.equal(X, Xs[i])
+    i = order[0]
+    p = ps[i]
+    om = fs[i].get_weights().double().cpu().numpy()
+    Xo, _, _ = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S, p.lam1, p.lam2,
+                         p.rho, om, iters, fast=True, inplace=True)
+    Xg = Xs[i].double().cpu().numpy()
+    assert np.linalg.norm(Xg - nlpr.to_lhw(Xo)) / np.linalg.norm(Xo) <= 1e-5
+    batch.close()

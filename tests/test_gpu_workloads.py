@@ -130,3 +130,78 @@ def test_hspan_parameters_on_crop():
     om = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
     Xo = _oracle(p, 8, om)
     assert rel(X, Xo) <= 1e-5
+
+
+def test_hspan_full_size_sampled():
+    # HS+PAN at its full size (512 x 512, 128 bands -> L_s 20, 11x11 blur, K = 2, S = 5,
+    # 120 offsets).  The oracle cannot hold its latent state (252 GB in FP64), so it computes
+    # the first two iterations' images in full (X_2 only needs the pixel updates of iteration 1:
+    # X_1 = 0 leaves the latent state at 0) and the latent state after iteration 2 entry by entry
+    # on a sample: Sigma'(tau, k, c, m) = -clamp(X_2(m) - X_2(m - tau), lambda2 omega_tau(m+k)/rho).
+    p, meta = synth.workload("hspan_512")
+    X, _, f = _gpu(p, 2, meta["dtype"], meta["wdtype"])
+    Yl, Yh = nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh)
+    dummy = np.zeros((1, 1, 1))
+    su = nlpr.setup(Yl, Yh, p.blur, p.d, p.R, p.E, p.K, p.S, p.lam1, p.lam2, p.rho, dummy)
+    st = nlpr.State(*(np.zeros((p.H, p.W, p.L_s)) for _ in range(4)), Q=np.zeros(1), Sig=np.zeros(1))
+    X1 = np.zeros((p.H, p.W, p.L_s))
+    P1, BX = nlpr.update_p1(X1, st, su)
+    P2 = nlpr.update_p2(X1, st, su)
+    L1, L2 = -(BX - P1), -(X1 - P2)
+    X2 = nlpr.solve_x(nlpr.blur_t(P1 + L1, p.blur) + P2 + L2, su.denom)
+    assert rel(X, nlpr.to_lhw(X2)) <= 1e-5
+    om = f.get_weights().double().cpu().numpy()
+    state = f.get_state()
+    n, Ls = p.H * p.W, p.L_s
+    img = n * Ls
+    offs = nlpr.search_offsets(p.S)
+    kept = [t for t, tau in enumerate(offs) if tau[0] > 0 or (tau[0] == 0 and tau[1] > 0)]
+    poffs = nlpr.patch_offsets(p.K)
+    sig = state[5 * img * 4:(5 * img + len(kept) * len(poffs) * img) * 4].view(torch.float32)
+    sig = sig.reshape(len(kept), len(poffs), Ls, p.H, p.W)
+    rng = np.random.default_rng(6)
+    coef = p.lam2 / p.rho
+    # the clamp is 1-Lipschitz, so an entry differs by at most the FP32 error of its difference
+    # of X_2 values (absolute, X ~ 1) plus the rounding of the threshold
+    xs = np.abs(X2).max()
+    nz = 0
+    for _ in range(3000):
+        j = int(rng.integers(len(kept))); kk = int(rng.integers(len(poffs)))
+        c = int(rng.integers(Ls)); y = int(rng.integers(p.H)); x = int(rng.integers(p.W))
+        tau, k = offs[kept[j]], poffs[kk]
+        mu = coef * om[kept[j], (y + k[0]) % p.H, (x + k[1]) % p.W]
+        v = X2[y, x, c] - X2[(y - tau[0]) % p.H, (x - tau[1]) % p.W, c]
+        want = -min(max(v, -mu), mu)
+        got = float(sig[j, kk, c, y, x].item())
+        assert abs(got - want) <= 1e-6 * mu + 5e-6 * xs, (got, want, mu)
+        nz += want != 0.0
+    assert nz > 0
+
+
+def test_hspan_full_size_fp32_vs_fp64_and_invariant():
+    # the benchmark's 200 iterations at full size: FP32 (BF16 weights) against the FP64 GPU form
+    # within the equal-error bound, and |Sigma'| <= mu on sampled state entries
+    p, meta = synth.workload("hspan_512")
+    X32, Z32, f = _gpu(p, p.iters, meta["dtype"], meta["wdtype"])
+    assert np.all(np.isfinite(Z32))
+    st = f.get_state()
+    om = f.get_weights().double().cpu().numpy()
+    n, Ls = p.H * p.W, p.L_s
+    img = n * Ls
+    offs = nlpr.search_offsets(p.S)
+    kept = [t for t, tau in enumerate(offs) if tau[0] > 0 or (tau[0] == 0 and tau[1] > 0)]
+    poffs = nlpr.patch_offsets(p.K)
+    sig = st[5 * img * 4:(5 * img + len(kept) * len(poffs) * img) * 4].view(torch.float32)
+    sig = sig.reshape(len(kept), len(poffs), Ls, p.H, p.W)
+    rng = np.random.default_rng(7)
+    coef = np.float32(p.lam2 / p.rho)
+    for _ in range(3000):
+        j = int(rng.integers(len(kept))); kk = int(rng.integers(len(poffs)))
+        c = int(rng.integers(Ls)); y = int(rng.integers(p.H)); x = int(rng.integers(p.W))
+        k = poffs[kk]
+        mu = coef * np.float32(om[kept[j], (y + k[0]) % p.H, (x + k[1]) % p.W])
+        assert abs(float(sig[j, kk, c, y, x].item())) <= mu * (1 + 1e-6)
+    del st, sig, f
+    torch.cuda.empty_cache()
+    X64, Z64, _ = _gpu(p, p.iters, "f64", "f64")
+    assert rel(Z32, Z64) <= 1e-4
