@@ -11,6 +11,8 @@ namespace fuse {
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 // Circular index for any a.
 __device__ __forceinline__ int wrapn(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+// Circular index for any a, without a division when a lies in [-n, 2n).
+__device__ __forceinline__ int wrapc(int a, int n) { return (a >= -n && a < 2 * n) ? wrap1(a, n) : wrapn(a, n); }
 
 template <typename T> struct cplx { T x, y; };
 

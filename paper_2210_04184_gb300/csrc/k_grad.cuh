@@ -186,6 +186,21 @@ struct PixelBwdArgs {
 template <typename T, int MAXLS>
 __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
     const int H = g.H, W = g.W, Ls = g.Ls, d = g.d;
+    // the five L_s x L_s matrices, read uniformly by the warp, staged in shared memory
+    __shared__ T sm[5][MAXLS * MAXLS];
+    for (int i = threadIdx.x; i < Ls * Ls; i += blockDim.x) {
+        sm[0][i] = g.F[i];
+        sm[1][i] = g.Krho[i];
+        sm[2][i] = g.Klam[i];
+        sm[3][i] = g.M1[i];
+        sm[4][i] = g.Kmu[i];
+    }
+    __syncthreads();
+    const T* __restrict__ sF = sm[0];
+    const T* __restrict__ sKr = sm[1];
+    const T* __restrict__ sKl = sm[2];
+    const T* __restrict__ sM1 = sm[3];
+    const T* __restrict__ sKm = sm[4];
     const size_t n = (size_t)H * W;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double q[3] = {0.0, 0.0, 0.0};
@@ -208,9 +223,9 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
 #pragma unroll
                 for (int j = 0; j < MAXLS; ++j) {
                     if (j < Ls) {
-                        ab += pb[j] * g.F[i * Ls + j];
-                        kr += g.Krho[i * Ls + j] * pb[j];
-                        kl += g.Klam[i * Ls + j] * pb[j];
+                        ab += pb[j] * sF[i * Ls + j];
+                        kr += sKr[i * Ls + j] * pb[j];
+                        kl += sKl[i * Ls + j] * pb[j];
                     }
                 }
                 const T d9b = g.D9b[(size_t)i * n + p];
@@ -243,8 +258,8 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
 #pragma unroll
                     for (int j = 0; j < MAXLS; ++j) {
                         if (j < Ls) {
-                            ab += pb[j] * g.M1[i * Ls + j];
-                            km += g.Kmu[i * Ls + j] * pb[j];
+                            ab += pb[j] * sM1[i * Ls + j];
+                            km += sKm[i * Ls + j] * pb[j];
                         }
                     }
                     const T a1 = g.rho * a[i] + g.D9a[(size_t)i * nl + pl];

@@ -46,9 +46,9 @@ __device__ __forceinline__ void stencil_body(const StencilArgs<T>& a, int bx, in
     const T* __restrict__ inc = a.in + (size_t)c * n;
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
     const int nthr = ST_TX * ST_BY;
-    for (int idx = tid; idx < th * tw; idx += nthr) {
-        const int rr = idx / tw, cc = idx - rr * tw;
-        tile[idx] = inc[(size_t)wrapn(y0 - rh + rr, H) * W + wrapn(x0 - rw + cc, W)];
+    for (int rr = threadIdx.y; rr < th; rr += ST_BY) {
+        const T* row = inc + (size_t)wrapc(y0 - rh + rr, H) * W;
+        for (int cc = threadIdx.x; cc < tw; cc += ST_TX) tile[rr * tw + cc] = row[wrapc(x0 - rw + cc, W)];
     }
     for (int idx = tid; idx < BH * bw; idx += nthr) tp[idx] = a.taps[idx];
     __syncthreads();
