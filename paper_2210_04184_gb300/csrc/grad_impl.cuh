@@ -30,6 +30,11 @@ struct GradWork {
     // box sums; omb_valid: the last reverse pass accumulated omb
     void *omb = nullptr, *Abox = nullptr;
     bool omb_valid = false;
+    // the taped forward loop and the reverse loop captured as CUDA graphs, with the launch
+    // configuration they were captured for and the launches they hold
+    cudaGraphExec_t gfwd = nullptr, gbwd = nullptr;
+    std::vector<long long> key_f, key_b;
+    long long nl_f = 0, nll_f = 0, nl_b = 0, nll_b = 0;
     std::vector<void*> allocs;
 };
 
@@ -37,6 +42,8 @@ namespace {
 
 void grad_free(GradWork* g) {
     if (!g) return;
+    if (g->gfwd) cudaGraphExecDestroy(g->gfwd);
+    if (g->gbwd) cudaGraphExecDestroy(g->gbwd);
     for (void* p : g->allocs)
         if (p) cudaFree(p);
     g->allocs.clear();
@@ -395,6 +402,50 @@ fuse_status run_segment(fuse_ctx* c, int j, bool save) {
     return FUSE_OK;
 }
 
+// Everything a captured loop's launches depend on besides the workspace itself.
+std::vector<long long> launch_key(const fuse_ctx* c, int extra) {
+    const GradWork* g = c->gw;
+    return {g->iters, g->seg, g->nseg, c->lat_impl, c->lat_target, c->lat_stages, c->lat_bpb, c->lt_Ty,
+            c->lt_ncons, (long long)c->lt_smem, c->fr_rpb, c->fc_cw, c->half, c->sfmt, (long long)(uintptr_t)c->mask,
+            (long long)(uintptr_t)c->Sig, c->grad_weights, (long long)c->wait_limit, extra};
+}
+
+// Runs body(stream) on the context stream: directly (profiling, or graphs switched off), else by
+// replaying a CUDA graph captured from it, recaptured when the launch configuration changed.
+template <typename F>
+fuse_status run_captured(fuse_ctx* c, cudaGraphExec_t* exec, std::vector<long long>* key, long long* nl,
+                         long long* nll, const std::vector<long long>& want, F&& body) {
+    if (c->profile || !c->use_graph) {
+        if (*exec) { cudaGraphExecDestroy(*exec); *exec = nullptr; }
+        return body(c->stream);
+    }
+    if (!*exec || *key != want) {
+        if (*exec) { cudaGraphExecDestroy(*exec); *exec = nullptr; }
+        const long long l0 = c->launches_all, ll0 = c->launches_latent;
+        cudaStream_t saved = c->stream;
+        CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        c->stream = c->cap_stream;
+        fuse_status st = body(c->cap_stream);
+        c->stream = saved;
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &gr);
+        *nl = c->launches_all - l0;
+        *nll = c->launches_latent - ll0;
+        c->launches_all = l0;
+        c->launches_latent = ll0;
+        if (st != FUSE_OK) { if (gr) cudaGraphDestroy(gr); return st; }
+        if (e != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture (reverse pass)", e);
+        e = cudaGraphInstantiate(exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) { *exec = nullptr; return fail_cuda(c, "cudaGraphInstantiate (reverse pass)", e); }
+        *key = want;
+    }
+    CK(c, cudaGraphLaunch(*exec, c->stream));
+    c->launches_all += *nl;
+    c->launches_latent += *nll;
+    return FUSE_OK;
+}
+
 fuse_status grad_forward_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, void* Xo) {
     fuse_status st = grad_prepare(c, iters);
     if (st != FUSE_OK) return st;
@@ -402,8 +453,14 @@ fuse_status grad_forward_impl(fuse_ctx* c, const void* Yl, const void* Yh, int i
     st = solve_impl(c, Yl, Yh, 0, 0, nullptr, nullptr);
     if (st != FUSE_OK) return st;
     GradWork* g = c->gw;
-    for (int j = 0; j < g->nseg && iters > 0; ++j) {
-        st = run_segment(c, j, true);
+    if (iters > 0) {
+        st = run_captured(c, &g->gfwd, &g->key_f, &g->nl_f, &g->nll_f, launch_key(c, 0), [&](cudaStream_t) {
+            for (int j = 0; j < g->nseg; ++j) {
+                fuse_status s2 = run_segment(c, j, true);
+                if (s2 != FUSE_OK) return s2;
+            }
+            return FUSE_OK;
+        });
         if (st != FUSE_OK) return st;
     }
     c->have_x = true;
@@ -449,24 +506,27 @@ fuse_status grad_backward_t(fuse_ctx* c, const void* Xbar, const void* Zbar, voi
         CK(c, cudaMemcpyAsync(g->Xb, Xbar, img, cudaMemcpyDeviceToDevice, s));
     }
     const int iters = g->iters;
-    bool recomputed = false;
-    for (int j = g->nseg - 1; j >= 0; --j) {
-        const int s0 = j * g->seg;
-        const int e0 = std::min(iters, s0 + g->seg);
-        if (j != g->nseg - 1) {
-            // refill the tape: restore the segment's entering state and re-run it
-            if (j == 0) st = zero_state(c, s);
-            else st = checkpoint_copy(c, j, false);
-            if (st != FUSE_OK) return st;
-            st = run_segment(c, j, false);
-            if (st != FUSE_OK) return st;
-            recomputed = true;
+    const bool recomputed = g->nseg > 1;
+    st = run_captured(c, &g->gbwd, &g->key_b, &g->nl_b, &g->nll_b, launch_key(c, 1), [&](cudaStream_t ls) {
+        for (int j = g->nseg - 1; j >= 0; --j) {
+            const int s0 = j * g->seg;
+            const int e0 = std::min(iters, s0 + g->seg);
+            fuse_status s2;
+            if (j != g->nseg - 1) {
+                // refill the tape: restore the segment's entering state and re-run it
+                s2 = j == 0 ? zero_state(c, ls) : checkpoint_copy(c, j, false);
+                if (s2 != FUSE_OK) return s2;
+                s2 = run_segment(c, j, false);
+                if (s2 != FUSE_OK) return s2;
+            }
+            for (int t = e0 - 1; t >= s0; --t) {
+                s2 = GradImpl<T>::reverse_step(c, ls, t, t - s0, t == iters - 1);
+                if (s2 != FUSE_OK) return s2;
+            }
         }
-        for (int t = e0 - 1; t >= s0; --t) {
-            st = GradImpl<T>::reverse_step(c, s, t, t - s0, t == iters - 1);
-            if (st != FUSE_OK) return st;
-        }
-    }
+        return FUSE_OK;
+    });
+    if (st != FUSE_OK) return st;
     g->omb_valid = c->grad_weights != 0;
     if (recomputed) {
         // the context's state is now that of an earlier iteration

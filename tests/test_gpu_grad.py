@@ -383,3 +383,24 @@ def test_weight_gradient_needs_the_option():
         f.grad_weights()
     assert e.value.status == FUSE_ESTATE
     fuse_reset_error(f.ctx)
+
+
+@pytest.mark.parametrize("seg", [0, 3])
+def test_graph_replay_equals_direct_launches(seg):
+    # the taped forward and the reverse loop replay captured graphs (recaptured when the launch
+    # configuration changes); direct launches give the same bits, and so does a second replay
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_GRAPH, FUSE_OPT_LATENT_STAGES
+    p = problem()
+    om = weights64(p).astype(np.float32).astype(np.float64)
+    Wt = np.random.default_rng(31).standard_normal((p.L_s, p.H, p.W))
+    outs = []
+    for graph in (1, 0):
+        f, yl, yh = context(p, "f32", "f32", om, opts=((FUSE_OPT_GRAD_SEGMENT, seg), (FUSE_OPT_GRAPH, graph)))
+        outs.append(gpu_grad(f, yl, yh, 7, Wt))
+        outs.append(gpu_grad(f, yl, yh, 7, Wt))          # replay (or direct again)
+        f.set_option(FUSE_OPT_LATENT_STAGES, 4)           # another launch shape: recapture
+        outs.append(gpu_grad(f, yl, yh, 7, Wt))
+    for o in outs[1:]:
+        for a, b in zip(o[:3], outs[0][:3]):
+            assert np.array_equal(a, b)
+        assert o[3] == outs[0][3]
