@@ -277,11 +277,15 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     sh->fr_tpr = t;
     sh->fr_rpb = 256 / t;
     while (sh->fr_rpb > 1 && 2 * (size_t)sh->fr_rpb * g->W * csz > 64 * 1024) sh->fr_rpb--;
+    // small images: fewer rows per block until the pass has about two blocks per SM
+    const int npair_ = (g->L_s + 1) / 2;
+    while (sh->fr_rpb > 1 && (long long)((g->H + sh->fr_rpb - 1) / sh->fr_rpb) * npair_ < 304) sh->fr_rpb /= 2;
     sh->fr_smem = 2 * (size_t)sh->fr_rpb * g->W * csz;
     if (sh->fr_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "W too large for the FFT");
     // fft columns
     sh->fc_cw = dtype == FUSE_F64 ? 4 : 8;
     while (sh->fc_cw > 1 && (size_t)sh->fc_cw * (2 * g->H + 1) * csz > kMaxSmem) sh->fc_cw /= 2;
+    while (sh->fc_cw > 2 && (long long)((g->W + sh->fc_cw - 1) / sh->fc_cw) * npair_ < 304) sh->fc_cw /= 2;
     sh->fc_smem = (size_t)sh->fc_cw * (2 * g->H + 1) * csz;
     if (sh->fc_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "H too large for the FFT");
     int tc = g->H / 4;

@@ -207,6 +207,11 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
     if (p < n) {
         T q0 = T(0), q1 = T(0), q2 = T(0);            // per pixel in T, FP64 across pixels
         T pb[MAXLS], a[MAXLS], wb[MAXLS];
+        // inputs of the P1 half, read before any store so that every load of the pixel is in
+        // flight at once (the stores below may alias them as far as the compiler knows); kept
+        // in registers only for the smaller band counts
+        constexpr bool kHoist = MAXLS <= 20;
+        T pb1[kHoist ? MAXLS : 1], wb1[kHoist ? MAXLS : 1], a1w[kHoist ? MAXLS : 1];
 #pragma unroll
         for (int j = 0; j < MAXLS; ++j) {
             if (j < Ls) {
@@ -214,6 +219,12 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
                 pb[j] = l2b + T(2) * u2b;
                 wb[j] = -(l2b + u2b);
                 a[j] = g.X[(size_t)j * n + p] - g.Lam2[(size_t)j * n + p] + g.D9b[(size_t)j * n + p];
+                if constexpr (kHoist) {
+                    const T l1b = g.L1b[(size_t)j * n + p], u1b = g.U1b[(size_t)j * n + p];
+                    pb1[j] = l1b + T(2) * u1b;
+                    wb1[j] = -(l1b + u1b);
+                    a1w[j] = g.BX[(size_t)j * n + p] - g.Lam1[(size_t)j * n + p];
+                }
             }
         }
 #pragma unroll
@@ -242,10 +253,16 @@ __global__ void __launch_bounds__(128) pixel_bwd_kernel(PixelBwdArgs<T> g) {
 #pragma unroll
         for (int j = 0; j < MAXLS; ++j) {
             if (j < Ls) {
-                const T l1b = g.L1b[(size_t)j * n + p], u1b = g.U1b[(size_t)j * n + p];
-                pb[j] = l1b + T(2) * u1b;
-                wb[j] = -(l1b + u1b);
-                a[j] = g.BX[(size_t)j * n + p] - g.Lam1[(size_t)j * n + p];      // w1
+                if constexpr (kHoist) {
+                    pb[j] = pb1[j];
+                    wb[j] = wb1[j];
+                    a[j] = a1w[j];                                              // w1
+                } else {
+                    const T l1b = g.L1b[(size_t)j * n + p], u1b = g.U1b[(size_t)j * n + p];
+                    pb[j] = l1b + T(2) * u1b;
+                    wb[j] = -(l1b + u1b);
+                    a[j] = g.BX[(size_t)j * n + p] - g.Lam1[(size_t)j * n + p];  // w1
+                }
             }
         }
         if (sampled_pixel(g.mask, p, y, x, d)) {
