@@ -102,6 +102,8 @@ struct fuse_ctx {
     std::vector<double> hM1, hF, hER;
     // spectral condition numbers of A (eq. inv), E E^T + rho I and F^{-1} (fuse_conditioning)
     double cond[3] = {0.0, 0.0, 0.0};
+    // host copies of the blur taps (b for B^T, flipped b for B) for the square-blur stencil
+    std::vector<double> htapsT, htapsB;
     // latent state read / written by the next latent launch (NULL = Sig, in place); set only
     // around directly launched iterations of the taped forward, never while capturing
     void *lat_in = nullptr, *lat_out = nullptr;
@@ -442,6 +444,8 @@ struct Impl {
             constexpr int BH = decltype(bh)::value;
             if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 0, BH>, A, kMaxSmem);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 1, BH>, A, kMaxSmem);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 0, BH>, A, kMaxSmem);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 1, BH>, A, kMaxSmem);
         });
         CK(c, e);
         CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, A, kMaxSmem));
@@ -466,14 +470,30 @@ struct Impl {
         return FUSE_OK;
     }
 
-    // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
+    // Launches a blur stencil: the square-blur kernel (taps in the argument space) when
+    // bh == bw, else the generic one (taps in shared memory).
     template <int MODE>
-    static void stencil(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
+    static void stencil_launch(fuse_ctx* c, cudaStream_t s, const StencilArgs<T>& a) {
         dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-        const StencilArgs<T> a = st_args(c, in, out, taps);
+        if (c->bh == c->bw) {
+            const std::vector<double>& ht = a.taps == (const T*)c->tapsB ? c->htapsB : c->htapsT;
+            with_bh(c->bh, [&](auto bh) {
+                constexpr int B = decltype(bh)::value;
+                SquareTaps<T, B> tp;
+                for (int i = 0; i < B * B; ++i) tp.t[i] = (T)ht[i];
+                stencil_sq_kernel<T, MODE, B><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a, tp);
+            });
+            return;
+        }
         with_bh(c->bh, [&](auto bh) {
             stencil_kernel<T, MODE, decltype(bh)::value><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a);
         });
+    }
+
+    // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
+    template <int MODE>
+    static void stencil(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps) {
+        stencil_launch<MODE>(c, s, st_args(c, in, out, taps));
     }
 
     static void pixel(fuse_ctx* c, cudaStream_t s) {
@@ -1234,6 +1254,8 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
         c->cond[0] = fmax / fmin;
     }
     if (!invert(M1, Ls) || !invert(Fm, Ls)) return bail(FUSE_EINVAL);
+    c->htapsT = tT;
+    c->htapsB = tB;
     c->hM1 = M1;
     c->hF = Fm;
     c->hER = ER;

@@ -234,12 +234,9 @@ struct GradImpl {
     template <int MODE>
     static fuse_status stencil(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* taps,
                                const void* U2, const void* planes) {
-        dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
         const StencilArgs<T> a{(const T*)in, (T*)out, (const T*)taps, c->bw, c->H, c->W,
                                (const T*)U2, (const T*)planes, c->S, c->half};
-        with_bh(c->bh, [&](auto bh) {
-            stencil_kernel<T, MODE, decltype(bh)::value><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a);
-        });
+        Impl<T>::template stencil_launch<MODE>(c, s, a);
         c->launches_all++;
         CKL(c, "stencil_kernel (reverse pass)");
         return FUSE_OK;

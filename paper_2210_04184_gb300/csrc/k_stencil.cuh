@@ -26,6 +26,40 @@ struct StencilArgs {
     int S, half;
 };
 
+// Writes the QY outputs of one thread (rows y_first.., column x of band c); MODE 1 adds U2 and
+// the adjoint sum R of the latent planes.
+template <typename T, int MODE, int QY>
+__device__ __forceinline__ void stencil_store(const StencilArgs<T>& a, const T (&acc)[QY], int x, int y_first, int c) {
+    const int H = a.H, W = a.W, S = a.S, half = a.half;
+    const size_t n = (size_t)H * W;
+    const int side = 2 * S + 1;
+    T rs[QY];
+#pragma unroll
+    for (int q = 0; q < QY; ++q) rs[q] = T(0);
+    if constexpr (MODE == 1) {
+        // per tau1 row, the plane reads of all QY outputs are issued together
+        const T* pc = a.planes + (size_t)c * 2 * side * n;
+        for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
+            const T* pa = pc + (size_t)(t1 + S) * n;
+            const T* pv = pc + (size_t)(side + t1 + S) * n;
+#pragma unroll
+            for (int q = 0; q < QY; ++q) {
+                const int y = y_first + q;
+                if (y < H) rs[q] += pa[(size_t)y * W + x] - pv[(size_t)wrap1(y + t1, H) * W + x];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QY; ++q) {
+        const int y = y_first + q;
+        if (y >= H) break;
+        T val = acc[q];
+        const size_t pix = (size_t)y * W + x;
+        if constexpr (MODE == 1) val += a.U2[(size_t)c * n + pix] + (half ? T(2) * rs[q] : rs[q]);
+        a.out[(size_t)c * n + pix] = val;
+    }
+}
+
 // Each thread computes QY = 4 vertically adjacent outputs; for every tap column v it holds the
 // BH + QY - 1 tile values of its column in registers, so each shared-memory read feeds up to
 // QY multiply-adds.  BH is a compile-time odd size (1..15); bw is a runtime odd size.
@@ -35,7 +69,7 @@ __device__ __forceinline__ void stencil_body(const StencilArgs<T>& a, int bx, in
                                              unsigned char* smem_raw) {
     constexpr int QY = ST_TY / ST_BY;                 // 4 outputs per thread
     constexpr int NR = BH + QY - 1;
-    const int bw = a.bw, H = a.H, W = a.W, S = a.S, half = a.half;
+    const int bw = a.bw, H = a.H, W = a.W;
     const int th = ST_TY + BH - 1, tw = ST_TX + bw - 1;
     T* tile = reinterpret_cast<T*>(smem_raw);         // [th][tw]
     T* tp = tile + (size_t)th * tw;                   // [BH][bw]
@@ -69,24 +103,52 @@ __device__ __forceinline__ void stencil_body(const StencilArgs<T>& a, int bx, in
             for (int q = 0; q < QY; ++q) acc[q] += t * col[q + u];
         }
     }
-    const int side = 2 * S + 1;
-#pragma unroll
-    for (int q = 0; q < QY; ++q) {
-        const int y = y0 + ly0 + q;
-        if (y >= H) break;
-        T val = acc[q];
-        const size_t pix = (size_t)y * W + x;
-        if constexpr (MODE == 1) {
-            const T* pc = a.planes + (size_t)c * 2 * side * n;
-            T rs = T(0);
-            for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
-                rs += pc[(size_t)(t1 + S) * n + pix];
-                rs -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
-            }
-            val += a.U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
-        }
-        a.out[(size_t)c * n + pix] = val;
+    stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
+}
+
+// Square blurs (B x B, the usual case): the tap loops are unrolled at compile time and the taps
+// travel in the kernel's argument space, so every multiply-add reads its tap as a constant
+// operand and the tile reads use fixed offsets.
+template <typename T, int B>
+struct SquareTaps {
+    T t[B * B];
+};
+
+template <typename T, int MODE, int B>
+__global__ void __launch_bounds__(256) stencil_sq_kernel(StencilArgs<T> a, SquareTaps<T, B> taps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int QY = ST_TY / ST_BY;
+    constexpr int NR = B + QY - 1;
+    constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, R = B / 2;
+    const int H = a.H, W = a.W;
+    const int c = blockIdx.z;
+    T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TW]
+    const int x0 = blockIdx.x * ST_TX, y0 = blockIdx.y * ST_TY;
+    const T* __restrict__ inc = a.in + (size_t)c * H * W;
+    for (int rr = threadIdx.y; rr < TH; rr += ST_BY) {
+        const T* row = inc + (size_t)wrapc(y0 - R + rr, H) * W;
+        for (int cc = threadIdx.x; cc < TW; cc += ST_TX) tile[rr * TW + cc] = row[wrapc(x0 - R + cc, W)];
     }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    const int ly0 = threadIdx.y * QY;
+    const T* tcol = tile + ly0 * TW + threadIdx.x;
+    T acc[QY];
+#pragma unroll
+    for (int q = 0; q < QY; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int v = 0; v < B; ++v) {
+        T col[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) col[r] = tcol[r * TW + v];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+#pragma unroll
+            for (int q = 0; q < QY; ++q) acc[q] += taps.t[u * B + v] * col[q + u];
+        }
+    }
+    stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
 }
 
 template <typename T, int MODE, int BH>
