@@ -33,29 +33,21 @@ __device__ __forceinline__ void stencil_store(const StencilArgs<T>& a, const T (
     const int H = a.H, W = a.W, S = a.S, half = a.half;
     const size_t n = (size_t)H * W;
     const int side = 2 * S + 1;
-    T rs[QY];
-#pragma unroll
-    for (int q = 0; q < QY; ++q) rs[q] = T(0);
-    if constexpr (MODE == 1) {
-        // per tau1 row, the plane reads of all QY outputs are issued together
-        const T* pc = a.planes + (size_t)c * 2 * side * n;
-        for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
-            const T* pa = pc + (size_t)(t1 + S) * n;
-            const T* pv = pc + (size_t)(side + t1 + S) * n;
-#pragma unroll
-            for (int q = 0; q < QY; ++q) {
-                const int y = y_first + q;
-                if (y < H) rs[q] += pa[(size_t)y * W + x] - pv[(size_t)wrap1(y + t1, H) * W + x];
-            }
-        }
-    }
 #pragma unroll
     for (int q = 0; q < QY; ++q) {
         const int y = y_first + q;
         if (y >= H) break;
         T val = acc[q];
         const size_t pix = (size_t)y * W + x;
-        if constexpr (MODE == 1) val += a.U2[(size_t)c * n + pix] + (half ? T(2) * rs[q] : rs[q]);
+        if constexpr (MODE == 1) {
+            const T* pc = a.planes + (size_t)c * 2 * side * n;
+            T rs = T(0);
+            for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
+                rs += pc[(size_t)(t1 + S) * n + pix];
+                rs -= pc[(size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x];
+            }
+            val += a.U2[(size_t)c * n + pix] + (half ? T(2) * rs : rs);
+        }
         a.out[(size_t)c * n + pix] = val;
     }
 }
