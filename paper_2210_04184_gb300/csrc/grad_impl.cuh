@@ -26,6 +26,9 @@ struct GradWork {
     void *Krho = nullptr, *Klam = nullptr, *Kmu = nullptr, *MhT = nullptr;
     double *lat_part = nullptr, *px_part = nullptr;
     size_t n_lat_part = 0, n_px_part = 0;
+    // launch shape of the bulk-copy latent reverse pass (tma = 0: the register-staged kernel)
+    int tma = 0, tb_Ty = 1, tb_ncons = 0, tb_D = 4;
+    size_t tb_smem = 0;
     // dL/domega [|W|][H][W] (allocated when FUSE_OPT_GRAD_WEIGHTS is on) and the guide step's
     // box sums; omb_valid: the last reverse pass accumulated omb
     void *omb = nullptr, *Abox = nullptr;
@@ -176,9 +179,25 @@ fuse_status grad_prepare(fuse_ctx* c, int iters) {
         U(&g->Klam, Kl);
         U(&g->Kmu, Km);
         U(&g->MhT, MhT);
+        // launch shape of the bulk-copy latent reverse pass: about 128 consumer threads of 16 bytes
+        // of pixels each over full rows, a ring of 4 slots of two planes (taped state, adjoint)
+        {
+            const int vec = (int)(16 / c->esz), tpr = c->W / vec;
+            int Ty = 128 / tpr;
+            Ty = Ty < 1 ? 1 : (Ty > c->H ? c->H : Ty);
+            while (Ty > 1 && ((tpr * Ty + 31) / 32) * 32 + 32 > 288) --Ty;
+            const int ncons = ((tpr * Ty + 31) / 32) * 32;
+            const size_t smem = (size_t)g->tb_D * 2 * Ty * c->W * c->esz + (size_t)(2 * c->S + 1) * Ty * c->W * c->esz +
+                                2 * (size_t)g->tb_D * 8;
+            g->tma = (c->lat_impl == 1 && ncons + 32 <= 288 && smem <= (size_t)kMaxSmem) ? 1 : 0;
+            g->tb_Ty = Ty;
+            g->tb_ncons = ncons;
+            g->tb_smem = smem;
+        }
         // partial sums: one slot per block of the latent and pixel reverse kernels
         const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
-        g->n_lat_part = (size_t)((c->H + c->lat_Ty - 1) / c->lat_Ty) * c->Ls * rowsW;
+        const int lty = g->tma ? g->tb_Ty : c->lat_Ty;
+        g->n_lat_part = (size_t)((c->H + lty - 1) / lty) * c->Ls * rowsW;
         g->n_px_part = 3 * ((c->n + 127) / 128);
         A((void**)&g->lat_part, g->n_lat_part * sizeof(double));
         A((void**)&g->px_part, g->n_px_part * sizeof(double));
@@ -205,9 +224,13 @@ struct GradImpl {
             constexpr int K = decltype(k)::value;
             if constexpr (sizeof(T) == 8) {
                 e = cudaFuncSetAttribute(latent_bwd_kernel<T, double, K, VEC>, A, kMaxSmem);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, double, K, VEC>, A, kMaxSmem);
             } else {
                 e = cudaFuncSetAttribute(latent_bwd_kernel<T, float, K, VEC>, A, kMaxSmem);
                 if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_kernel<T, __nv_bfloat16, K, VEC>, A, kMaxSmem);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, float, K, VEC>, A, kMaxSmem);
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, __nv_bfloat16, K, VEC>, A, kMaxSmem);
             }
         });
         CK(c, e);
@@ -246,6 +269,17 @@ struct GradImpl {
     static void latent_bwd(fuse_ctx* c, cudaStream_t s, const void* Xt, const void* Sin) {
         GradWork* g = c->gw;
         const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
+        if (g->tma) {
+            dim3 grid((unsigned)((c->H + g->tb_Ty - 1) / g->tb_Ty), (unsigned)c->Ls, rowsW);
+            const LatentBwdArgs<T, WT> a{(const T*)Xt, (const WT*)c->omega, (const T*)Sin, (T*)g->Sb, (const T*)g->Cb,
+                                         (T*)g->planesB, g->lat_part, c->H, c->W, c->Ls, c->S, g->tb_Ty,
+                                         g->tb_ncons, g->tb_D, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit,
+                                         c->half};
+            with_k(c->K, [&](auto k) {
+                latent_bwd_tma_kernel<T, WT, decltype(k)::value, VEC><<<grid, g->tb_ncons + 32, g->tb_smem, s>>>(a);
+            });
+            return;
+        }
         dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
         with_k(c->K, [&](auto k) {
             latent_bwd_kernel<T, WT, decltype(k)::value, VEC><<<grid, (c->lat_threads + 31) / 32 * 32, c->lat_smem, s>>>(

@@ -27,6 +27,7 @@
 // of vbar and the threshold partial sums are counted twice, like the forward adjoint sum.
 #pragma once
 #include "common.cuh"
+#include "k_latent.cuh"
 #include "k_objective.cuh"
 
 namespace fuse {
@@ -149,6 +150,199 @@ latent_bwd_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T
     }
     vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + (size_t)y * W + x0, A);
     vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + (size_t)y * W + x0, V);
+}
+
+// Pipelined form of latent_bwd_kernel (same arithmetic, same outputs): the taped state Sin and the
+// state adjoint Sb stream through a shared-memory ring of D slots by bulk asynchronous copies
+// issued by one producer warp; a slot holds the block's rows of one (tau, k) plane of both.  The
+// consumers rewrite Sb in place with streaming stores.  The threshold partials are reduced among
+// the consumer warps through shared memory in a fixed order (deterministic) and added to
+// part[block].  Every barrier wait is bounded (`limit` polls); a timeout sets bit 1 of *err and
+// the block still finishes in bounded time.
+template <typename T, typename WT>
+struct LatentBwdArgs {
+    const T* X;
+    const WT* omega;
+    const T* Sin;
+    T* Sb;
+    const T* Rb;
+    T* planes;
+    double* part;
+    int H, W, Ls, S, Ty, ncons, D;
+    T coef;
+    int* err;
+    unsigned limit;
+    int half;
+};
+
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(288, 2) latent_bwd_tma_kernel(LatentBwdArgs<T, WT> a) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    constexpr int PS = 2 * K + 1;
+    constexpr int NP = PS * PS;
+    const int H = a.H, W = a.W, Ls = a.Ls, S = a.S, Ty = a.Ty, ncons = a.ncons, D = a.D;
+    const int side = 2 * S + 1;
+    const int tile = Ty * W;
+    T* ring = reinterpret_cast<T*>(smem_tma);                 // [D][2][Ty][W]: Sin, Sb
+    T* Hs = ring + (size_t)D * 2 * tile;                      // [(2S+1)][Ty][W]
+    uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)side * tile);
+    uint64_t* empty = full + D;
+    __shared__ volatile int s_abort;
+    __shared__ double red[9];
+
+    const int tid = threadIdx.x;
+    const int tpr = W / VEC;
+    const int y0 = blockIdx.x * Ty;
+    const int rows = min(Ty, H - y0);
+    const TauMap tm{a.S, a.half};
+    const int t1 = tm.t1_of_block(blockIdx.z);
+    const int nt2 = tm.nt2(t1);
+    const int c = blockIdx.y;
+    const size_t n = (size_t)H * W;
+    const int nq = nt2 * NP;
+    const unsigned bytes = (unsigned)(rows * W * (int)sizeof(T));
+
+    if (tid == 0) {
+        for (int q = 0; q < D; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], (unsigned)(ncons / 32));
+        }
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    if (tid >= ncons) {
+        // ---------------- producer warp ----------------
+        if (tid == ncons) {
+            const uint64_t pol = l2_evict_first_policy();
+            int issued = 0;
+            for (int q = 0; q < nq; ++q) {
+                if (s_abort) break;
+                const int slot = q % D;
+                if (q >= D && !mbar_wait(&empty[slot], (unsigned)((q / D - 1) & 1), a.limit, a.err, 1)) {
+                    s_abort = 1;
+                    break;
+                }
+                const int j = q / NP, kidx = q - j * NP;
+                const int t2 = tm.t2_of(t1, j);
+                const size_t off = ((size_t)(tm.s_index(t1, t2) * NP + kidx) * Ls + c) * n + (size_t)y0 * W;
+                mbar_arrive_expect_tx(&full[slot], 2 * bytes);
+                tma_load_1d(ring + (size_t)slot * 2 * tile, a.Sin + off, bytes, &full[slot], pol);
+                tma_load_1d(ring + (size_t)slot * 2 * tile + tile, a.Sb + off, bytes, &full[slot], pol);
+                issued = q + 1;
+            }
+            const unsigned dlim = a.limit > (1u << 20) ? a.limit : (1u << 20);
+            for (int q = issued > D ? issued - D : 0; q < issued; ++q)
+                if (!mbar_wait(&full[q % D], (unsigned)((q / D) & 1), dlim, a.err, 1)) break;
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int lane = tid & 31;
+    const int r = tid / tpr;
+    const int x0 = (tid - r * tpr) * VEC;
+    const int y = y0 + r;
+    const bool owner = tid < tpr * Ty;
+    const bool active = owner && r < rows;
+    const T* Xc = a.X + (size_t)c * n;
+    const T* Rc = a.Rb + (size_t)c * n;
+    const size_t pix = (size_t)y * W + x0;
+    const size_t xsrow = (size_t)wrap1(y - t1, H) * W;
+    const size_t kstride = (size_t)Ls * n;
+    T Xm[VEC], Rm[VEC];
+    if (active) {
+        vload<T, VEC>(Xc + pix, Xm);
+        vload<T, VEC>(Rc + pix, Rm);
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) { Xm[j] = T(0); Rm[j] = T(0); }
+    }
+    int slot = 0;
+    unsigned par = 0;
+    double smu = 0.0;
+    for (int jt = 0; jt < nt2; ++jt) {
+        const int t2 = tm.t2_of(t1, jt);
+        T Hacc[VEC], delta[VEC], gb[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            Hacc[j] = T(0);
+            const size_t q = xsrow + wrap1(x0 + j - t2, W);
+            delta[j] = active ? Xm[j] - Xc[q] : T(0);           // D X at the re-indexed pixel
+            gb[j] = active ? Rm[j] - Rc[q] : T(0);              // Gbar = D Rbar
+        }
+        const WT* om = a.omega + (size_t)tm.w_index(t1, t2) * n;
+        T* gp = a.Sb + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
+        T smu_t = T(0);
+#pragma unroll
+        for (int k1 = 0; k1 < PS; ++k1) {
+            const WT* orow = om + (size_t)wrap1(y + k1 - K, H) * W;
+            T w[VEC + 2 * K];
+#pragma unroll
+            for (int j = 0; j < VEC + 2 * K; ++j) w[j] = active ? (T)wload(orow + wrap1(x0 - K + j, W)) : T(0);
+#pragma unroll
+            for (int k2 = 0; k2 < PS; ++k2) {
+                const unsigned lim = s_abort ? 64u : a.limit;
+                if (!mbar_wait(&full[slot], par, lim, a.err, 1)) s_abort = 1;
+                if (active) {
+                    T sin[VEC], sbv[VEC];
+                    const T* rs = ring + (size_t)slot * 2 * tile + (size_t)r * W + x0;
+                    vload<T, VEC>(rs, sin);
+                    vload<T, VEC>(rs + tile, sbv);
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        const T v = delta[j] - sin[j];
+                        const T wt = w[j + k2];
+                        const bool inside = (v < T(0) ? -v : v) < a.coef * wt;
+                        const T vb = inside ? -(gb[j] + sbv[j]) : gb[j];
+                        if (!inside && v != T(0)) {
+                            const T mb = -(sbv[j] + T(2) * gb[j]);
+                            smu_t += v > T(0) ? mb * wt : -mb * wt;
+                        }
+                        Hacc[j] += vb;
+                        sbv[j] = -vb;
+                    }
+                    vstore_stream<T, VEC>(gp, sbv);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                gp += kstride;
+                if (++slot == D) { slot = 0; par ^= 1u; }
+            }
+        }
+        smu += (double)smu_t;
+        if (owner) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
+        }
+    }
+    // threshold partials: consumer warps only, fixed order
+    const double ws = warp_sum(smu);
+    if (lane == 0) red[tid >> 5] = ws;
+    consumer_barrier(ncons);                 // every H_tau is in Hs and every warp sum in red
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int q = 0; q < ncons / 32; ++q) sum += red[q];
+        double* pp = a.part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        *pp += a.half ? 2.0 * sum : sum;
+    }
+    if (active) {
+        T A[VEC], V[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) { A[j] = T(0); V[j] = T(0); }
+        for (int jt = 0; jt < nt2; ++jt) {
+            const int t2 = tm.t2_of(t1, jt);
+            const T* hrow = Hs + ((size_t)(t2 + S) * Ty + r) * W;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                A[j] += hrow[x0 + j];
+                V[j] += hrow[wrap1(x0 + j + t2, W)];
+            }
+        }
+        vstore<T, VEC>(a.planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
+        vstore<T, VEC>(a.planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
+    }
 }
 
 // Pixel reverse pass of one iteration.
