@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-vs-FP32 comparison")
     ap.add_argument("--no-grad", action="store_true", help="skip the reverse-pass measurement")
     ap.add_argument("--grad-only", action="store_true", help="only the reverse-pass measurement")
+    ap.add_argument("--grad-workload", default="unrolled_256", help="workload of the reverse-pass measurement")
     ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-point state measurement")
     ap.add_argument("--fixed-state", action="store_true",
                     help="run the main measurement with the 16-bit fixed-point latent state")
@@ -477,7 +478,8 @@ def grad_bench(a, rank):
     from oracle import grad as ograd, nlpr
     from paper_2210_04184_gb300 import synth
     from paper_2210_04184_gb300.fuse import Fusion, fuse_grad_bytes
-    p, meta = _workload("unrolled_256", rank, None)
+    name = getattr(a, "grad_workload", "unrolled_256")
+    p, meta = _workload(name, rank, a.iters if name != "unrolled_256" else None)
     td = torch.float32
     f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
     yl = torch.tensor(p.Yl, dtype=td, device="cuda")
@@ -506,14 +508,14 @@ def grad_bench(a, rank):
         fwd.append(e0.elapsed_time(e1)); bwd.append(e1.elapsed_time(e2)); plain.append(e3.elapsed_time(e4))
     fm, bm, pm = statistics.median(fwd), statistics.median(bwd), statistics.median(plain)
     units = p.H * p.W / 1e6 * p.L_s * p.iters
-    out = {"workload": "unrolled_256", "H": p.H, "W": p.W, "bands": p.L_l, "L_s": p.L_s,
+    out = {"workload": name, "H": p.H, "W": p.W, "bands": p.L_l, "L_s": p.L_s,
            "patch": f"{2 * p.K + 1}x{2 * p.K + 1}", "search": f"{2 * p.S + 1}x{2 * p.S + 1}",
            "iters": p.iters, "dtype": "f32", "weights": meta["wdtype"],
            "ms_forward_with_tape": fm, "ms_backward": bm, "ms_plain_forward": pm,
            "value_forward_backward": units / ((fm + bm) / 1e3), "unit": UNIT,
            "backward_over_plain_forward": bm / pm, "workspace_bytes": fuse_grad_bytes(f.ctx, p.iters)}
     f.close()
-    if rank == 0 and not a.no_cpu_baseline:
+    if rank == 0 and not a.no_cpu_baseline and name == "unrolled_256":
         # the oracle as it stands, the workload's 20 iterations on a square crop: 64 x 64, or
         # 128 x 128 when the 64 x 64 run took under 3 s (a sample of several seconds)
         spec = dict(synth.WORKLOADS["unrolled_256"])
