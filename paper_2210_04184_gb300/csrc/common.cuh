@@ -123,6 +123,18 @@ struct FixedCode {
     static __device__ __forceinline__ uint32_t pack(uint32_t lo, uint32_t hi) {
         return __byte_perm(lo, hi, 0x5410u) ^ 0x80008000u;
     }
+    // both codes of a word, as decode(w, 0) and decode(w, 1)
+    static __device__ __forceinline__ float2 decode2(uint32_t w) {
+        const uint32_t o = w ^ 0x80008000u;
+        const float2 b = make_float2(__uint_as_float(__byte_perm(o, 0x4B000000u, 0x7610u)),
+                                     __uint_as_float(__byte_perm(o, 0x4B000000u, 0x7632u)));
+        return __fadd2_rn(b, make_float2(-kBias, -kBias));
+    }
+    // the rounded codes of two values in [-32767, 32767], packed as pack(round_bits(.), round_bits(.))
+    static __device__ __forceinline__ uint32_t pack2(float2 c) {
+        const float2 r = __fadd2_rn(c, make_float2(kBias, kBias));
+        return pack(__float_as_uint(r.x), __float_as_uint(r.y));
+    }
 };
 
 // The pixels kept by the sampling operator S: the lattice i1 = i2 = 0 (mod d), or, when a mask

@@ -328,18 +328,22 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                             uint32_t out[4];
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
-                                uint32_t t[2];
-#pragma unroll
-                                for (int e = 0; e < 2; ++e) {
-                                    const int j = 2 * h + e;
-                                    const float m = mu[j + k2];
-                                    const float q = FixedCode::decode(wd[h], e);
-                                    const float uc = fmaf(-delta[j], __fdividef(FixedCode::kLevels, m), q);  // Sigma - D X
-                                    const float s2c = fminf(fmaxf(uc, -FixedCode::kLevels), FixedCode::kLevels);
-                                    Hacc[j] = fmaf(fmaf(2.0f, s2c, -uc), m * FixedCode::kStep, Hacc[j]);
-                                    t[e] = FixedCode::round_bits(s2c);
-                                }
-                                out[h] = FixedCode::pack(t[0], t[1]);
+                                // the two codes of a word are updated together with the paired
+                                // FP32 instructions (same rounding as the scalar ones)
+                                const int j0 = 2 * h, j1 = 2 * h + 1;
+                                const float2 m = make_float2(mu[j0 + k2], mu[j1 + k2]);
+                                const float2 q = FixedCode::decode2(wd[h]);
+                                const float2 inv = make_float2(__fdividef(FixedCode::kLevels, m.x),
+                                                               __fdividef(FixedCode::kLevels, m.y));
+                                const float2 uc = __ffma2_rn(make_float2(-delta[j0], -delta[j1]), inv, q);  // Sigma - D X
+                                const float2 s2c = make_float2(fminf(fmaxf(uc.x, -FixedCode::kLevels), FixedCode::kLevels),
+                                                               fminf(fmaxf(uc.y, -FixedCode::kLevels), FixedCode::kLevels));
+                                const float2 g2 = __ffma2_rn(make_float2(2.0f, 2.0f), s2c, make_float2(-uc.x, -uc.y));
+                                const float2 sc = __fmul2_rn(m, make_float2(FixedCode::kStep, FixedCode::kStep));
+                                const float2 hacc = __ffma2_rn(g2, sc, make_float2(Hacc[j0], Hacc[j1]));
+                                Hacc[j0] = hacc.x;
+                                Hacc[j1] = hacc.y;
+                                out[h] = FixedCode::pack2(s2c);
                             }
                             __stcs(reinterpret_cast<int4*>(gp), make_int4((int)out[0], (int)out[1], (int)out[2], (int)out[3]));
                         }

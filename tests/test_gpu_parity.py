@@ -151,6 +151,8 @@ CASES = {
     "60x20_K0S1": dict(H=60, W=20, L_l=5, L_h=2, L_s=2, K=0, S=1, iters=25),
     # lambda2 = 0 (the latent pass still runs: Sigma stays 0, G = D X)
     "32x32_lam0": dict(H=32, W=32, L_l=4, L_h=2, L_s=2, K=1, S=1, lam2=0.0, iters=20),
+    # the largest patch (7x7, K = 3)
+    "36x40_K3S1": dict(H=36, W=40, L_l=4, L_h=2, L_s=2, K=3, S=1, iters=15),
 }
 
 
@@ -321,3 +323,26 @@ def test_autotune_and_fft_shapes_keep_results():
     X, _ = f.solve(yl, yh, 8)
     f.sync()
     assert np.array_equal(X.double().cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_more_than_32_subspace_bands(dtype):
+    # E = I with 40 bands: the pixel updates take the shared-memory path for L_s > 32
+    p = synth.make_problem(H=24, W=32, L_l=40, L_h=3, L_s=40, d=4, blur_size=5, blur_sigma=1.0, K=1, S=2,
+                           lam1=1.0, lam2=1e-2, rho=5e-2, h=0.3, seed=9, E_identity=True)
+    assert p.L_s == 40
+    g = gpu_solve(p, 15, dtype=dtype, wdtype=dtype)
+    Xo, _, _ = oracle_solve(p, 15)
+    assert rel(g["X"], Xo) <= (1e-5 if dtype == "f32" else 1e-11)
+    assert rel(g["Z"], np.einsum("chw,cl->lhw", Xo, p.E)) <= (1e-5 if dtype == "f32" else 1e-11)
+
+
+def test_identity_subspace_at_93_bands():
+    # the HS+MS bands with E = I (L_s = 93, the secondary form of that workload) on a 64 x 64 crop
+    p = synth.make_problem(H=64, W=64, L_l=93, L_h=4, L_s=93, d=4, blur_size=9, blur_sigma=1.7, K=2, S=3,
+                           snr_l=35.0, snr_h=35.0, kind="hsms", seed=10, E_identity=True)
+    om = nlpr.round_bf16(nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h))
+    g = gpu_solve(p, 4, dtype="f32", wdtype="bf16", omega=om)
+    Xo, _, _ = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S, p.lam1, p.lam2,
+                         p.rho, om, 4, fast=True, inplace=True)
+    assert rel(g["X"], nlpr.to_lhw(Xo)) <= 1e-5
