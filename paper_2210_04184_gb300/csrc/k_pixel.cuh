@@ -51,13 +51,15 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
     const size_t n = (size_t)H * W;
     const size_t p = (size_t)bx * nb + tid;
     if (p >= n) return;
-    T a[MAXLS], w[MAXLS];
-    // P2 and Lambda2: a = X - Lambda2 + lambda1/rho Y_h R^T E^T, w = X - Lambda2
+    T a[MAXLS], w[MAXLS], w1[MAXLS];
+    // P2 and Lambda2: a = X - Lambda2 + lambda1/rho Y_h R^T E^T, w = X - Lambda2; the P1 side's
+    // w1 = B X - Lambda1 is read here too, before any store, so all loads of the pixel are in flight
 #pragma unroll
     for (int j = 0; j < MAXLS; ++j) {
         if (j < Ls) {
             w[j] = X[(size_t)j * n + p] - Lam2[(size_t)j * n + p];
             a[j] = w[j] + D9b[(size_t)j * n + p];
+            w1[j] = BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p];
         }
     }
 #pragma unroll
@@ -75,7 +77,7 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
     // P1 and Lambda1: w = B X - Lambda1
 #pragma unroll
     for (int j = 0; j < MAXLS; ++j)
-        if (j < Ls) w[j] = BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p];
+        if (j < Ls) w[j] = w1[j];
     const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
     if (sampled_pixel(args.mask, p, y, x, d)) {
         const size_t nl = (size_t)(H / d) * (W / d);
