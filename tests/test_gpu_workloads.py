@@ -205,3 +205,23 @@ def test_hspan_full_size_fp32_vs_fp64_and_invariant():
     torch.cuda.empty_cache()
     X64, Z64, _ = _gpu(p, p.iters, "f64", "f64")
     assert rel(Z32, Z64) <= 1e-4
+
+
+def test_hspan_full_size_fixed_point_state():
+    # the 16-bit fixed-point state on the largest workload (512 x 512, 120 offsets, 200
+    # iterations): Z within the equal-error bound of the FP64 GPU form
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_STATE_FORMAT
+    p, meta = synth.workload("hspan_512")
+    f = Fusion.from_problem(p, dtype="f32", wdtype="bf16")
+    f.set_option(FUSE_OPT_STATE_FORMAT, 1)
+    yl = torch.tensor(p.Yl, dtype=torch.float32, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=torch.float32, device="cuda")
+    f.weights(yh)
+    _, Z = f.solve(yl, yh, p.iters, want_X=False, want_Z=True)
+    f.sync()
+    Zq = Z.double().cpu().numpy()
+    f.close()
+    del Z
+    torch.cuda.empty_cache()
+    _, Z64, _ = _gpu(p, p.iters, "f64", "f64")
+    assert rel(Zq, Z64) <= 1e-4
