@@ -191,3 +191,17 @@ def test_mask_needs_ratio_one_and_can_be_cleared():
     g.sync()
     assert np.array_equal(X1.double().cpu().numpy(), X0)
     assert not np.array_equal(Xm.double().cpu().numpy(), X0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_denoising_variant(dtype):
+    # S = B = I (ratio 1, 1x1 blur): guided denoising of every band with the same kernels
+    p = synth.make_problem(H=40, W=48, L_l=6, L_h=2, L_s=3, d=1, blur_size=1, blur_sigma=1.0, K=1, S=2,
+                           lam1=1.0, lam2=2e-2, rho=5e-2, h=0.3, seed=61)
+    om = nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h)
+    if dtype == "f32":
+        om = om.astype(np.float32).astype(np.float64)
+    X, Z, _, _, _ = run(p, 25, om, dtype)
+    Xo = oracle(p, 25, om)
+    tol = 1e-5 if dtype == "f32" else 1e-11
+    assert rel(X, Xo) <= tol and rel(Z, np.einsum("chw,cl->lhw", Xo, p.E)) <= tol
