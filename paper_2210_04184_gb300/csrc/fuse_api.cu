@@ -287,7 +287,9 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     // fft columns
     sh->fc_cw = dtype == FUSE_F64 ? 4 : 8;
     while (sh->fc_cw > 1 && (size_t)sh->fc_cw * (2 * g->H + 1) * csz > kMaxSmem) sh->fc_cw /= 2;
-    while (sh->fc_cw > 2 && (long long)((g->W + sh->fc_cw - 1) / sh->fc_cw) * npair_ < 304) sh->fc_cw /= 2;
+    // narrower blocks until the pass has about four blocks per SM (one wave at four resident
+    // blocks: a column block holds 256 threads and tens of KB of shared memory)
+    while (sh->fc_cw > 2 && (long long)((g->W + sh->fc_cw - 1) / sh->fc_cw) * npair_ < 4 * 152) sh->fc_cw /= 2;
     sh->fc_smem = (size_t)sh->fc_cw * (2 * g->H + 1) * csz;
     if (sh->fc_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "H too large for the FFT");
     int tc = g->H / 4;
