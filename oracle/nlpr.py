@@ -12,7 +12,10 @@ What it computes, in the paper's order and notation:
   * the ADMM of Sec. IV for the splitting of eq. fusionoptim: X update
     (eqs. x_linear_system_main and inv), P1 update (eq. Qh_update), P2 update
     (eq. Qm_update), Q update (eq. Qj_main) and the dual updates
-    (eqs. dualvar1_main, dualvar2_main, dualvar3_main).  Q and Sigma are both stored.
+    (eqs. dualvar1_main, dualvar2_main, dualvar3_main).  Q and Sigma are both stored;
+  * a variant that is not the paper's: the same objective with only P2 = X and Q = D X split,
+    so the X system keeps S B and is solved as one dense d^2 x d^2 system per alias class of
+    the DFT grid (FUSE-type direct solve of the S B term); admm(..., x_update="sb").
 
 Readings where the paper is silent or inconsistent:
   * threshold mu = lambda2 * omega / rho (eq. Qj_main) and the objective
@@ -268,6 +271,67 @@ def solve_x_dense(C: np.ndarray, kern: np.ndarray, K: int, S: int) -> np.ndarray
 
 
 # --------------------------------------------------------------------------------------
+# Alternative X update with S B kept in the X system (FUSE-type per-frequency systems)
+# --------------------------------------------------------------------------------------
+#
+# Not the paper's splitting: there P1 = B X moves S into the per-pixel P1 update and the X
+# system is diagonal in the DFT basis (eq. inv).  Here only P2 = X and Q = D X are split, so the
+# X subproblem keeps the data term 1/2 ||Y_l - S B X E||^2 and its normal equations are
+#   B^T S^T S B X (E E^T) + rho (I + sum D^T D) X = B^T S^T Y_l E^T + rho (P2 + Lambda2
+#                                                    + sum D^T (Q + Sigma)).
+# With E E^T = V diag(e) V^T, band c' of X V solves
+#   (I + sum D^T D + (e_c'/rho) B^T S^T S B) x = (rhs V)_c' / rho.
+# S^T S keeps the lattice i1 = i2 = 0 (mod d), whose DFT couples frequency (u, v) with its d^2
+# aliases (u + a H/d, v + b W/d):  (S^T S y)^(w) = d^-2 sum_{w' ~ w} y^(w').  Each alias class
+# is therefore one d^2 x d^2 system  diag(g) + (gamma / d^2) conj(b^) b^T  with
+# g = 1 + |P| sum_tau |d^_{tau 0}|^2 (the same filter sum as eq. inv) and gamma = e_c'/rho.
+
+
+def sb_spectra(H: int, W: int, kern: np.ndarray, K: int, S: int):
+    """b^(w) (complex) and g(w) = 1 + |P| sum_tau |d^_{tau 0}(w)|^2 on the H x W DFT grid."""
+    bhat = np.fft.fft2(filter_image(blur_taps(kern), H, W))
+    g = x_denominator(H, W, np.zeros((1, 1)), K, S)      # a zero blur leaves 1 + |P| sum |d^|^2
+    return bhat, g
+
+
+def solve_x_sb_band(c: np.ndarray, bhat: np.ndarray, g: np.ndarray, d: int, gamma: float) -> np.ndarray:
+    """x with (I + sum D^T D + gamma B^T S^T S B) x = c for one (H, W) band: one dense
+    d^2 x d^2 solve per alias class of the DFT grid."""
+    H, W = c.shape
+    h, w = H // d, W // d
+    # class (u0, v0) holds the frequencies (u0 + a h, v0 + b w), a, b in [0, d): index arrays
+    # of shape (h w, d^2), one row per class
+    a = np.arange(d)
+    U = (np.arange(h)[:, None, None, None] + h * a[None, None, :, None]) + np.zeros((1, w, 1, d), int)
+    V = (np.arange(w)[None, :, None, None] + w * a[None, None, None, :]) + np.zeros((h, 1, d, 1), int)
+    U, V = U.reshape(h * w, d * d), V.reshape(h * w, d * d)
+    ch = np.fft.fft2(c)
+    bv = bhat[U, V]
+    A = np.zeros((h * w, d * d, d * d), dtype=complex)
+    A[:, np.arange(d * d), np.arange(d * d)] = g[U, V]
+    A += (gamma / d ** 2) * np.conj(bv)[:, :, None] * bv[:, None, :]
+    xh = np.empty_like(ch)
+    xh[U, V] = np.linalg.solve(A, ch[U, V][:, :, None])[:, :, 0]
+    return np.fft.ifft2(xh).real
+
+
+def solve_x_sb(C: np.ndarray, su) -> np.ndarray:
+    """X update of the S B-in-X variant: C is the right-hand side divided by rho, (H, W, L_s)."""
+    e, V = np.linalg.eigh(su.E @ su.E.T)
+    Crot = img(mat(C) @ V, su.H, su.W)
+    bhat, g = sb_spectra(su.H, su.W, su.kern, su.K, su.S)
+    Xrot = np.stack([solve_x_sb_band(Crot[:, :, j], bhat, g, su.d, e[j] / su.rho) for j in range(su.L_s)],
+                    axis=-1)
+    return img(mat(Xrot) @ V.T, su.H, su.W)
+
+
+def rhs_sb(st, su, dtsum_fn=None) -> np.ndarray:
+    """B^T S^T Y_l E^T / rho + P2 + Lambda2 + sum D^T (Q + Sigma)."""
+    dts = (dtsum_fn or dt_sum)(st.Q, st.Sig, su.K, su.S)
+    return blur_t(su.SYlEt, su.kern) / su.rho + st.P2 + st.Lam2 + dts
+
+
+# --------------------------------------------------------------------------------------
 # proximal step (eq. Qj_main)
 # --------------------------------------------------------------------------------------
 
@@ -402,6 +466,20 @@ def update_sigma(X, Q, st: State, su: Setup) -> np.ndarray:
     return Sig
 
 
+def admm_step_sb(st: State, su: Setup, latent_fn=None, dtsum_fn=None) -> State:
+    """One iteration of the S B-in-X variant: X (solve_x_sb), P2, Q, Sigma, Lambda2; P1 and
+    Lambda1 are not variables of this splitting and stay zero."""
+    X = solve_x_sb(rhs_sb(st, su, dtsum_fn), su)
+    P2 = update_p2(X, st, su)
+    if latent_fn is not None:
+        Q, Sig = latent_fn(X, st, su)
+    else:
+        Q = update_q(X, st, su)
+        Sig = update_sigma(X, Q, st, su)
+    Lam2 = st.Lam2 - (X - P2)           # eq. dualvar2_main
+    return State(st.P1, P2, st.Lam1, Lam2, Q, Sig, X, st.t + 1)
+
+
 def admm_step(st: State, su: Setup, x_solver=None, latent_fn=None, dtsum_fn=None) -> State:
     """One ADMM iteration t -> t+1 in the order X, P1, P2, Q, duals (Sec. IV)."""
     C = rhs(st, su, dtsum_fn)
@@ -435,7 +513,8 @@ def quantize_state(Sig: np.ndarray, omega: np.ndarray, lam2: float, rho: float, 
 
 
 def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
-         x_solver=None, fast=False, callback=None, inplace=False, state_levels=None, mask=None):
+         x_solver=None, fast=False, callback=None, inplace=False, state_levels=None, mask=None,
+         x_update="paper"):
     """Run `iters` ADMM iterations from `state` (zero initialisation by default).
 
     Images in (H, W, L) layout.  fast=True uses the C loops of oracle/loops.c for the
@@ -445,7 +524,13 @@ def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
     state_levels: Sigma enters the Q and Sigma updates as stored in fixed point
     (quantize_state); the right-hand side still sums the exact Q + Sigma of the last update.
     mask: general sampling operator (see setup).
+    x_update: "paper" (the splitting of eq. fusionoptim) or "sb" (S B kept in the X system,
+    admm_step_sb; lattice sampling only).
     Returns (X, state, setup)."""
+    if x_update not in ("paper", "sb"):
+        raise ValueError("x_update is 'paper' or 'sb'")
+    if x_update == "sb" and mask is not None:
+        raise ValueError("the S B-in-X update needs the regular lattice")
     su = setup(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, mask)
     if state is not None:
         st = state if inplace else state.copy()
@@ -466,7 +551,10 @@ def admm(Yl, Yh, kern, d, R, E, K, S, lam1, lam2, rho, omega, iters, state=None,
             Q = update_q(X, sq, u)
             return Q, update_sigma(X, Q, sq, u)
     for _ in range(iters):
-        st = admm_step(st, su, x_solver, latent_fn, dtsum_fn)
+        if x_update == "sb":
+            st = admm_step_sb(st, su, latent_fn, dtsum_fn)
+        else:
+            st = admm_step(st, su, x_solver, latent_fn, dtsum_fn)
         if callback is not None:
             callback(st, su)
     X = st.X if st.X is not None else np.zeros((su.H, su.W, su.L_s))
