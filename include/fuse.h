@@ -88,7 +88,7 @@ enum {
     FUSE_OPT_GRAD_WEIGHTS = 12,  /* 1: fuse_grad_backward also accumulates dL/domega for
                                     fuse_grad_weights (one more read of the state per reverse
                                     iteration); default 0 */
-    FUSE_OPT_STATE_FORMAT = 13   /* storage of the latent state: 0 (default) the iterate type;
+    FUSE_OPT_STATE_FORMAT = 13,  /* storage of the latent state: 0 (default) the iterate type;
                                     1 = 16-bit fixed point relative to each entry's threshold
                                     (|Sigma'| <= mu always, so q = rint(32767 Sigma'/mu) stands
                                     for q mu / 32767; absolute error <= mu/65534 per entry, half
@@ -96,6 +96,20 @@ enum {
                                     pass (W % 8 == 0) only; not with the reverse pass.  Switching
                                     reallocates the state and clears it.  A batch takes the
                                     format of its contexts (all the same). */
+    FUSE_OPT_X_UPDATE = 14       /* X update: 0 (default) the paper's splitting (P1 = B X, the X
+                                    system diagonal in the DFT basis, eq. inv); 1 = a variant that
+                                    is not the paper's: only P2 = X and Q = D X are split, so the X
+                                    system keeps the data term,
+                                      (I + sum D^T D + eps/rho B^T S^T S B) X
+                                        = B^T S^T Y_l E^T / rho + P2 + Lambda2 + sum D^T (Q + Sigma),
+                                    solved per alias class of d^2 DFT frequencies in closed form
+                                    (diagonal plus rank one; FUSE-type direct solve of the S B
+                                    term).  Same objective and limit, other iterates; P1 and
+                                    Lambda1 are unused.  Needs the regular lattice (no mask),
+                                    E E^T = eps I (orthonormal rows up to a scale, relative
+                                    deviation <= 1e-6) and H, W with 2H+1 complex values per
+                                    column fitting shared memory; not with the reverse pass or a
+                                    batch (FUSE_EUNSUPPORTED).  Switching clears the ADMM state. */
 };
 
 /* Kernel groups for fuse_profile. */

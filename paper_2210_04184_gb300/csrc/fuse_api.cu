@@ -107,6 +107,15 @@ struct fuse_ctx {
     // latent state read / written by the next latent launch (NULL = Sig, in place); set only
     // around directly launched iterations of the taped forward, never while capturing
     void *lat_in = nullptr, *lat_out = nullptr;
+    // X update: 0 = the paper's splitting, 1 = S B kept in the X system (per-alias-class solve).
+    // E E^T = eet_eps I up to the relative deviation eet_dev (measured at fuse_init); the class
+    // tables (sbq, sbp, sbk) and the column-pass shape (fa_m base columns per block, fa_tpc
+    // threads per column) are set when the variant is first selected.
+    int xmode = 0;
+    double eet_eps = 0.0, eet_dev = 0.0;
+    void *sbq = nullptr, *sbp = nullptr, *sbk = nullptr;
+    int fa_m = 1, fa_tpc = 32;
+    size_t fa_smem = 0;
 };
 
 namespace {
@@ -423,7 +432,7 @@ struct Impl {
     static PixelArgs<T> px_args(fuse_ctx* c) {
         return PixelArgs<T>{(const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2,
                             (const T*)c->D9a, (const T*)c->D9b, (const T*)c->M1, (const T*)c->F,
-                            c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask};
+                            c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask, c->xmode == 1 ? 1 : 0};
     }
     template <typename WT>
     static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb) {
@@ -440,6 +449,7 @@ struct Impl {
         CK(c, cudaFuncSetAttribute(fft_rows_fwd_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, A, kMaxSmem));
+        CK(c, cudaFuncSetAttribute(fft_cols_alias_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(pixel_kernel_wide<T>, A, kMaxSmem));
         cudaError_t e = cudaSuccess;
         with_bh(c->bh, [&](auto bh) {
@@ -558,21 +568,40 @@ struct Impl {
 
     static void latent_any(fuse_ctx* c, cudaStream_t s);
 
-    // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.
+    // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.  With xmode 1 (S B
+    // kept in the X system): C = G + U2 + R with the fixed data term G in U1, the column pass
+    // solves the alias classes, and there is no B X and no P1.
     static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed) {
-        stencil<1>(c, s, c->U1, c->C, c->tapsT);
-        CKL(c, "stencil_kernel (right-hand side)");
+        if (c->xmode == 1) {
+            dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
+            rhs_sum_kernel<T><<<grid, dim3(ST_TX, ST_BY), 0, s>>>(st_args(c, c->U1, c->C, nullptr));
+            CKL(c, "rhs_sum_kernel");
+        } else {
+            stencil<1>(c, s, c->U1, c->C, c->tapsT);
+            CKL(c, "stencil_kernel (right-hand side)");
+        }
         const FFTArgs<T> fa = fft_args(c, c->fr_rpb, c->fc_cw);
         dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
         fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
         CKL(c, "fft_rows_fwd_kernel");
-        dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
-        fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
-        CKL(c, "fft_cols_kernel");
+        if (c->xmode == 1) {
+            const FFTAliasArgs<T> aa{(cplx<T>*)c->Y, c->H, c->W, c->d, c->fa_m, c->planH, (const cplx<T>*)c->twH,
+                                     (const T*)c->sbq, (const cplx<T>*)c->sbp, (const T*)c->sbk};
+            const int w = c->W / c->d;
+            dim3 agrid((unsigned)((w + c->fa_m - 1) / c->fa_m), (unsigned)c->npair);
+            fft_cols_alias_kernel<T><<<agrid, c->fa_m * c->d * c->fa_tpc, c->fa_smem, s>>>(aa);
+            CKL(c, "fft_cols_alias_kernel");
+        } else {
+            dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
+            fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
+            CKL(c, "fft_cols_kernel");
+        }
         fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
         CKL(c, "fft_rows_inv_kernel");
-        stencil<0>(c, s, c->X, c->BX, c->tapsB);
-        CKL(c, "stencil_kernel (B X)");
+        if (c->xmode != 1) {
+            stencil<0>(c, s, c->X, c->BX, c->tapsB);
+            CKL(c, "stencil_kernel (B X)");
+        }
         pixel(c, s);
         CKL(c, "pixel_kernel");
         if (timed) {
@@ -594,6 +623,17 @@ struct Impl {
     }
 
     static fuse_status objective(fuse_ctx* c, const void* Yl, const void* Yh, double out[4]);
+
+    static fuse_status sb_data_term(fuse_ctx* c, cudaStream_t s) {
+        const size_t tot = c->n * c->Ls;
+        upsample_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const T*)c->D9a, (T*)c->BX, c->H, c->W, c->d,
+                                                                         c->Ls, (T)(1.0 / c->rho));
+        CKL(c, "upsample_kernel");
+        stencil<0>(c, s, c->BX, c->U1, c->tapsT);
+        CKL(c, "stencil_kernel (B^T S^T Y_l E^T)");
+        c->launches_all += 2;
+        return FUSE_OK;
+    }
 };
 
 template <typename T>
@@ -665,6 +705,9 @@ fuse_status zero_state(fuse_ctx* c, cudaStream_t s) {
     return FUSE_OK;
 }
 
+// kernels launched by one iteration (Impl::iterate)
+int iteration_launches(const fuse_ctx* c) { return c->xmode == 1 ? 6 : 7; }
+
 fuse_status run_iterations(fuse_ctx* c, int iters) {
     if (iters <= 0) return FUSE_OK;
     const bool f64 = c->dtype == FUSE_F64;
@@ -673,7 +716,7 @@ fuse_status run_iterations(fuse_ctx* c, int iters) {
             fuse_status st = f64 ? Impl<double>::iterate(c, c->stream, c->profile)
                                  : Impl<float>::iterate(c, c->stream, c->profile);
             if (st != FUSE_OK) return st;
-            c->launches_all += 7;
+            c->launches_all += iteration_launches(c);
             c->launches_latent += 1;
         }
         return FUSE_OK;
@@ -690,7 +733,7 @@ fuse_status run_iterations(fuse_ctx* c, int iters) {
     }
     for (int t = 0; t < iters; ++t) {
         CK(c, cudaGraphLaunch(c->gexec, c->stream));
-        c->launches_all += 7;
+        c->launches_all += iteration_launches(c);
         c->launches_latent += 1;
     }
     return FUSE_OK;
@@ -711,6 +754,11 @@ fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, i
         st = zero_state(c, c->stream);
         if (st != FUSE_OK) return st;
         c->have_state = true;
+    }
+    if (c->xmode == 1) {
+        // the fixed data term of the variant: U1 = G = B^T S^T Y_l E^T / rho (B X as scratch)
+        st = f64 ? Impl<double>::sb_data_term(c, c->stream) : Impl<float>::sb_data_term(c, c->stream);
+        if (st != FUSE_OK) return st;
     }
     st = run_iterations(c, iters);
     if (st != FUSE_OK) return st;
@@ -784,6 +832,74 @@ fuse_status upload(fuse_ctx* c, void** dst, const std::vector<double>& v) {
 fuse_status upload_any(fuse_ctx* c, void** dst, const std::vector<double>& v) {
     return c->dtype == FUSE_F64 ? upload<double>(c, dst, v) : upload<float>(c, dst, v);
 }
+
+// Tables and launch shape of the column pass of the variant with S B in the X system, in FP64 on
+// the host (see fft_cols_alias_kernel):
+//   b^(u,v) = sum_{a,b} blur(a,b) exp(-2 pi i (u (a - bh/2)/H + v (b - bw/2)/W)),
+//   g = 1 + |P| (2|W| - 2 (Cu Cv - 1)),  p = b^/g,  q = 1/(g H W),
+//   kappa(class) = beta / ((1 + beta sum_class |b^|^2/g) H W),  beta = eps / (rho d^2).
+fuse_status sb_prepare(fuse_ctx* c) {
+    const int H = c->H, W = c->W, d = c->d, h = H / d, w = W / d;
+    // shape: m base columns (m d columns) per block, 2H+1 complex values per column in shared memory
+    const size_t csz = 2 * c->esz;
+    int m = d >= 8 ? 1 : 8 / d;
+    if (m > w) m = w;
+    while (m > 1 && (size_t)m * d * (2 * H + 1) * csz > kMaxSmem) m /= 2;
+    if ((size_t)m * d * (2 * H + 1) * csz > kMaxSmem || m * d > 256)
+        return fail(c, FUSE_EUNSUPPORTED, "the alias-class column pass does not fit shared memory");
+    int tpc = H / 4 < 1 ? 1 : H / 4;
+    while (tpc > 1 && m * d * tpc > 256) tpc /= 2;
+    if (!c->sbq) {
+        const double tp = 2.0 * M_PI;
+        const int rh = c->bh / 2, rw = c->bw / 2;
+        std::vector<double> q(c->n), pf(2 * c->n), kap((size_t)h * w, 0.0), b2g(c->n);
+        std::vector<double> Cu(H), Cv(W);
+        for (int u = 0; u < H; ++u) { double t = 0; for (int k = -c->S; k <= c->S; ++k) t += std::cos(tp * u * k / H); Cu[u] = t; }
+        for (int v = 0; v < W; ++v) { double t = 0; for (int k = -c->S; k <= c->S; ++k) t += std::cos(tp * v * k / W); Cv[v] = t; }
+        // row sums over b first: gr + i gi = sum_b blur(a,b) exp(-2 pi i v (b - bw/2)/W)
+        std::vector<double> gr((size_t)c->bh * W), gi((size_t)c->bh * W);
+        for (int a = 0; a < c->bh; ++a)
+            for (int v = 0; v < W; ++v) {
+                double sr = 0, si = 0;
+                for (int b = 0; b < c->bw; ++b) {
+                    const double ang = -tp * (double)v * (double)(b - rw) / W;
+                    sr += c->htapsT[(size_t)a * c->bw + b] * std::cos(ang);
+                    si += c->htapsT[(size_t)a * c->bw + b] * std::sin(ang);
+                }
+                gr[(size_t)a * W + v] = sr;
+                gi[(size_t)a * W + v] = si;
+            }
+        for (int u = 0; u < H; ++u)
+            for (int v = 0; v < W; ++v) {
+                double br = 0, bi = 0;
+                for (int a = 0; a < c->bh; ++a) {
+                    const double ang = -tp * (double)u * (double)(a - rh) / H;
+                    const double er = std::cos(ang), ei = std::sin(ang);
+                    const double xr = gr[(size_t)a * W + v], xi = gi[(size_t)a * W + v];
+                    br += er * xr - ei * xi;
+                    bi += er * xi + ei * xr;
+                }
+                const double g = 1.0 + (double)c->nP * (2.0 * c->nW - 2.0 * (Cu[u] * Cv[v] - 1.0));
+                const size_t i = (size_t)u * W + v;
+                q[i] = 1.0 / (g * (double)H * (double)W);
+                pf[2 * i] = br / g;
+                pf[2 * i + 1] = bi / g;
+                b2g[i] = (br * br + bi * bi) / g;
+                kap[(size_t)(u % h) * w + (v % w)] += b2g[i];
+            }
+        const double beta = c->eet_eps / (c->rho * (double)d * (double)d);
+        for (double& t : kap) t = beta / ((1.0 + beta * t) * (double)H * (double)W);
+        fuse_status st;
+        if ((st = upload_any(c, &c->sbq, q)) != FUSE_OK) return st;
+        if ((st = upload_any(c, &c->sbp, pf)) != FUSE_OK) return st;
+        if ((st = upload_any(c, &c->sbk, kap)) != FUSE_OK) return st;
+    }
+    c->fa_m = m;
+    c->fa_tpc = tpc;
+    c->fa_smem = (size_t)m * d * (2 * H + 1) * csz;
+    return FUSE_OK;
+}
+
 
 }  // namespace
 
@@ -1244,6 +1360,17 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
             Fm[(size_t)i * Ls + j] = cr * t + (i == j ? 1.0 : 0.0);
         }
     {
+        // E E^T = eps I test for the variant with S B in the X system
+        double tr = 0.0;
+        for (int i = 0; i < Ls; ++i) tr += M1[(size_t)i * Ls + i] - rho;
+        c->eet_eps = tr / Ls;
+        double dev = 0.0;
+        for (int i = 0; i < Ls; ++i)
+            for (int j = 0; j < Ls; ++j)
+                dev = std::max(dev, std::fabs(M1[(size_t)i * Ls + j] - (i == j ? rho + c->eet_eps : 0.0)));
+        c->eet_dev = c->eet_eps > 0 ? dev / c->eet_eps : INFINITY;
+    }
+    {
         // conditioning (before inversion): E E^T + rho I and F^{-1} = I + lambda1/rho E R R^T E^T;
         // A = I + B^T B + sum D^T D is diagonal in the DFT basis with eigenvalues 1/(HW f)
         double lo, hi;
@@ -1539,6 +1666,23 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             }
             return realloc_state(c, c->half, f);
         }
+        case FUSE_OPT_X_UPDATE: {
+            if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "X update is 0 or 1");
+            if (value == c->xmode) return FUSE_OK;
+            if (value == 1) {
+                if (c->mask) return fail(c, FUSE_EUNSUPPORTED, "the S B-in-X update needs the regular lattice");
+                if (!(c->eet_dev <= 1e-6))
+                    return fail(c, FUSE_EUNSUPPORTED, "the S B-in-X update needs E E^T = eps I");
+                if ((st = sb_prepare(c)) != FUSE_OK) return st;
+            }
+            c->xmode = (int)value;
+            ++c->epoch;
+            c->have_state = false;
+            c->have_x = false;
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            return FUSE_OK;
+        }
         case FUSE_OPT_WAIT_LIMIT:
             if (value < 1) return fail(c, FUSE_EINVAL, "wait limit must be positive");
             c->wait_limit = (unsigned)value;
@@ -1666,6 +1810,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_FFT_COLS: *value = c->fc_cw; return FUSE_OK;
         case FUSE_OPT_GRAD_SEGMENT: *value = c->grad_seg; return FUSE_OK;
         case FUSE_OPT_GRAD_WEIGHTS: *value = c->grad_weights; return FUSE_OK;
+        case FUSE_OPT_X_UPDATE: *value = c->xmode; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }
@@ -1714,6 +1859,7 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
             c->Ls != c0->Ls || c->bh != c0->bh || c->bw != c0->bw || c->half != c0->half || c->device != c0->device ||
             c->sfmt != c0->sfmt)
             return FUSE_EINVAL;
+        if (c->xmode != 0) return FUSE_EUNSUPPORTED;     // batches run the paper's splitting
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return FUSE_EINVAL;
     }
@@ -1921,6 +2067,7 @@ fuse_status fuse_set_mask(fuse_ctx* c, const void* mask) {
     fuse_status st = guard(c);
     if (st != FUSE_OK) return st;
     if (mask && c->d != 1) return fail(c, FUSE_EINVAL, "a sampling mask needs ratio 1");
+    if (mask && c->xmode == 1) return fail(c, FUSE_EUNSUPPORTED, "the S B-in-X update needs the regular lattice");
     if (!mask) {
         c->mask = nullptr;
     } else {
@@ -1955,6 +2102,7 @@ fuse_status fuse_grad_forward(fuse_ctx* c, const void* Yl, const void* Yh, int i
     if (!c->have_weights) return FUSE_ESTATE;
     if (pixel_bucket(c->Ls) == 0) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass supports L_s <= 32");
     if (c->sfmt) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass needs the state in the iterate type");
+    if (c->xmode) return fail(c, FUSE_EUNSUPPORTED, "the reverse pass follows the paper's splitting");
     return grad_forward_impl(c, Yl, Yh, iters, X_out);
 }
 

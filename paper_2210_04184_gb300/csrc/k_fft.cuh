@@ -235,6 +235,90 @@ __global__ void __launch_bounds__(256) fft_rows_inv_kernel(FFTArgs<T> a) {
     fft_rows_inv_body<T>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// Column pass of the variant that keeps S B in the X system (not the paper's splitting):
+//   (I + sum D^T D + beta d^2 B^T S^T S B) X_c = C_c,   beta = eps / (rho d^2),  E E^T = eps I.
+// S^T S keeps the lattice i1 = i2 = 0 (mod d), so in the DFT basis frequency (u, v) couples with
+// its d^2 aliases (u + a H/d, v + b W/d): per alias class the system is diag(g) + beta u u^H with
+// u = conj(b^) and g = 1 + |P| sum_tau |d^_{tau 0}|^2.  Sherman-Morrison solves it in closed form:
+//   s = sum_k p_k r_k,   x_j = q_j r_j - conj(p_j) kappa s,
+// with p = b^/g, q = 1/(g H W) and kappa = beta / ((1 + beta sum_k |b^_k|^2/g_k) H W) per class,
+// all precomputed on the host in FP64 (the 1/(HW) of the inverse DFT folded into q and kappa).
+// The solve is C-linear, so the two real bands of a complex transform still ride together.
+//
+// Block (bx, p): the m base columns x0 = bx m .. bx m + m - 1 (< W/d) and, for each, its d alias
+// columns x0 + j + b W/d: column cc = b m + j of the block.  Forward FFT along y of every column,
+// the class solves (one thread per class (u0, j), u0 < H/d), inverse FFT along y.
+template <typename T>
+struct FFTAliasArgs {
+    cplx<T>* Y;              // complex work array [ceil(L_s/2)][H][W], transformed along x already
+    int H, W, d, m;
+    FFTPlan planH;
+    const cplx<T>* twH;
+    const T* q;              // [H][W]
+    const cplx<T>* pf;       // [H][W]
+    const T* kap;            // [H/d][W/d]
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) fft_cols_alias_kernel(FFTAliasArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);      // [CW][2H + 1]
+    const int H = a.H, W = a.W, d = a.d, m = a.m;
+    const int CW = m * d, h = H / d, w = W / d;
+    const int tpc = blockDim.x / CW;
+    const int cw = threadIdx.x / tpc, t = threadIdx.x - cw * tpc;
+    const int x0 = blockIdx.x * m;
+    const size_t n = (size_t)H * W;
+    const int pitch = 2 * H + 1;
+    cplx<T>* Yp = a.Y + (size_t)blockIdx.y * n;
+    const int nld = blockDim.x - blockDim.x % CW;
+    if ((int)threadIdx.x < nld)
+        for (int idx = threadIdx.x; idx < H * CW; idx += nld) {
+            const int row = idx / CW, cc = idx - row * CW;
+            const int b = cc / m, j = cc - b * m;
+            sm[(size_t)cc * pitch + row] =
+                x0 + j < w ? Yp[(size_t)row * W + x0 + j + b * w] : cplx<T>{T(0), T(0)};
+        }
+    __syncthreads();
+    const bool mine = cw < CW;
+    cplx<T>* b0 = sm + (size_t)(mine ? cw : 0) * pitch;
+    cplx<T>* b1 = b0 + H;
+    cplx<T>* res = fft_smem(b0, b1, a.planH, a.twH, -1, t, mine ? tpc : 0);
+    const int off = (int)(res - b0);      // the spectrum of every column sits at this offset
+    for (int cls = threadIdx.x; cls < h * m; cls += blockDim.x) {
+        const int u0 = cls / m, j = cls - u0 * m;
+        if (x0 + j >= w) continue;
+        cplx<T> s = {T(0), T(0)};
+        for (int aa = 0; aa < d; ++aa)
+            for (int bb = 0; bb < d; ++bb) {
+                const int u = u0 + aa * h, x = x0 + j + bb * w;
+                s = cadd(s, cmul(a.pf[(size_t)u * W + x], sm[(size_t)(bb * m + j) * pitch + off + u]));
+            }
+        const T kp = a.kap[(size_t)u0 * w + x0 + j];
+        s.x *= kp;
+        s.y *= kp;
+        for (int aa = 0; aa < d; ++aa)
+            for (int bb = 0; bb < d; ++bb) {
+                const int u = u0 + aa * h, x = x0 + j + bb * w;
+                const cplx<T> pv = a.pf[(size_t)u * W + x];
+                const T qv = a.q[(size_t)u * W + x];
+                const cplx<T> corr = cmul(cplx<T>{pv.x, -pv.y}, s);
+                cplx<T>& r = sm[(size_t)(bb * m + j) * pitch + off + u];
+                r = cplx<T>{qv * r.x - corr.x, qv * r.y - corr.y};
+            }
+    }
+    __syncthreads();
+    cplx<T>* other = res == b0 ? b1 : b0;
+    res = fft_smem(res, other, a.planH, a.twH, +1, t, mine ? tpc : 0);
+    const int off2 = (int)(res - b0);
+    if ((int)threadIdx.x < nld)
+        for (int idx = threadIdx.x; idx < H * CW; idx += nld) {
+            const int row = idx / CW, cc = idx - row * CW;
+            const int b = cc / m, j = cc - b * m;
+            if (x0 + j < w) Yp[(size_t)row * W + x0 + j + b * w] = sm[(size_t)cc * pitch + off2 + row];
+        }
+}
+
 // Batched forms (one launch over many problems, see Segment).
 template <typename T, int PASS>
 __global__ void __launch_bounds__(256)

@@ -29,6 +29,7 @@ struct PixelArgs {
     int H, W, Ls, d;
     T rho;
     const uint8_t* mask;   // sampling mask [H][W] (d = 1) or NULL for the lattice of ratio d
+    int no_p1;             // 1: P2 and Lambda2 only (the variant with S B in the X system has no P1)
 };
 
 template <typename T, int MAXLS>
@@ -52,6 +53,7 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
     const size_t p = (size_t)bx * nb + tid;
     if (p >= n) return;
     T a[MAXLS], w[MAXLS], w1[MAXLS];
+    const bool p1 = !args.no_p1;
     // P2 and Lambda2: a = X - Lambda2 + lambda1/rho Y_h R^T E^T, w = X - Lambda2; the P1 side's
     // w1 = B X - Lambda1 is read here too, before any store, so all loads of the pixel are in flight
 #pragma unroll
@@ -59,7 +61,7 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
         if (j < Ls) {
             w[j] = X[(size_t)j * n + p] - Lam2[(size_t)j * n + p];
             a[j] = w[j] + D9b[(size_t)j * n + p];
-            w1[j] = BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p];
+            w1[j] = p1 ? BX[(size_t)j * n + p] - Lam1[(size_t)j * n + p] : T(0);
         }
     }
 #pragma unroll
@@ -74,6 +76,7 @@ __device__ __forceinline__ void pixel_body(const PixelArgs<T>& args, int bx, uns
             U2[(size_t)c * n + p] = acc + l2;
         }
     }
+    if (!p1) return;
     // P1 and Lambda1: w = B X - Lambda1
 #pragma unroll
     for (int j = 0; j < MAXLS; ++j)
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(128) pixel_kernel_wide(PixelArgs<T> args) {
         Lam2[c * n + p] = l2;
         U2[c * n + p] = acc + l2;
     }
+    if (args.no_p1) return;
     const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
     if (sampled_pixel(args.mask, p, y, x, d)) {
         const size_t nl = (size_t)(H / d) * (W / d);
@@ -174,6 +178,21 @@ __global__ void __launch_bounds__(128) pixel_kernel_wide(PixelArgs<T> args) {
             U1[c * n + p] = w1;
         }
     }
+}
+
+// S^T Y_l E^T / rho on the full grid: out[c][y][x] = scale lo[c][y/d][x/d] on the lattice
+// y = x = 0 (mod d), 0 elsewhere (the data term of the variant with S B in the X system).
+template <typename T>
+__global__ void __launch_bounds__(256)
+upsample_kernel(const T* __restrict__ lo, T* __restrict__ out, int H, int W, int d, int Ls, T scale) {
+    const size_t n = (size_t)H * W;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * Ls) return;
+    const int c = (int)(idx / n);
+    const size_t pix = idx - (size_t)c * n;
+    const int y = (int)(pix / W), x = (int)(pix - (size_t)y * W);
+    const size_t nl = (size_t)(H / d) * (W / d);
+    out[idx] = (y % d == 0 && x % d == 0) ? scale * lo[(size_t)c * nl + (size_t)(y / d) * (W / d) + x / d] : T(0);
 }
 
 // out[c][p] = sum_l in[l][p] M[l][c] for every pixel p (band mixing: S^T Y_l E^T,

@@ -143,6 +143,26 @@ __global__ void __launch_bounds__(256) stencil_sq_kernel(StencilArgs<T> a, Squar
     stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
 }
 
+// C = G + U2 + R without a blur: the right-hand side of the variant that keeps S B in the X
+// system, where the data term G = B^T S^T Y_l E^T / rho is fixed for the whole solve and
+// precomputed once (in = G).  Same tiles and epilogue as the stencils.
+template <typename T>
+__global__ void __launch_bounds__(256) rhs_sum_kernel(StencilArgs<T> a) {
+    constexpr int QY = ST_TY / ST_BY;
+    const int x = blockIdx.x * ST_TX + threadIdx.x;
+    if (x >= a.W) return;
+    const int y0 = blockIdx.y * ST_TY + threadIdx.y * QY;
+    const int c = blockIdx.z;
+    const size_t n = (size_t)a.H * a.W;
+    T acc[QY];
+#pragma unroll
+    for (int q = 0; q < QY; ++q) {
+        const int y = y0 + q;
+        acc[q] = y < a.H ? a.in[(size_t)c * n + (size_t)y * a.W + x] : T(0);
+    }
+    stencil_store<T, 1, QY>(a, acc, x, y0, c);
+}
+
 template <typename T, int MODE, int BH>
 __global__ void __launch_bounds__(256) stencil_kernel(StencilArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
