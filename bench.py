@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--grad-only", action="store_true", help="only the reverse-pass measurement")
     ap.add_argument("--grad-workload", default="unrolled_256", help="workload of the reverse-pass measurement")
     ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-point state measurement")
+    ap.add_argument("--no-sb", action="store_true", help="skip the S B-in-X update measurement")
     ap.add_argument("--fixed-state", action="store_true",
                     help="run the main measurement with the 16-bit fixed-point latent state")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
@@ -319,6 +320,42 @@ def fixed_point_bench(a, p, meta, yl, yh, Z64):
                          "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per, "launches": lat_n,
                          "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
             "rel_err_Z_vs_fp64": err, "equal_error_1e-4": err is not None and err <= 1e-4}
+
+
+def sb_bench(a, p, meta, yl, yh, f0):
+    """The same workload with the X update that keeps S B in the X system (FUSE_OPT_X_UPDATE = 1,
+    alias-class solves in the column FFT pass): throughput, and the objective after the
+    workload's iterations next to the paper's splitting (same objective, other iterates)."""
+    import torch
+    from paper_2210_04184_gb300.fuse import Fusion, FUSE_OPT_X_UPDATE, fuse_solve, fuse_weights, fuse_set_stream
+    f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
+    f.set_option(FUSE_OPT_X_UPDATE, 1)
+    st = torch.cuda.current_stream()
+    fuse_set_stream(f.ctx, st.cuda_stream)
+    fuse_weights(f.ctx, yh.data_ptr())
+    Z = torch.empty((p.L_l, p.H, p.W), dtype=yl.dtype, device="cuda")
+
+    def step():
+        fuse_weights(f.ctx, yh.data_ptr())
+        fuse_solve(f.ctx, yl.data_ptr(), yh.data_ptr(), p.iters, 0, None, Z.data_ptr())
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    obj_sb = sum(f.objective(yl, yh)[:3])
+    obj_paper = sum(f0.objective(yl, yh)[:3])
+    f.close()
+    return {"x_update": "S B kept in the X system (alias-class solves)",
+            "value": p.H * p.W / 1e6 * p.L_s * p.iters * a.steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / a.steps, "iters": p.iters,
+            "objective": obj_sb, "objective_paper_splitting": obj_paper}
 
 
 def run_batch(a, rank, world, local_rank):
@@ -643,6 +680,9 @@ def run_ours(a, rank, world, local_rank):
     fixed = None
     if not a.no_fixed and rank == 0 and meta["dtype"] == "f32" and p.W % 8 == 0:
         fixed = fixed_point_bench(a, p, meta, yl, yh, Z64)
+    sbx = None
+    if not a.no_sb and rank == 0 and p.d > 1 and "mask" not in meta:
+        sbx = sb_bench(a, p, meta, yl, yh, f)
     grad = None
     if not a.no_grad and rank == 0 and a.workload == "hsms_256":
         grad = grad_bench(a, rank)
@@ -679,6 +719,7 @@ def run_ours(a, rank, world, local_rank):
         "fp64_compare": fp64,
         "conditioning": dict(zip(("A_x_update", "EEt_plus_rho", "F_inverse"), fuse_conditioning(f.ctx))),
         "fixed_point_state": fixed,
+        "sb_x_update": sbx,
         "grad": grad,
     }
     if not a.no_cpu_baseline and world == 1:
