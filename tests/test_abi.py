@@ -36,6 +36,27 @@ def test_binding_has_same_names(lib):
         assert callable(getattr(fuse, name)), name
 
 
+def test_binding_constants_match_the_header():
+    # every enumerator of include/fuse.h (statuses, dtypes, options, kernel groups) has the same
+    # value in the Python binding
+    txt = re.sub(r"/\*.*?\*/", "", (ROOT / "include" / "fuse.h").read_text(), flags=re.S)
+    enums = re.findall(r"enum\s*(?:\w+\s*)?\{(.*?)\}", txt, flags=re.S)
+    found = {}
+    for body in enums:
+        nxt = 0
+        for item in (e.strip() for e in body.split(",")):
+            if not item:
+                continue
+            m = re.fullmatch(r"(FUSE_\w+)\s*(?:=\s*(-?\d+))?", item)
+            assert m, item
+            nxt = int(m.group(2)) if m.group(2) is not None else nxt
+            found[m.group(1)] = nxt
+            nxt += 1
+    assert "FUSE_OPT_X_UPDATE" in found and "FUSE_EUNSUPPORTED" in found
+    for name, value in found.items():
+        assert getattr(fuse, name) == value, name
+
+
 def test_status_strings(lib):
     assert fuse.fuse_status_string(fuse.FUSE_OK) == "FUSE_OK"
     assert fuse.fuse_status_string(fuse.FUSE_EUNSUPPORTED) == "FUSE_EUNSUPPORTED"
