@@ -845,6 +845,8 @@ fuse_status sb_prepare(fuse_ctx* c) {
     int m = d >= 8 ? 1 : 8 / d;
     if (m > w) m = w;
     while (m > 1 && (size_t)m * d * (2 * H + 1) * csz > kMaxSmem) m /= 2;
+    // fewer base columns per block until the pass has about four blocks per SM
+    while (m > 1 && (long long)((w + m - 1) / m) * c->npair < 4 * 152) m /= 2;
     if ((size_t)m * d * (2 * H + 1) * csz > kMaxSmem || m * d > 256)
         return fail(c, FUSE_EUNSUPPORTED, "the alias-class column pass does not fit shared memory");
     int tpc = H / 4 < 1 ? 1 : H / 4;

@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(256) fft_cols_alias_kernel(FFTAliasArgs<T> a) 
         if (x0 + j >= w) continue;
         cplx<T> s = {T(0), T(0)};
         for (int aa = 0; aa < d; ++aa)
+#pragma unroll 4
             for (int bb = 0; bb < d; ++bb) {
                 const int u = u0 + aa * h, x = x0 + j + bb * w;
                 s = cadd(s, cmul(a.pf[(size_t)u * W + x], sm[(size_t)(bb * m + j) * pitch + off + u]));
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(256) fft_cols_alias_kernel(FFTAliasArgs<T> a) 
         s.x *= kp;
         s.y *= kp;
         for (int aa = 0; aa < d; ++aa)
+#pragma unroll 4
             for (int bb = 0; bb < d; ++bb) {
                 const int u = u0 + aa * h, x = x0 + j + bb * w;
                 const cplx<T> pv = a.pf[(size_t)u * W + x];
