@@ -1780,14 +1780,18 @@ fuse_status fuse_autotune(fuse_ctx* c, const void* Yl, const void* Yh, int iters
             if (t < best) { best = t; best_r = r; }
         }
         fuse_set_option(c, FUSE_OPT_FFT_ROWS, best_r);
-        best = 1e30;
-        int best_c = c->fc_cw;
-        for (int cw : {2, 4, 8, 16}) {
-            if (fuse_set_option(c, FUSE_OPT_FFT_COLS, cw) != FUSE_OK) { fuse_reset_error(c); continue; }
-            if ((st = time_iterations(c, iters, &t)) != FUSE_OK) return st;
-            if (t < best) { best = t; best_c = cw; }
+        // the column width applies to the paper's column pass only (the S B-in-X variant's
+        // column pass takes its shape from the alias classes)
+        if (c->xmode != 1) {
+            best = 1e30;
+            int best_c = c->fc_cw;
+            for (int cw : {2, 4, 8, 16}) {
+                if (fuse_set_option(c, FUSE_OPT_FFT_COLS, cw) != FUSE_OK) { fuse_reset_error(c); continue; }
+                if ((st = time_iterations(c, iters, &t)) != FUSE_OK) return st;
+                if (t < best) { best = t; best_c = cw; }
+            }
+            fuse_set_option(c, FUSE_OPT_FFT_COLS, best_c);
         }
-        fuse_set_option(c, FUSE_OPT_FFT_COLS, best_c);
     }
     if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
     if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }

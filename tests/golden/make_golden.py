@@ -2,7 +2,8 @@
 
 tiny_admm.json: a 6x8 problem (L_l=3, L_h=2, L_s=2, d=2, 3x3 blur, K=1, S=1) with its
 inputs and the oracle's X after 1, 2 and 7 ADMM iterations of Sec. IV from zero
-initialisation (threshold lambda2*omega/rho, eq. Qj_main).  Regression fixture: the paper
+initialisation (threshold lambda2*omega/rho, eq. Qj_main), and after 1 and 7 iterations of
+the variant that keeps S B in the X system (x_update="sb").  Regression fixture: the paper
 prints no worked example, so these values are the oracle's, pinned by the oracle tests.
 
 Run:  python tests/golden/make_golden.py
@@ -43,6 +44,10 @@ def main():
                              p["lam1"], p["lam2"], p["rho"], om, n - done, state=st)
         done = n
         out[f"X_{n}"] = X.tolist()
+    for n in (1, 7):
+        X, _, _ = nlpr.admm(p["Yl"], p["Yh"], p["kern"], p["d"], p["R"], p["E"], p["K"], p["S"],
+                            p["lam1"], p["lam2"], p["rho"], om, n, x_update="sb")
+        out[f"Xsb_{n}"] = X.tolist()
     path = pathlib.Path(__file__).with_name("tiny_admm.json")
     path.write_text(json.dumps(out))
     print("wrote", path)
