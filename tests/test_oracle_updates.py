@@ -262,3 +262,66 @@ def test_p1_update_with_a_random_mask_solves_its_subproblem():
     rhs = np.concatenate([nlpr.mat(Yl)[keep].reshape(-1), np.sqrt(rho) * V.reshape(-1)])
     ref = np.linalg.lstsq(lhs, rhs, rcond=None)[0].reshape(H, W, L_s)
     assert np.abs(P1 - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def _cg(apply_A, b, tol=1e-15, maxit=5000):
+    """Plain conjugate gradients for a symmetric positive definite operator (matrix-free)."""
+    x = np.zeros_like(b)
+    r = b - apply_A(x)
+    p = r.copy()
+    rr = float((r * r).sum())
+    b2 = float((b * b).sum())
+    for _ in range(maxit):
+        Ap = apply_A(p)
+        alpha = rr / float((p * Ap).sum())
+        x += alpha * p
+        r -= alpha * Ap
+        rn = float((r * r).sum())
+        if rn <= tol * tol * b2:
+            break
+        p = r + (rn / rr) * p
+        rr = rn
+    return x
+
+
+@pytest.mark.parametrize("H,W,K,S", [(16, 20, 1, 2), (18, 15, 2, 1)])
+def test_x_update_matches_matrix_free_cg(H, W, K, S):
+    # eq. x_linear_system_main solved by CG with the spatial operators (the paper's rejected
+    # splitting solves this system iteratively); the per-frequency division of eq. inv agrees.
+    rng = _rng(31)
+    kern = rng.random((5, 3))
+    kern /= kern.sum()
+    C = rng.standard_normal((H, W, 2))
+
+    def A(x):
+        y = x + nlpr.blur_t(nlpr.blur(x, kern), kern)
+        for tau in nlpr.search_offsets(S):
+            for k in nlpr.patch_offsets(K):
+                y = y + nlpr.diff_op_t(nlpr.diff_op(x, tau, k), tau, k)
+        return y
+    Xcg = _cg(A, C)
+    Xf = nlpr.solve_x(C, nlpr.x_denominator(H, W, kern, K, S))
+    assert np.abs(Xf - Xcg).max() <= 1e-12 * np.abs(Xcg).max()
+
+
+@pytest.mark.parametrize("H,W,d,K,S", [(16, 24, 4, 1, 1), (18, 12, 3, 1, 2)])
+def test_sb_band_solve_matches_matrix_free_cg(H, W, d, K, S):
+    # the S B-in-X system I + sum D^T D + gamma B^T S^T S B, by CG with the spatial operators
+    rng = _rng(32)
+    kern = rng.random((3, 5))
+    kern /= kern.sum()
+    c = rng.standard_normal((H, W))
+    gamma = 2.3
+
+    def A(x):
+        x3 = x[:, :, None]
+        y = x3.copy()
+        for tau in nlpr.search_offsets(S):
+            for k in nlpr.patch_offsets(K):
+                y = y + nlpr.diff_op_t(nlpr.diff_op(x3, tau, k), tau, k)
+        sb = nlpr.decimate_t(nlpr.decimate(nlpr.blur(x3, kern), d), d, H, W)
+        return (y + gamma * nlpr.blur_t(sb, kern))[:, :, 0]
+    xcg = _cg(A, c)
+    bhat, g = nlpr.sb_spectra(H, W, kern, K, S)
+    x = nlpr.solve_x_sb_band(c, bhat, g, d, gamma)
+    assert np.abs(x - xcg).max() <= 1e-12 * np.abs(xcg).max()
