@@ -1,6 +1,7 @@
 """Theorem 1 pins (CPU only): the oracle's ADMM converges to a minimiser of
 l(X) + lambda2 phi(X), checked against an independent primal-dual (Chambolle-Pock)
-solver built here from dense matrices written from the definitions, and against the
+solver built here from dense matrices written from the definitions, against a gradient
+method on the Huber-smoothed objective (within the smoothing bound), and against the
 special cases lambda2 = 0 (least squares) and lambda2 -> infinity (constant bands)."""
 import numpy as np
 import pytest
@@ -107,6 +108,25 @@ def test_admm_limit_matches_chambolle_pock_objective():
     # primal residuals of the splitting are small at the limit
     BX = nlpr.blur(X, kern)
     assert np.abs(BX - st.P1).max() < 1e-9 and np.abs(X - st.P2).max() < 1e-9
+    # a gradient method on the Huber-smoothed objective (|x| -> x^2/(2 delta) within delta):
+    # 0 <= |x| - huber(x) <= delta/2, so its minimiser lies within sum(w) delta/2 of the minimum
+    opt = pytest.importorskip("scipy.optimize")
+    A = dp.M1.T @ dp.M1 + dp.lam1 * dp.M2.T @ dp.M2
+    b = dp.M1.T @ dp.y1 + dp.lam1 * dp.M2.T @ dp.y2
+    c0 = 0.5 * dp.y1 @ dp.y1 + 0.5 * dp.lam1 * dp.y2 @ dp.y2
+    gaps = []
+    for delta in (1e-2, 1e-3, 1e-4):
+        def fg(x, delta=delta):
+            kx = dp.Kop @ x
+            hub = np.where(np.abs(kx) <= delta, kx * kx / (2 * delta), np.abs(kx) - delta / 2)
+            g = A @ x - b + dp.Kop.T @ (dp.w * np.clip(kx / delta, -1.0, 1.0))
+            return 0.5 * x @ A @ x - b @ x + c0 + dp.w @ hub, g
+        r = opt.minimize(fg, np.zeros(A.shape[0]), jac=True, method="L-BFGS-B",
+                         options=dict(maxiter=200000, maxfun=400000, gtol=1e-13, ftol=1e-16, maxcor=30))
+        gap = dp.objective(r.x) - f_admm
+        assert -1e-10 * abs(f_admm) <= gap <= dp.w.sum() * delta / 2
+        gaps.append(gap)
+    assert gaps[2] < gaps[1] < gaps[0]
 
 
 @pytest.mark.slow
