@@ -143,6 +143,28 @@ def test_admm_limit_unique_minimiser_strictly_convex():
     assert np.abs(X.reshape(-1) - x_cp).max() < 1e-10
 
 
+@pytest.mark.slow
+def test_anisotropic_tv_ablation_limit_matches_chambolle_pock():
+    # K = 0, omega = 1 on the 4-neighbour offsets and 0 on the diagonals of the 3x3 window:
+    # phi is anisotropic TV (the paper's local-regulariser ablation); same CP comparison.
+    Yl, Yh, kern, R, E, G = _tiny(34, d=2)
+    K, S, lam1, lam2, rho = 0, 1, 0.8, 0.03, 0.5
+    H, W = Yh.shape[:2]
+    om = np.zeros((len(nlpr.search_offsets(S)), H, W))
+    for t, tau in enumerate(nlpr.search_offsets(S)):
+        if abs(tau[0]) + abs(tau[1]) == 1:
+            om[t] = 1.0
+    X, _, _ = nlpr.admm(Yl, Yh, kern, 2, R, E, K, S, lam1, lam2, rho, om, 6000, fast=True)
+    dp = DenseProblem(Yl, Yh, kern, 2, R, E, K, S, lam1, lam2, om)
+    f_admm = dp.objective(X.reshape(-1))
+    # phi is the sum of |X_c(i) - X_c(i - e)| over both axes and both signs of e
+    tv = sum(np.abs(X - nlpr.shift(X, e)).sum() for e in ((1, 0), (-1, 0), (0, 1), (0, -1)))
+    f_def = nlpr.objective(X, Yl, Yh, kern, 2, R, E, np.zeros_like(om), K, S, lam1, 0.0) + lam2 * tv
+    assert abs(f_admm - f_def) <= 1e-12 * abs(f_def)
+    f_cp = dp.objective(dp.chambolle_pock(20000))
+    assert abs(f_admm - f_cp) <= 1e-10 * abs(f_cp)
+
+
 def test_lambda2_zero_is_least_squares():
     # lambda2 = 0: the ADMM limit minimises l(X) alone; compare with a dense least squares.
     Yl, Yh, kern, R, E, G = _tiny(32, d=1, E_identity=True, H=5, W=5, center=0.6)
