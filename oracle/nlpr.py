@@ -496,6 +496,23 @@ def admm_step(st: State, su: Setup, x_solver=None, latent_fn=None, dtsum_fn=None
     return State(P1, P2, Lam1, Lam2, Q, Sig, X, st.t + 1)
 
 
+def residuals(prev: State, st: State, su: Setup) -> tuple[float, float]:
+    """ADMM residual norms of the iteration prev -> st (scaled form of the splitting of eq.
+    fusionoptim: constraint A X = z with A = (B; I; D_{tau k}) and z = (P1, P2, Q)):
+      primal  ||A X - z||        = sqrt(||B X - P1||^2 + ||X - P2||^2 + sum ||D_{tau k} X - Q||^2)
+      dual    rho ||A^T (z - z_prev)|| = rho ||B^T dP1 + dP2 + sum D^T dQ||
+    at the new iterates (X, z) = (st.X, st.P1, st.P2, st.Q).  Not printed in the paper, which
+    monitors the objective; the standard ADMM stopping quantities."""
+    X = st.X
+    r2 = float(((blur(X, su.kern) - st.P1) ** 2).sum() + ((X - st.P2) ** 2).sum())
+    for t, tau in enumerate(search_offsets(su.S)):
+        for kk, k in enumerate(patch_offsets(su.K)):
+            r2 += float(((diff_op(X, tau, k) - st.Q[t, kk]) ** 2).sum())
+    s = blur_t(st.P1 - prev.P1, su.kern) + (st.P2 - prev.P2) + dt_sum(st.Q - prev.Q, np.zeros_like(st.Q),
+                                                                        su.K, su.S)
+    return float(np.sqrt(r2)), float(su.rho * np.sqrt((s * s).sum()))
+
+
 def quantize_state(Sig: np.ndarray, omega: np.ndarray, lam2: float, rho: float, levels: int) -> np.ndarray:
     """Sigma as stored in `levels`-step fixed point relative to its own threshold.
 

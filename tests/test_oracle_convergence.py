@@ -205,3 +205,37 @@ def test_objective_plateaus():
     assert abs(vals[-1] - vals[-100]) <= 1e-4 * abs(vals[-1])
     tail = np.array(vals[-500:])
     assert np.all(np.diff(tail) <= 1e-12 * abs(vals[-1]))        # monotone tail
+
+
+def test_residuals_follow_the_dual_updates_and_vanish_at_the_limit():
+    # primal residual = size of the scaled-dual change of the same iteration (eqs. dualvar1_main,
+    # dualvar2_main, dualvar3_main: Lambda1 - (B X - P1), Lambda2 - (X - P2), Sigma - (D X - Q));
+    # both residuals -> 0 as the iterates converge (Theorem 1).
+    Yl, Yh, kern, R, E, G = _tiny(35, d=2)
+    K, S, lam1, lam2, rho = 1, 1, 0.8, 0.02, 0.5
+    om = nlpr.weights(G, K, S, 0.5)
+    su = nlpr.setup(Yl, Yh, kern, 2, R, E, K, S, lam1, lam2, rho, om)
+    st = nlpr.State.zeros(su.H, su.W, su.L_s, K, S)
+    from oracle import cloops
+    hist = []
+    for t in range(3000):
+        nxt = nlpr.admm_step(st, su, latent_fn=cloops.latent_update, dtsum_fn=cloops.dt_sum)
+        if t in (0, 1, 10, 2999):
+            rp, rd = nlpr.residuals(st, nxt, su)
+            dl = np.sqrt(((nxt.Lam1 - st.Lam1) ** 2).sum() + ((nxt.Lam2 - st.Lam2) ** 2).sum()
+                         + ((nxt.Sig - st.Sig) ** 2).sum())
+            assert abs(rp - dl) <= 1e-12 * max(dl, 1e-300)
+            # dual residual another way: C = A^T (z + Lambda) and Lambda' - Lambda = -(A X' - z'),
+            # so A^T (z' - z) = C' - C + A^T r' with r' = A X' - z'
+            X = nxt.X
+            Atr = nlpr.blur_t(nlpr.blur(X, kern) - nxt.P1, kern) + (X - nxt.P2)
+            for ti, tau in enumerate(nlpr.search_offsets(S)):
+                for kk, k in enumerate(nlpr.patch_offsets(K)):
+                    Atr = Atr + nlpr.diff_op_t(nlpr.diff_op(X, tau, k) - nxt.Q[ti, kk], tau, k)
+            sv = nlpr.rhs(nxt, su) - nlpr.rhs(st, su) + Atr
+            rd2 = rho * np.sqrt((sv * sv).sum())
+            assert abs(rd - rd2) <= 1e-9 * max(rd2, 1e-300)
+            hist.append((rp, rd))
+        st = nxt
+    assert hist[0][0] > 1e-3 and hist[0][1] > 1e-3
+    assert hist[-1][0] < 1e-6 * hist[0][0] and hist[-1][1] < 1e-4 * hist[0][1]
