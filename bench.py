@@ -34,6 +34,8 @@ METRIC = "ADMM throughput (megapixel*band*iter/s)"
 # ncu capture summarised in profiles/latent_tma_kernel_hsms128.md (128x128 case, the same kernel
 # and launch shape), per pixel; scaled to the workload by its pixel count (the traffic is
 # proportional to it).  Must be re-measured whenever the latent kernel changes.
+# nominal HBM3e bandwidth of one GB300 (context only; the roofline divides by the measured copy)
+NOMINAL_HBM_GBS = 7900.0
 LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.702720e6 + 738.255872e6) / (128 * 128)}
 UNIT = "Mpx*band*iter/s"
 
@@ -712,7 +714,7 @@ def run_ours(a, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "kernel": "latent_tma_kernel",
                      "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms,
-                     "launches": lat_n, "peak_source": peak_src},
+                     "launches": lat_n, "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS},
         "gpu_launches": launches,
         "clocks": clk,
         "e2e": e2e,
