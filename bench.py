@@ -33,10 +33,10 @@ METRIC = "ADMM throughput (megapixel*band*iter/s)"
 # nominal HBM3e bandwidth of one GB300 (context only; the roofline divides by the measured copy)
 NOMINAL_HBM_GBS = 7900.0
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch, from the
-# ncu capture summarised in profiles/latent_tma_kernel_hsms128.md (128x128 case, the same kernel
-# and launch shape), per pixel; scaled to the workload by its pixel count (the traffic is
-# proportional to it).  Must be re-measured whenever the latent kernel changes.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch, from an
+# ncu capture of the 128x128 case of the same workload (the same kernel and launch shape), per
+# pixel; scaled to the workload by its pixel count (the traffic is proportional to it).  Must be
+# re-measured whenever the latent kernel changes.
 LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.702720e6 + 738.255872e6) / (128 * 128)}
 UNIT = "Mpx*band*iter/s"
 
