@@ -46,7 +46,7 @@ typedef enum fuse_status {
     FUSE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
     FUSE_ENONFINITE = 5,    /* a non-finite value was detected in a monitored quantity */
     FUSE_ESTATE = 6,        /* call not valid in the context's state (sticky error, no weights) */
-    FUSE_EUNSUPPORTED = 7   /* valid request this build does not support (e.g. FFT size) */
+    FUSE_EUNSUPPORTED = 7   /* valid request the library does not support (e.g. FFT size) */
 } fuse_status;
 
 typedef enum fuse_dtype {
