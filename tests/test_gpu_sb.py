@@ -30,8 +30,8 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def problem(H=40, W=48, d=4, L_s=3, K=1, S=2, blur=(5, 5), seed=81, E_scale=1.0, **kw):
-    p = synth.make_problem(H=H, W=W, L_l=6, L_h=2, L_s=L_s, d=d, blur_size=5, blur_sigma=1.0, K=K, S=S,
+def problem(H=40, W=48, d=4, L_s=3, K=1, S=2, blur=(5, 5), seed=81, E_scale=1.0, L_l=6, **kw):
+    p = synth.make_problem(H=H, W=W, L_l=L_l, L_h=2, L_s=L_s, d=d, blur_size=5, blur_sigma=1.0, K=K, S=S,
                            lam1=1.0, lam2=1e-2, rho=5e-2, h=0.3, seed=seed, **kw)
     rng = np.random.default_rng(seed + 1)
     k = rng.random(blur) + 0.2                      # asymmetric: b^ is complex
@@ -71,6 +71,8 @@ def omega_of(p, dtype):
     dict(H=30, W=40, d=1, K=0, blur=(5, 3), seed=84),           # classes of one frequency
     dict(E_scale=1.7, seed=85),                                  # E E^T = 2.89 I
     dict(H=64, W=96, d=4, L_s=5, K=1, S=1, seed=86),            # several blocks per band pair, odd L_s
+    # 49 band pairs: two base columns per block and W/d = 25, so the last block is half masked
+    dict(H=40, W=100, d=4, L_l=100, L_s=98, K=0, S=1, blur=(3, 3), seed=91),
 ])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_sb_update_matches_oracle(case, dtype):
