@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
 """Benchmark of the NLPR fusion ADMM on GB300 (prints one JSON line on rank 0).
 
-A step is one pass of the whole hot path over one synthetic problem: guide weights
-(eq. wts), `iters` ADMM iterations (Sec. IV) and the output Z = X E.  The default workload
-is HS+MS fusion at 256 x 256 x 93 bands, subspace L_s = 20, 5x5 patches, 7x7 search window,
-BF16 weights, FP32 iterates, 100 iterations.
+Default workload (batch64): 64 independent HS+MS problems of square sizes drawn from
+{96, 128, 192, 256, 320, 384}, 31 bands, MS guide of 3 bands, subspace L_s = 8, 3x3 patches,
+7x7 search window, FP32 iterates with BF16 weights, 100 iterations each, solved together
+(one launch per ADMM phase over all problems, the whole iteration loop replayed from a CUDA
+graph).  A step is one pass of the whole hot path over the batch: guide weights of every
+problem (eq. wts), the 100 batched ADMM iterations (Sec. IV) and the outputs Z = X E.  The
+line also carries the single-problem HS+MS workload (256 x 256 x 93 bands, L_s = 20, 5x5
+patches, 7x7 window, 100 iterations) as a secondary measurement.
 
-Metric: megapixel-band-iterations per second, (H W / 1e6) L_s iters / seconds, summed over
-ranks (each rank solves its own independent problem: weak scaling, no data-path collective).
+Metric: megapixel-band-iterations per second, (sum of H W / 1e6) L_s iters / seconds, summed over
+ranks (each rank solves its own independent batch: weak scaling, no data-path collective).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 """
@@ -33,11 +37,18 @@ METRIC = "ADMM throughput (megapixel*band*iter/s)"
 # nominal HBM3e bandwidth of one GB300 (context only; the roofline divides by the measured copy)
 NOMINAL_HBM_GBS = 7900.0
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch, from an
-# ncu capture of the 128x128 case of the same workload (the same kernel and launch shape), per
-# pixel; scaled to the workload by its pixel count (the traffic is proportional to it).  Must be
-# re-measured whenever the latent kernel changes.
-LATENT_TRAFFIC_PER_PIXEL = {"hsms": (788.702720e6 + 738.255872e6) / (128 * 128)}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one latent-pass launch per pixel of
+# the problems it covers, from an ncu capture of a smaller case of the same kernel and launch shape
+# (the traffic is proportional to the pixel count), with a digest of the kernel's sources at the
+# time of the capture: a line reports the traffic only while the sources still match (null once
+# the kernel has changed since the counters were taken).
+LATENT_TRAFFIC = {
+    # latent_tma_kernel, hsms_128 (FP32 state, BF16 weights, K = 2, S = 3, L_s = 20)
+    "hsms": {"bytes_per_pixel": (788.702720e6 + 738.255872e6) / (128 * 128), "sources": None},
+    # latent_tma_batch_kernel, the batch workload's first 8 problems (K = 1, S = 3, L_s = 8)
+    "batch": {"bytes_per_pixel": None, "sources": None},
+}
+LATENT_SOURCES = ("k_latent.cuh", "tma.cuh", "common.cuh", "launch_latent.cu")
 UNIT = "Mpx*band*iter/s"
 
 
@@ -47,7 +58,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hsms_256")
+    ap.add_argument("--workload", default="batch64")
+    ap.add_argument("--problems", type=int, default=64, help="problems of the batch workload")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the single-problem secondary line")
     ap.add_argument("--iters", type=int, default=None, help="override the workload's iteration count")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -174,6 +187,57 @@ def latent_bytes(p, esz, wsz, half=True, ssz=None):
             + 2 * rows * p.L_s * n * esz)
 
 
+def _sources_digest():
+    """sha256 (16 hex digits) of the latent kernel's sources, to tell whether a stored traffic
+    figure still describes the kernel that runs."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = ROOT / "paper_2210_04184_gb300" / "csrc"
+    for name in LATENT_SOURCES:
+        h.update((csrc / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def latent_traffic(kind, pixels):
+    """DRAM bytes of one latent launch over `pixels` pixels from the stored capture, or None when
+    there is none or the kernel's sources changed since it was taken."""
+    t = LATENT_TRAFFIC.get(kind)
+    if not t or t["bytes_per_pixel"] is None or t["sources"] != _sources_digest():
+        return None
+    return t["bytes_per_pixel"] * pixels
+
+
+def timed_region(step, steps, stream, dist):
+    """Device time (ms) of `steps` calls of step() between CUDA events on `stream`, bracketed by
+    a barrier and a device synchronisation on both sides."""
+    import torch
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1)
+
+
+def batch_config(ps, iters, world):
+    sizes = sorted(set(p.H for p in ps))
+    p0 = ps[0]
+    return {"workload": "batch64", "problems": len(ps), "sizes": sizes, "pixels": sum(p.H * p.W for p in ps),
+            "bands": p0.L_l, "L_h": p0.L_h, "L_s": p0.L_s, "ratio": p0.d,
+            "patch": f"{2 * p0.K + 1}x{2 * p0.K + 1}", "search": f"{2 * p0.S + 1}x{2 * p0.S + 1}",
+            "offsets": (2 * p0.S + 1) ** 2 - 1, "iters": iters, "weights": "bf16",
+            "global_batch": len(ps) * world, "parallelism": f"batched problems, independent batches x{world}",
+            "l2": "latent state of the batch exceeds L2 (no flush needed)",
+            "latent_state": "half window (one offset of each +-tau pair)"}
+
+
 def cpu_baseline(p, target_s=15.0):
     """The FP64 oracle timed on the host cores on a bounded crop of the same workload
     (same bands, subspace, patch and window; a 48 x 48 image; weights plus n iterations,
@@ -204,14 +268,19 @@ def cpu_baseline(p, target_s=15.0):
 
 
 def run_reference(a, rank, world):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on bounded samples of the
+    workload (see cpu_baseline), with this arm's metric, unit and config."""
     if rank != 0:
         return
+    from paper_2210_04184_gb300 import synth
     if a.workload == "batch64":
-        from paper_2210_04184_gb300 import synth
-        p = synth.batch_workload(1)[0]
-        meta = {"dtype": "f32", "wdtype": "bf16"}
+        ps = synth.batch_workload(a.problems)
+        iters = a.iters or ps[0].iters
+        p = ps[0]
+        config = batch_config(ps, iters, a.gpus)
     else:
         p, meta = _workload(a.workload, 0, a.iters)
+        config = _config(p, meta, a.workload, a.gpus)
     samples = []
     cb = None
     for i in range(a.warmup + a.steps):
@@ -223,7 +292,7 @@ def run_reference(a, rank, world):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": _config(p, meta, a.workload, a.gpus), "cpu_baseline": cb,
+           "config": config, "cpu_baseline": cb,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -296,17 +365,11 @@ def fixed_point_bench(a, p, meta, yl, yh, Z64):
 
     for _ in range(a.warmup):
         step()
-    torch.cuda.synchronize()
+    ms = timed_region(step, a.steps, st, None)
     f.set_option(FUSE_OPT_PROFILE, 1)
     f.profile(FUSE_K_LATENT, reset=True)
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(a.steps):
-        step()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    lat_ms, lat_n = f.profile(FUSE_K_LATENT)
+    step()
+    lat_ms, lat_n = f.profile(FUSE_K_LATENT, reset=True)
     f.set_option(FUSE_OPT_PROFILE, 0)
     f.close()
     peaks = _peaks()
@@ -363,7 +426,8 @@ def sb_bench(a, p, meta, yl, yh, f0):
 
 def run_batch(a, rank, world, local_rank):
     """The batched uneven-tile workload: 64 problems of sizes 96..384, one launch per ADMM phase
-    over all of them (FP32, BF16 weights), against per-problem sequential FP64 GPU solves."""
+    over all of them (FP32, BF16 weights), the iteration loop replayed from a CUDA graph; against
+    per-problem sequential FP64 GPU solves of the same problems."""
     import torch
     torch.cuda.set_device(local_rank)
     from paper_2210_04184_gb300 import build as _build, synth
@@ -374,8 +438,7 @@ def run_batch(a, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    nprob = 64
-    ps = synth.batch_workload(nprob, seed=synth.SEED_BASE + 4 + 7919 * rank)
+    ps = synth.batch_workload(a.problems, seed=synth.SEED_BASE + 4 + 7919 * rank)
     iters = a.iters or ps[0].iters
     for p in ps:
         p.iters = iters
@@ -386,36 +449,26 @@ def run_batch(a, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     for f, h in zip(fs, yh):
         fuse_weights(f.ctx, h.data_ptr())
-    batch.autotune(yl, yh, iters=1)                # launch shapes only; results are unchanged
+    if not a.no_autotune:
+        batch.autotune(yl, yh, iters=1)            # launch shapes only; results are unchanged
+    Zs = None
 
     def step():
+        nonlocal Zs
         for f, h in zip(fs, yh):
             fuse_weights(f.ctx, h.data_ptr())
-        return batch.solve(yl, yh, iters, want_X=False, want_Z=True)
+        _, Zs = batch.solve(yl, yh, iters, want_X=False, want_Z=True)
 
     for _ in range(a.warmup):
         step()
     batch.sync()
-    batch.set_option(FUSE_OPT_PROFILE, 1)
-    batch.profile(FUSE_K_LATENT, reset=True)
+    # the timed region runs what a caller runs: graphs on, no per-launch events
+    batch.profile(FUSE_K_ALL, reset=True)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        _, Zs = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = timed_region(step, a.steps, stream, dist)
     clk = clocks.stop()
-    lat_ms, lat_n = batch.profile(FUSE_K_LATENT)
-    _, launches = batch.profile(FUSE_K_ALL)
-    batch.set_option(FUSE_OPT_PROFILE, 0)
+    _, launches = batch.profile(FUSE_K_ALL, reset=True)
     batch.sync()
     ms = max_over_ranks(ms, dist)
     px = sum(p.H * p.W for p in ps)
@@ -423,22 +476,27 @@ def run_batch(a, rank, world, local_rank):
     units = px / 1e6 * Ls * iters * a.steps * world
     value = job_value(units / world, world, ms / 1e3)
 
-    # end to end: pinned host inputs copied in, Z of every problem read back, each step
+    # the latent pass's average launch duration from a separate profiled pass of one step
+    # (direct launches with CUDA events on the launching stream around every latent launch)
+    batch.set_option(FUSE_OPT_PROFILE, 1)
+    batch.profile(FUSE_K_LATENT, reset=True)
+    step()
+    lat_ms, lat_n = batch.profile(FUSE_K_LATENT, reset=True)
+    batch.set_option(FUSE_OPT_PROFILE, 0)
+    batch.sync()
+
+    # end to end through the host-buffer batch entry point: pinned inputs copied in, weights,
+    # batched solve, Z of every problem read back, every step
     e2e = None
     if not a.no_e2e:
         hyl = [torch.from_numpy(np.ascontiguousarray(p.Yl, dtype=np.float32)).pin_memory() for p in ps]
         hyh = [torch.from_numpy(np.ascontiguousarray(p.Yh, dtype=np.float32)).pin_memory() for p in ps]
+        from paper_2210_04184_gb300.fuse import fuse_batch_run_host
         hz = [torch.empty((p.L_l, p.H, p.W), dtype=torch.float32).pin_memory() for p in ps]
+        lp, hp, zp = [h.data_ptr() for h in hyl], [h.data_ptr() for h in hyh], [z.data_ptr() for z in hz]
 
         def e2e_step():
-            dl = [h.to("cuda", non_blocking=True) for h in hyl]
-            dh = [h.to("cuda", non_blocking=True) for h in hyh]
-            for f, h in zip(fs, dh):
-                fuse_weights(f.ctx, h.data_ptr())
-            _, Zs2 = batch.solve(dl, dh, iters, want_X=False, want_Z=True)
-            for z, hzz in zip(Zs2, hz):
-                hzz.copy_(z, non_blocking=True)
-            torch.cuda.synchronize()
+            fuse_batch_run_host(batch.b, lp, hp, None, iters, None, zp)
 
         e2e_step()
         if dist:
@@ -447,11 +505,12 @@ def run_batch(a, rank, world, local_rank):
         for _ in range(a.steps):
             e2e_step()
         dt = max_over_ranks(time.perf_counter() - t0, dist)
-        e2e = {"value": units / dt, "unit": UNIT,
+        zmax = max(float(np.abs(np.asarray(z)).max()) for z in hz)
+        e2e = {"value": units / dt, "unit": UNIT, "entry_point": "fuse_batch_run_host",
                "h2d_bytes_per_step": sum(h.numel() * 4 for h in hyl) + sum(h.numel() * 4 for h in hyh),
-               "d2h_bytes_per_step": sum(h.numel() * 4 for h in hz)}
+               "d2h_bytes_per_step": sum(h.numel() * 4 for h in hz), "outputs_finite": bool(np.isfinite(zmax))}
 
-    # per-problem sequential FP64 GPU solves of the same problems
+    # per-problem sequential FP64 GPU solves of the same problems (the plain FP64 form)
     seq = None
     if not a.no_fp64 and rank == 0:
         t64 = 0.0
@@ -461,7 +520,7 @@ def run_batch(a, rank, world, local_rank):
             a64 = torch.tensor(p.Yl, dtype=torch.float64, device="cuda")
             b64 = torch.tensor(p.Yh, dtype=torch.float64, device="cuda")
             f64.weights(b64)
-            f64.solve(a64, b64, 2, want_X=False)          # graph capture outside the timing
+            f64.solve(a64, b64, iters, want_X=False)      # graph capture outside the timing
             torch.cuda.synchronize()
             s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
             s0.record(stream)
@@ -482,29 +541,34 @@ def run_batch(a, rank, world, local_rank):
             dist.destroy_process_group()
         return
     peaks = _peaks()
-    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
     per_launch_ms = lat_ms / max(lat_n, 1)
     lb = sum(latent_bytes(p, 4, 2) for p in ps)
     achieved = lb / (per_launch_ms / 1e3) / 1e9
-    sizes = sorted(set(p.H for p in ps))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batch64", "problems": nprob, "sizes": sizes, "pixels": px, "bands": 31,
-                   "L_h": 3, "L_s": Ls, "ratio": 4, "patch": "3x3", "search": "7x7", "iters": iters,
-                   "weights": "bf16", "global_batch": nprob * world,
-                   "parallelism": f"batched problems, independent batches x{world}",
-                   "l2": "latent state exceeds L2 (no flush needed)",
-                   "latent_state": "half window (one offset of each +-tau pair)"},
+        "config": batch_config(ps, iters, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "latent_tma_batch_kernel", "algorithmic_bytes_per_launch": lb,
-                     "avg_launch_ms": per_launch_ms, "launches": lat_n,
-                     "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"},
+                     "traffic": latent_traffic("batch", px), "kernel": "latent_tma_batch_kernel",
+                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms, "launches": lat_n,
+                     "timing": "CUDA events around each latent launch in a separate profiled step",
+                     "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS},
         "gpu_launches": launches, "clocks": clk, "e2e": e2e, "fp64_sequential": seq,
     }
-    print(json.dumps(out), flush=True)
     batch.close()
+    for f in fs:
+        f.close()
+    del yl, yh, Zs
+    torch.cuda.empty_cache()
+    if not a.no_secondary and world == 1:
+        out["hsms_256"] = single_problem(a, "hsms_256", 0, None)
+    if not a.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(ps[0])
+    print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -584,22 +648,20 @@ def grad_bench(a, rank):
     return out
 
 
-def run_ours(a, rank, world, local_rank):
+def single_problem(a, name, rank, dist, keep=False):
+    """One problem of workload `name`: the timed product path (weights, the whole iteration loop
+    replayed from a CUDA graph, Z), a separate profiled step for the latent pass's launch
+    duration, and the end-to-end host-buffer call.  Returns the measurement (and with keep=True
+    also the context and device inputs for further measurements)."""
     import torch
-    torch.cuda.set_device(local_rank)
-    from paper_2210_04184_gb300 import build as _build
-    from paper_2210_04184_gb300.fuse import Fusion, FUSE_OPT_PROFILE, FUSE_K_ALL, FUSE_K_LATENT
-    _build.build()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    p, meta = _workload(a.workload, rank, a.iters)
+    from paper_2210_04184_gb300.fuse import (Fusion, FUSE_OPT_PROFILE, FUSE_K_ALL, FUSE_K_LATENT, fuse_solve,
+                                             fuse_weights, fuse_set_stream)
+    p, meta = _workload(name, rank, a.iters if keep else None)
     td = torch.float64 if meta["dtype"] == "f64" else torch.float32
     esz = 8 if meta["dtype"] == "f64" else 4
     wsz = {"bf16": 2, "f32": 4, "f64": 8}[meta["wdtype"]]
     f = Fusion.from_problem(p, dtype=meta["dtype"], wdtype=meta["wdtype"])
-    if a.fixed_state:
+    if keep and a.fixed_state:
         from paper_2210_04184_gb300.fuse import FUSE_OPT_STATE_FORMAT
         f.set_option(FUSE_OPT_STATE_FORMAT, 1)
     if "mask" in meta:
@@ -608,8 +670,6 @@ def run_ours(a, rank, world, local_rank):
     yh = torch.tensor(p.Yh, dtype=td, device="cuda")
     Z = torch.empty((p.L_l, p.H, p.W), dtype=td, device="cuda")
     stream = torch.cuda.current_stream()
-
-    from paper_2210_04184_gb300.fuse import fuse_solve, fuse_weights, fuse_set_stream, fuse_conditioning
     fuse_set_stream(f.ctx, stream.cuda_stream)
     fuse_weights(f.ctx, yh.data_ptr())
     if a.no_autotune:
@@ -628,31 +688,27 @@ def run_ours(a, rank, world, local_rank):
 
     for _ in range(a.warmup):
         step()
-    torch.cuda.synchronize()
-    f.set_option(FUSE_OPT_PROFILE, 1)
-    f.profile(FUSE_K_LATENT, reset=True)
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    lat_ms, lat_n = f.profile(FUSE_K_LATENT)
-    _, launches = f.profile(FUSE_K_ALL)
-    f.set_option(FUSE_OPT_PROFILE, 0)
+    f.sync()
+    f.profile(FUSE_K_ALL, reset=True)
+    clocks = ClockSampler(torch.cuda.current_device()) if keep else None
+    if clocks:
+        clocks.start()
+    ms = timed_region(step, a.steps, stream, dist)
+    clk = clocks.stop() if clocks else None
+    _, launches = f.profile(FUSE_K_ALL, reset=True)
+    f.sync()
+    world = dist.get_world_size() if dist else 1
     ms = max_over_ranks(ms, dist)
     units = p.H * p.W / 1e6 * p.L_s * p.iters * a.steps * world
     value = job_value(units / world, world, ms / 1e3)
+
+    # the latent pass's average launch duration from a separate profiled step
+    f.set_option(FUSE_OPT_PROFILE, 1)
+    f.profile(FUSE_K_LATENT, reset=True)
+    step()
+    lat_ms, lat_n = f.profile(FUSE_K_LATENT, reset=True)
+    f.set_option(FUSE_OPT_PROFILE, 0)
+    f.sync()
 
     # end to end through the host-buffer entry point (pinned inputs, Z read back each step)
     e2e = None
@@ -662,7 +718,6 @@ def run_ours(a, rank, world, local_rank):
         hyl = torch.from_numpy(np.ascontiguousarray(p.Yl, dtype=nd)).pin_memory()
         hyh = torch.from_numpy(np.ascontiguousarray(p.Yh, dtype=nd)).pin_memory()
         hz = torch.empty((p.L_l, p.H, p.W), dtype=td).pin_memory()
-        f.set_option(FUSE_OPT_PROFILE, 0)
         for _ in range(max(1, a.warmup)):
             fuse_run_host(f.ctx, hyl.data_ptr(), hyh.data_ptr(), None, p.iters, None, hz.data_ptr())
         if dist:
@@ -670,11 +725,47 @@ def run_ours(a, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(a.steps):
             fuse_run_host(f.ctx, hyl.data_ptr(), hyh.data_ptr(), None, p.iters, None, hz.data_ptr())
-        dt = time.perf_counter() - t0
-        dt = max_over_ranks(dt, dist)
-        e2e = {"value": units / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": units / dt, "unit": UNIT, "entry_point": "fuse_run_host",
                "h2d_bytes_per_step": hyl.numel() * hyl.element_size() + hyh.numel() * hyh.element_size(),
                "d2h_bytes_per_step": hz.numel() * hz.element_size()}
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    per_launch_ms = lat_ms / max(lat_n, 1)
+    fixed = keep and a.fixed_state
+    lb = latent_bytes(p, esz, wsz, ssz=2 if fixed else None)
+    traffic = None
+    if name.startswith("hsms") and meta["wdtype"] == "bf16" and not fixed:
+        traffic = latent_traffic("hsms", p.H * p.W)
+    achieved = lb / (per_launch_ms / 1e3) / 1e9
+    res = {"workload": name, "value": value, "unit": UNIT, "ms_per_step": ms / a.steps, "steps": a.steps,
+           "dtype": meta["dtype"], "config": dict(_config(p, meta, name, world), launch_shapes=tuned),
+           "iters_per_s": p.iters * a.steps * world / (ms / 1e3),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm, "traffic": traffic, "kernel": "latent_tma_kernel",
+                        "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms, "launches": lat_n,
+                        "timing": "CUDA events around each latent launch in a separate profiled step",
+                        "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS},
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e}
+    if keep:
+        return res, (f, p, meta, yl, yh, Z)
+    f.close()
+    return res
+
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2210_04184_gb300 import build as _build
+    from paper_2210_04184_gb300.fuse import fuse_conditioning
+    _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res, (f, p, meta, yl, yh, Z) = single_problem(a, a.workload, rank, dist, keep=True)
 
     fp64 = None
     Z64 = None
@@ -694,31 +785,12 @@ def run_ours(a, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return
-    peaks = _peaks()
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    per_launch_ms = lat_ms / max(lat_n, 1)
-    traffic = None
-    if a.workload.startswith("hsms") and meta["wdtype"] == "bf16" and "hsms" in LATENT_TRAFFIC_PER_PIXEL:
-        traffic = LATENT_TRAFFIC_PER_PIXEL["hsms"] * p.H * p.W
-    lb = latent_bytes(p, esz, wsz, ssz=2 if a.fixed_state else None)
-    if a.fixed_state:
-        traffic = None
-    achieved = lb / (per_launch_ms / 1e3) / 1e9
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": meta["dtype"], "data": "synthetic",
-        "config": dict(_config(p, meta, a.workload, world), launch_shapes=tuned),
-        "iters_per_s": p.iters * a.steps * world / (ms / 1e3),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "kernel": "latent_tma_kernel",
-                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms,
-                     "launches": lat_n, "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS},
-        "gpu_launches": launches,
-        "clocks": clk,
-        "e2e": e2e,
+        "config": res["config"], "iters_per_s": res["iters_per_s"], "roofline": res["roofline"],
+        "gpu_launches": res["gpu_launches"], "clocks": res["clocks"], "e2e": res["e2e"],
         "fp64_compare": fp64,
         "conditioning": dict(zip(("A_x_update", "EEt_plus_rho", "F_inverse"), fuse_conditioning(f.ctx))),
         "fixed_point_state": fixed,

@@ -69,8 +69,13 @@ typedef struct fuse_ctx fuse_ctx;
 
 /* Options for fuse_set_option. */
 enum {
-    FUSE_OPT_PROFILE = 1,        /* 1: time every latent-pass launch with CUDA events (no graph) */
-    FUSE_OPT_GRAPH = 2,          /* 1 (default): replay iterations from a captured CUDA graph */
+    FUSE_OPT_PROFILE = 1,        /* 1: time every latent-pass launch with CUDA events (direct
+                                    launches, no graph) */
+    FUSE_OPT_GRAPH = 2,          /* 1 (default): the whole iteration loop of a solve is one
+                                    captured CUDA graph (up to 256 iterations per graph; longer
+                                    solves replay it and one graph for the remainder), captured
+                                    on first use and kept while the launch configuration holds;
+                                    0: direct launches */
     FUSE_OPT_LATENT_IMPL = 3,    /* latent pass: 1 (default) bulk-copy ring, 0 register-staged loads */
     FUSE_OPT_LATENT_THREADS = 4, /* consumer threads per latent block, 32..256 (default 128;
                                     256 in batches) */
@@ -183,7 +188,9 @@ fuse_status fuse_solve(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, in
 /* End-to-end call on HOST buffers: copies Y_l, Y_h (and the guide; NULL = use Y_h) to the
  * device, computes the weights, runs fuse_solve from a zero start and copies X and/or Z back
  * (each nullable).  Synchronous: returns after the results are in host memory.  Device
- * staging buffers are allocated on first use and kept by the context. */
+ * staging buffers are allocated on first use and kept by the context.  Sizes and types as in
+ * fuse_solve; guide_host [L_guide][H][W].  Errors: as fuse_weights and fuse_solve, and
+ * FUSE_EINVAL when the guide is NULL but L_guide != L_h. */
 fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_host,
                           const void* guide_host, int iters, void* X_host, void* Z_host);
 
@@ -341,7 +348,8 @@ fuse_status fuse_selftest(fuse_ctx* ctx, int which);
 /* ---- Batches of independent problems (uneven sizes) ------------------------------------
  * A batch runs the ADMM of several contexts together: each iteration is one launch per
  * phase (right-hand side, three FFT passes, B X, pixel updates, latent pass) over the work of
- * every problem, replayed from one captured CUDA graph.  The contexts must share dtype,
+ * every problem, and the whole iteration loop is replayed from captured CUDA graphs as in
+ * FUSE_OPT_GRAPH.  The contexts must share dtype,
  * wdtype, K, S, L_s (<= 32), blur size and half-window mode; sizes (H, W, ratio, L_l, L_h) may
  * differ.  The batch does not own the contexts: destroy the batch before them.  Creating a
  * batch moves every context onto the batch's stream. */
@@ -357,6 +365,21 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
  * fuse_set_weights).  Asynchronous on the batch's stream. */
 fuse_status fuse_batch_solve(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters,
                              void* const* X_out, void* const* Z_out);
+
+/* End-to-end batch call on HOST buffers (the batch counterpart of fuse_run_host): for every
+ * problem i, copies Yl_host[i] [L_l][H/ratio][W/ratio] and Yh_host[i] [L_h][H][W] (and
+ * guide_host[i] [L_guide][H][W] when guide_host and guide_host[i] are non-NULL; otherwise the
+ * guide is Y_h) to device staging buffers, computes problem i's weights (eq. wts), solves all
+ * problems together from a zero start for `iters` iterations (fuse_batch_solve) and copies
+ * X_host[i] [L_s][H][W] and/or Z_host[i] [L_l][H][W] back (X_host, Z_host and their entries
+ * nullable).  Element type of every buffer: the contexts' dtype; host buffers should be pinned
+ * for asynchronous copies.  The staging buffers are allocated on first use and kept by each
+ * context.  Synchronous: returns after the results are in host memory and the device-side
+ * checks of fuse_batch_sync.  Errors: FUSE_EINVAL (NULL inputs, guide NULL with
+ * L_guide != L_h, iters < 0), FUSE_ESTATE, FUSE_ENOMEM, FUSE_ECUDA, FUSE_ETIMEOUT. */
+fuse_status fuse_batch_run_host(fuse_batch* b, const void* const* Yl_host, const void* const* Yh_host,
+                                const void* const* guide_host, int iters, void* const* X_host,
+                                void* const* Z_host);
 
 /* FUSE_OPT_PROFILE, FUSE_OPT_GRAPH, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES,
  * FUSE_OPT_LATENT_BANDS. */

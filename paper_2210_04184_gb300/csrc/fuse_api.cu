@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dispatch.cuh"
 #include "k_fft.cuh"
 #include "k_grad.cuh"
 #include "k_latent.cuh"
@@ -20,14 +21,59 @@
 #include "k_pixel.cuh"
 #include "k_stencil.cuh"
 #include "k_weights.cuh"
+#include "launch.cuh"
 
 using namespace fuse;
+
+namespace fuse {
+
+// Self-check of the bounded-wait machinery: waits on a barrier that nothing ever completes.
+// The wait must give up after `limit` polls and set bit `code` in *err.
+__global__ void wait_selftest_kernel(int* err, unsigned limit, int code) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0u, limit, err, code);
+}
+
+}  // namespace fuse
 
 namespace {
 
 constexpr int kMaxSmem = 200 * 1024;
 
 struct Event2 { cudaEvent_t a, b; };
+
+// Iterations captured in one CUDA graph: a solve of up to this many iterations replays one graph;
+// longer solves replay full graphs and one for the remainder.
+constexpr int kGraphIters = 256;
+
+// A captured loop of `len` iterations; `cold` marks a loop whose first latent pass reads no state
+// (it starts a solve from zero).  Two are cached per context or batch (the full loop and the
+// remainder of a long solve), the least recently used one is replaced.
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    int len = 0, cold = 0;
+    long long launches = 0;
+    unsigned long long used = 0;
+};
+
+struct LoopCache {
+    LoopGraph g[2];
+    unsigned long long tick = 0;
+    LoopGraph* find(int len, int cold) {
+        for (LoopGraph& x : g)
+            if (x.exec && x.len == len && x.cold == cold) { x.used = ++tick; return &x; }
+        return nullptr;
+    }
+    LoopGraph* victim() { return g[0].used <= g[1].used ? &g[0] : &g[1]; }
+    void clear() {
+        for (LoopGraph& x : g) {
+            if (x.exec) cudaGraphExecDestroy(x.exec);
+            x = LoopGraph{};
+        }
+    }
+};
 
 }  // namespace
 
@@ -76,8 +122,7 @@ struct fuse_ctx {
     size_t ev_used = 0;
     double latent_ms = 0.0;
     long long launches_all = 0, launches_latent = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    LoopCache loops;
     int fault_alloc = -1, alloc_count = 0;
     // latent pass variant: 0 = register-staged loads, 1 = bulk-copy (TMA) ring
     int lat_impl = 1, lat_target = 128, lat_stages = 6, lat_bpb = 1;
@@ -121,6 +166,8 @@ struct fuse_ctx {
 namespace {
 inline void* lat_src(const fuse_ctx* c) { return c->lat_in ? c->lat_in : c->Sig; }
 inline void* lat_dst(const fuse_ctx* c) { return c->lat_out ? c->lat_out : c->Sig; }
+// The captured iteration loops depend on the launch configuration: dropped whenever it changes.
+inline void drop_graphs(fuse_ctx* c) { c->loops.clear(); }
 }  // namespace
 
 namespace {
@@ -373,48 +420,6 @@ bool latent_tma_shape(fuse_ctx* c) {
 // typed launch sequence
 // ---------------------------------------------------------------------------------------
 
-// Compile-time dispatch helpers: call f(std::integral_constant<int, V>{}) for a runtime value.
-template <typename F>
-void with_bh(int bh, F&& f) {
-    switch (bh) {
-        case 1: f(std::integral_constant<int, 1>{}); break;
-        case 3: f(std::integral_constant<int, 3>{}); break;
-        case 5: f(std::integral_constant<int, 5>{}); break;
-        case 7: f(std::integral_constant<int, 7>{}); break;
-        case 9: f(std::integral_constant<int, 9>{}); break;
-        case 11: f(std::integral_constant<int, 11>{}); break;
-        case 13: f(std::integral_constant<int, 13>{}); break;
-        default: f(std::integral_constant<int, 15>{}); break;
-    }
-}
-
-template <typename F>
-void with_k(int K, F&& f) {
-    switch (K) {
-        case 0: f(std::integral_constant<int, 0>{}); break;
-        case 1: f(std::integral_constant<int, 1>{}); break;
-        case 2: f(std::integral_constant<int, 2>{}); break;
-        default: f(std::integral_constant<int, 3>{}); break;
-    }
-}
-
-// MAXLS bucket of the register-resident pixel kernel (0 = wide kernel).
-inline int pixel_bucket(int Ls) {
-    return Ls <= 4 ? 4 : Ls <= 8 ? 8 : Ls <= 16 ? 16 : Ls <= 20 ? 20 : Ls <= 32 ? 32 : 0;
-}
-
-template <typename F>
-void with_maxls(int Ls, F&& f) {
-    switch (pixel_bucket(Ls)) {
-        case 4: f(std::integral_constant<int, 4>{}); break;
-        case 8: f(std::integral_constant<int, 8>{}); break;
-        case 16: f(std::integral_constant<int, 16>{}); break;
-        case 20: f(std::integral_constant<int, 20>{}); break;
-        case 32: f(std::integral_constant<int, 32>{}); break;
-        default: f(std::integral_constant<int, 0>{}); break;
-    }
-}
-
 template <typename T>
 struct Impl {
     static constexpr int VEC = 16 / sizeof(T);
@@ -435,11 +440,11 @@ struct Impl {
                             c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask, c->xmode == 1 ? 1 : 0};
     }
     template <typename WT>
-    static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb) {
+    static LatentArgs<T, WT> lat_args(fuse_ctx* c, int Ty, int ncons, int D, int bpb, int zero_in = 0) {
         return LatentArgs<T, WT>{(const T*)c->X, (const WT*)c->omega, (const T*)lat_src(c), (T*)lat_dst(c),
                                  (T*)c->planes, c->H, c->W,
                                  c->Ls, c->S, Ty, ncons, D, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit,
-                                 c->half, bpb};
+                                 c->half, bpb, zero_in};
     }
 
     static fuse_status set_attrs(fuse_ctx* c) {
@@ -450,16 +455,7 @@ struct Impl {
         CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_cols_alias_kernel<T>, A, kMaxSmem));
-        CK(c, cudaFuncSetAttribute(pixel_kernel_wide<T>, A, kMaxSmem));
-        cudaError_t e = cudaSuccess;
-        with_bh(c->bh, [&](auto bh) {
-            constexpr int BH = decltype(bh)::value;
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 0, BH>, A, kMaxSmem);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 1, BH>, A, kMaxSmem);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 0, BH>, A, kMaxSmem);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 1, BH>, A, kMaxSmem);
-        });
-        CK(c, e);
+        CK(c, pixel_stencil_set_smem<T>(c->bh, kMaxSmem));
         CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, A, kMaxSmem));
         return FUSE_OK;
     }
@@ -468,17 +464,7 @@ struct Impl {
     static fuse_status set_attrs_w(fuse_ctx* c) {
         const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
         CK(c, cudaFuncSetAttribute(weights_kernel<T, WT>, A, kMaxSmem));
-        cudaError_t e = cudaSuccess;
-        with_k(c->K, [&](auto k) {
-            constexpr int K = decltype(k)::value;
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_kernel<T, WT, K, VEC>, A, kMaxSmem);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, K, TVEC>, A, kMaxSmem);
-            if constexpr (sizeof(T) == 4) {
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, K, TVEC, int16_t>, A, kMaxSmem);
-            }
-        });
-        CK(c, e);
+        CK(c, (latent_set_smem<T, WT>(c->K, kMaxSmem)));
         return FUSE_OK;
     }
 
@@ -487,19 +473,9 @@ struct Impl {
     template <int MODE>
     static void stencil_launch(fuse_ctx* c, cudaStream_t s, const StencilArgs<T>& a) {
         dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-        if (c->bh == c->bw) {
-            const std::vector<double>& ht = a.taps == (const T*)c->tapsB ? c->htapsB : c->htapsT;
-            with_bh(c->bh, [&](auto bh) {
-                constexpr int B = decltype(bh)::value;
-                SquareTaps<T, B> tp;
-                for (int i = 0; i < B * B; ++i) tp.t[i] = (T)ht[i];
-                stencil_sq_kernel<T, MODE, B><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a, tp);
-            });
-            return;
-        }
-        with_bh(c->bh, [&](auto bh) {
-            stencil_kernel<T, MODE, decltype(bh)::value><<<grid, dim3(ST_TX, ST_BY), c->st_smem, s>>>(a);
-        });
+        const double* ht = nullptr;
+        if (c->bh == c->bw) ht = a.taps == (const T*)c->tapsB ? c->htapsB.data() : c->htapsT.data();
+        fuse::stencil_launch<T, MODE>(a, c->bh, ht, grid, c->st_smem, s);
     }
 
     // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
@@ -510,12 +486,7 @@ struct Impl {
 
     static void pixel(fuse_ctx* c, cudaStream_t s) {
         const unsigned pblocks = (unsigned)((c->n + c->px_threads - 1) / c->px_threads);
-        const PixelArgs<T> a = px_args(c);
-        with_maxls(c->Ls, [&](auto m) {
-            constexpr int M = decltype(m)::value;
-            if constexpr (M == 0) pixel_kernel_wide<T><<<pblocks, c->px_threads, c->px_smem, s>>>(a);
-            else pixel_kernel<T, M><<<pblocks, c->px_threads, c->px_smem, s>>>(a);
-        });
+        pixel_launch<T>(px_args(c), pblocks, (unsigned)c->px_threads, c->px_smem, s);
     }
 
     static fuse_status band_mix(fuse_ctx* c, cudaStream_t s, const void* in, void* out, const void* M, size_t npix,
@@ -539,39 +510,30 @@ struct Impl {
         return FUSE_OK;
     }
 
+    // zero_in: the state entering this pass is zero (the first iteration of a cold solve); the
+    // bulk-copy pass then reads none of it.  The register-staged pass always reads it.
     template <typename WT>
-    static void latent(fuse_ctx* c, cudaStream_t s) {
+    static void latent(fuse_ctx* c, cudaStream_t s, bool zero_in) {
         const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
         if (c->lat_impl == 1) {
             dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)((c->Ls + c->lat_bpb - 1) / c->lat_bpb),
                       rowsW);
-            const LatentArgs<T, WT> a = lat_args<WT>(c, c->lt_Ty, c->lt_ncons, c->lat_stages, c->lat_bpb);
-            with_k(c->K, [&](auto k) {
-                constexpr int K = decltype(k)::value;
-                if constexpr (sizeof(T) == 4) {
-                    if (c->sfmt == 1) {
-                        latent_tma_kernel<T, WT, K, TVEC, int16_t><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
-                        return;
-                    }
-                }
-                latent_tma_kernel<T, WT, K, TVEC><<<grid, c->lt_ncons + 32, c->lt_smem, s>>>(a);
-            });
+            const LatentArgs<T, WT> a = lat_args<WT>(c, c->lt_Ty, c->lt_ncons, c->lat_stages, c->lat_bpb, zero_in);
+            latent_tma_launch<T, WT>(a, c->K, c->sfmt == 1, grid, (unsigned)(c->lt_ncons + 32), c->lt_smem, s);
             return;
         }
         dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
-        with_k(c->K, [&](auto k) {
-            latent_kernel<T, WT, decltype(k)::value, VEC><<<grid, c->lat_threads, c->lat_smem, s>>>(
-                (const T*)c->X, (const WT*)c->omega, (const T*)lat_src(c), (T*)lat_dst(c), (T*)c->planes, c->H, c->W, c->Ls, c->S,
-                c->lat_Ty, (T)(c->lam2 / c->rho), c->half);
-        });
+        latent_reg_launch<T, WT>((const T*)c->X, (const WT*)c->omega, (const T*)lat_src(c), (T*)lat_dst(c),
+                                 (T*)c->planes, c->H, c->W, c->Ls, c->S, c->lat_Ty, (T)(c->lam2 / c->rho), c->half,
+                                 c->K, grid, (unsigned)c->lat_threads, c->lat_smem, s);
     }
 
-    static void latent_any(fuse_ctx* c, cudaStream_t s);
+    static void latent_any(fuse_ctx* c, cudaStream_t s, bool zero_in);
 
     // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.  With xmode 1 (S B
     // kept in the X system): C = G + U2 + R with the fixed data term G in U1, the column pass
-    // solves the alias classes, and there is no B X and no P1.
-    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed) {
+    // solves the alias classes, and there is no B X and no P1.  zero_in: see latent().
+    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed, bool zero_in = false) {
         if (c->xmode == 1) {
             dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
             rhs_sum_kernel<T><<<grid, dim3(ST_TX, ST_BY), 0, s>>>(st_args(c, c->U1, c->C, nullptr));
@@ -613,10 +575,10 @@ struct Impl {
             }
             Event2& e = c->ev[c->ev_used++];
             CK(c, cudaEventRecord(e.a, s));
-            latent_any(c, s);
+            latent_any(c, s, zero_in);
             CK(c, cudaEventRecord(e.b, s));
         } else {
-            latent_any(c, s);
+            latent_any(c, s, zero_in);
         }
         CKL(c, "latent kernel");
         return FUSE_OK;
@@ -637,12 +599,12 @@ struct Impl {
 };
 
 template <typename T>
-void Impl<T>::latent_any(fuse_ctx* c, cudaStream_t s) {
+void Impl<T>::latent_any(fuse_ctx* c, cudaStream_t s, bool zero_in) {
     if constexpr (sizeof(T) == 8) {
-        latent<double>(c, s);
+        latent<double>(c, s, zero_in);
     } else {
-        if (c->wdtype == FUSE_BF16) latent<__nv_bfloat16>(c, s);
-        else latent<float>(c, s);
+        if (c->wdtype == FUSE_BF16) latent<__nv_bfloat16>(c, s, zero_in);
+        else latent<float>(c, s, zero_in);
     }
 }
 
@@ -693,14 +655,16 @@ fuse_status guard(fuse_ctx* c) {
     return FUSE_OK;
 }
 
-fuse_status zero_state(fuse_ctx* c, cudaStream_t s) {
+// Zero ADMM state.  clear_sigma = false leaves the latent state as it is: the caller's next
+// iteration then runs a latent pass that reads none of it (zero_in) and overwrites all of it.
+fuse_status zero_state(fuse_ctx* c, cudaStream_t s, bool clear_sigma = true) {
     const size_t img = c->n * c->Ls * c->esz;
     CK(c, cudaMemsetAsync(c->Lam1, 0, img, s));
     CK(c, cudaMemsetAsync(c->U1, 0, img, s));
     CK(c, cudaMemsetAsync(c->Lam2, 0, img, s));
     CK(c, cudaMemsetAsync(c->U2, 0, img, s));
     CK(c, cudaMemsetAsync(c->X, 0, img, s));
-    CK(c, cudaMemsetAsync(c->Sig, 0, c->sig_bytes, s));
+    if (clear_sigma) CK(c, cudaMemsetAsync(c->Sig, 0, c->sig_bytes, s));
     CK(c, cudaMemsetAsync(c->planes, 0, c->plane_bytes, s));
     return FUSE_OK;
 }
@@ -708,33 +672,59 @@ fuse_status zero_state(fuse_ctx* c, cudaStream_t s) {
 // kernels launched by one iteration (Impl::iterate)
 int iteration_launches(const fuse_ctx* c) { return c->xmode == 1 ? 6 : 7; }
 
-fuse_status run_iterations(fuse_ctx* c, int iters) {
+// Replays `len` iterations from one captured graph (captured on first use; `cold`: the first
+// iteration's latent pass reads no state).
+fuse_status launch_loop(fuse_ctx* c, int len, bool cold) {
+    LoopGraph* lg = c->loops.find(len, cold);
+    if (!lg) {
+        const bool f64 = c->dtype == FUSE_F64;
+        CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        fuse_status st = FUSE_OK;
+        for (int t = 0; t < len && st == FUSE_OK; ++t)
+            st = f64 ? Impl<double>::iterate(c, c->cap_stream, false, cold && t == 0)
+                     : Impl<float>::iterate(c, c->cap_stream, false, cold && t == 0);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture", e);
+        lg = c->loops.victim();
+        if (lg->exec) cudaGraphExecDestroy(lg->exec);
+        *lg = LoopGraph{};
+        e = cudaGraphInstantiate(&lg->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { lg->exec = nullptr; return fail_cuda(c, "cudaGraphInstantiate", e); }
+        lg->len = len;
+        lg->cold = cold;
+        lg->launches = (long long)len * iteration_launches(c);
+        lg->used = ++c->loops.tick;
+    }
+    CK(c, cudaGraphLaunch(lg->exec, c->stream));
+    c->launches_all += lg->launches;
+    c->launches_latent += len;
+    return FUSE_OK;
+}
+
+// Runs `iters` iterations: the whole loop replayed from captured graphs of up to kGraphIters
+// iterations, or launched directly when profiling or with graphs switched off.  cold: the state
+// entering the first iteration is zero and its latent pass reads none of it.
+fuse_status run_iterations(fuse_ctx* c, int iters, bool cold = false) {
     if (iters <= 0) return FUSE_OK;
     const bool f64 = c->dtype == FUSE_F64;
     if (c->profile || !c->use_graph) {
         for (int t = 0; t < iters; ++t) {
-            fuse_status st = f64 ? Impl<double>::iterate(c, c->stream, c->profile)
-                                 : Impl<float>::iterate(c, c->stream, c->profile);
+            fuse_status st = f64 ? Impl<double>::iterate(c, c->stream, c->profile, cold && t == 0)
+                                 : Impl<float>::iterate(c, c->stream, c->profile, cold && t == 0);
             if (st != FUSE_OK) return st;
             c->launches_all += iteration_launches(c);
             c->launches_latent += 1;
         }
         return FUSE_OK;
     }
-    if (!c->gexec) {
-        CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        fuse_status st = f64 ? Impl<double>::iterate(c, c->cap_stream, false) : Impl<float>::iterate(c, c->cap_stream, false);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-        if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
-        if (e != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture", e);
-        c->graph = g;
-        CK(c, cudaGraphInstantiate(&c->gexec, c->graph, 0));
-    }
-    for (int t = 0; t < iters; ++t) {
-        CK(c, cudaGraphLaunch(c->gexec, c->stream));
-        c->launches_all += iteration_launches(c);
-        c->launches_latent += 1;
+    for (int done = 0; done < iters;) {
+        const int len = std::min(iters - done, kGraphIters);
+        fuse_status st = launch_loop(c, len, cold && done == 0);
+        if (st != FUSE_OK) return st;
+        done += len;
     }
     return FUSE_OK;
 }
@@ -750,8 +740,12 @@ fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, i
     st = f64 ? Impl<double>::band_mix(c, c->stream, Yh, c->D9b, c->Mh, c->n, c->Lh, c->Ls)
              : Impl<float>::band_mix(c, c->stream, Yh, c->D9b, c->Mh, c->n, c->Lh, c->Ls);
     if (st != FUSE_OK) return st;
+    // A cold start with at least one iteration leaves the latent state uncleared: the first
+    // latent pass of the bulk-copy kernel takes it as zero and overwrites every entry.
+    bool cold = false;
     if (!warm || !c->have_state) {
-        st = zero_state(c, c->stream);
+        cold = iters > 0 && c->lat_impl == 1;
+        st = zero_state(c, c->stream, !cold);
         if (st != FUSE_OK) return st;
         c->have_state = true;
     }
@@ -760,7 +754,7 @@ fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, i
         st = f64 ? Impl<double>::sb_data_term(c, c->stream) : Impl<float>::sb_data_term(c, c->stream);
         if (st != FUSE_OK) return st;
     }
-    st = run_iterations(c, iters);
+    st = run_iterations(c, iters, cold);
     if (st != FUSE_OK) return st;
     c->have_x = true;
     const size_t img = c->n * c->Ls * c->esz;
@@ -802,16 +796,14 @@ fuse_status realloc_state(fuse_ctx* c, int h, int f) {
     ++c->epoch;
     c->have_state = false;
     c->have_x = false;
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    drop_graphs(c);
     return FUSE_OK;
 }
 
 void release(fuse_ctx* c) {
     grad_free(c->gw);
     c->gw = nullptr;
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    drop_graphs(c);
     for (auto& e : c->ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (void* p : c->allocs)
         if (p) cudaFree(p);
@@ -927,8 +919,7 @@ struct fuse_batch {
     void* d_px = nullptr; Segment* d_px_seg = nullptr; int px_nseg = 0, px_blocks = 0;
     std::vector<void*> allocs;
     bool profile = false, use_graph = true;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    LoopCache loops;
     std::vector<Event2> ev;
     size_t ev_used = 0;
     double latent_ms = 0.0;
@@ -1078,47 +1069,26 @@ struct BatchImpl {
 
         // attributes
         const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = cudaSuccess;
-        with_k(b->K, [&](auto k) {
-            e = cudaFuncSetAttribute(latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC>, A, kMaxSmem);
-            if constexpr (sizeof(T) == 4) {
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(latent_tma_batch_kernel<T, WT, decltype(k)::value, VEC, int16_t>, A,
-                                             kMaxSmem);
-            }
-        });
-        BCK(b, e);
-        with_bh(b->bh, [&](auto bh) {
-            constexpr int BH = decltype(bh)::value;
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 0, BH>, A, kMaxSmem);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 1, BH>, A, kMaxSmem);
-        });
-        BCK(b, e);
+        BCK(b, (latent_batch_set_smem<T, WT>(b->K, kMaxSmem)));
+        BCK(b, stencil_batch_set_smem<T>(b->bh, kMaxSmem));
         BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 0>, A, kMaxSmem));
         BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 1>, A, kMaxSmem));
         BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 2>, A, kMaxSmem));
         return FUSE_OK;
     }
 
-    // One batched ADMM iteration: 7 launches cover every problem.
-    static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed) {
-        with_bh(b->bh, [&](auto bh) {
-            stencil_batch_kernel<T, 1, decltype(bh)::value><<<b->st_blocks, dim3(ST_TX, ST_BY), b->st_smem, s>>>(
-                (const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg);
-        });
+    // One batched ADMM iteration: 7 launches cover every problem.  zero_in: the latent state of
+    // every problem is zero on entry (first iteration of the solve) and is not read.
+    static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false) {
+        stencil_batch_launch<T, 1>((const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg, b->bh,
+                                   (unsigned)b->st_blocks, b->st_smem, s);
         fft_batch_kernel<T, 0><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
         fft_batch_kernel<T, 1><<<b->fc_blocks, 256, b->fc_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fc_seg, b->fc_nseg);
         fft_batch_kernel<T, 2><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
-        with_bh(b->bh, [&](auto bh) {
-            stencil_batch_kernel<T, 0, decltype(bh)::value><<<b->st_blocks, dim3(ST_TX, ST_BY), b->st_smem, s>>>(
-                (const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg);
-        });
-        with_maxls(b->Ls, [&](auto m) {
-            constexpr int M = decltype(m)::value;
-            if constexpr (M != 0)
-                pixel_batch_kernel<T, M><<<b->px_blocks, 128, b->px_smem, s>>>((const PixelArgs<T>*)b->d_px,
-                                                                             b->d_px_seg, b->px_nseg);
-        });
+        stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
+                                   (unsigned)b->st_blocks, b->st_smem, s);
+        pixel_batch_launch<T>((const PixelArgs<T>*)b->d_px, b->d_px_seg, b->px_nseg, b->Ls, (unsigned)b->px_blocks,
+                              b->px_smem, s);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timed) {
             if (b->ev_used == b->ev.size()) {
@@ -1132,18 +1102,9 @@ struct BatchImpl {
             b->ev_used++;
             BCK(b, cudaEventRecord(e0, s));
         }
-        with_k(b->K, [&](auto k) {
-            constexpr int K = decltype(k)::value;
-            if constexpr (sizeof(T) == 4) {
-                if (b->sfmt) {
-                    latent_tma_batch_kernel<T, WT, K, VEC, int16_t><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
-                        (const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg);
-                    return;
-                }
-            }
-            latent_tma_batch_kernel<T, WT, K, VEC><<<b->lat_blocks, b->lat_ncons + 32, b->lat_smem, s>>>(
-                (const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg);
-        });
+        latent_tma_batch_launch<T, WT>((const LatentArgs<T, WT>*)b->d_lat, b->d_lat_seg, b->lat_nseg, zero_in ? 1 : 0,
+                                       b->K, b->sfmt != 0, (unsigned)b->lat_blocks, (unsigned)(b->lat_ncons + 32),
+                                       b->lat_smem, s);
         if (timed) BCK(b, cudaEventRecord(e1, s));
         BCK(b, cudaGetLastError());
         return FUSE_OK;
@@ -1156,48 +1117,66 @@ fuse_status batch_build(fuse_batch* b) {
     return BatchImpl<float, float>::build(b);
 }
 
-fuse_status batch_iterate(fuse_batch* b, cudaStream_t s, bool timed) {
-    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::iterate(b, s, timed);
-    if (b->wdtype == FUSE_BF16) return BatchImpl<float, __nv_bfloat16>::iterate(b, s, timed);
-    return BatchImpl<float, float>::iterate(b, s, timed);
+fuse_status batch_iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false) {
+    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::iterate(b, s, timed, zero_in);
+    if (b->wdtype == FUSE_BF16) return BatchImpl<float, __nv_bfloat16>::iterate(b, s, timed, zero_in);
+    return BatchImpl<float, float>::iterate(b, s, timed, zero_in);
 }
 
 void batch_release(fuse_batch* b) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    b->gexec = nullptr;
-    b->graph = nullptr;
+    b->loops.clear();
     for (auto& e : b->ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     b->ev.clear();
     for (void* p : b->allocs) if (p) cudaFree(p);
     b->allocs.clear();
 }
 
-fuse_status batch_run(fuse_batch* b, int iters) {
+// Batched counterpart of launch_loop: `len` batched iterations replayed from one graph.
+fuse_status batch_launch_loop(fuse_batch* b, int len, bool cold) {
+    LoopGraph* lg = b->loops.find(len, cold);
+    if (!lg) {
+        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        fuse_status st = FUSE_OK;
+        for (int t = 0; t < len && st == FUSE_OK; ++t) st = batch_iterate(b, b->cap_stream, false, cold && t == 0);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
+        BCK(b, e);
+        lg = b->loops.victim();
+        if (lg->exec) cudaGraphExecDestroy(lg->exec);
+        *lg = LoopGraph{};
+        e = cudaGraphInstantiate(&lg->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { lg->exec = nullptr; BCK(b, e); }
+        lg->len = len;
+        lg->cold = cold;
+        lg->launches = 7LL * len;
+        lg->used = ++b->loops.tick;
+    }
+    BCK(b, cudaGraphLaunch(lg->exec, b->stream));
+    b->launches_all += lg->launches;
+    b->launches_latent += len;
+    return FUSE_OK;
+}
+
+// `iters` batched iterations (whole loop in graphs of up to kGraphIters iterations, or direct
+// launches when profiling or with graphs off); cold as in run_iterations.
+fuse_status batch_run(fuse_batch* b, int iters, bool cold = false) {
     if (iters <= 0) return FUSE_OK;
     if (b->profile || !b->use_graph) {
         for (int t = 0; t < iters; ++t) {
-            fuse_status st = batch_iterate(b, b->stream, b->profile);
+            fuse_status st = batch_iterate(b, b->stream, b->profile, cold && t == 0);
             if (st != FUSE_OK) return st;
             b->launches_all += 7;
             b->launches_latent += 1;
         }
         return FUSE_OK;
     }
-    if (!b->gexec) {
-        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        fuse_status st = batch_iterate(b, b->cap_stream, false);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
-        if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
-        BCK(b, e);
-        b->graph = g;
-        BCK(b, cudaGraphInstantiate(&b->gexec, b->graph, 0));
-    }
-    for (int t = 0; t < iters; ++t) {
-        BCK(b, cudaGraphLaunch(b->gexec, b->stream));
-        b->launches_all += 7;
-        b->launches_latent += 1;
+    for (int done = 0; done < iters;) {
+        const int len = std::min(iters - done, kGraphIters);
+        fuse_status st = batch_launch_loop(b, len, cold && done == 0);
+        if (st != FUSE_OK) return st;
+        done += len;
     }
     return FUSE_OK;
 }
@@ -1599,8 +1578,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
         case FUSE_OPT_LATENT_BANDS:
             if (value < 1 || value > 64) return fail(c, FUSE_EINVAL, "bands per latent block must be in [1, 64]");
             c->lat_bpb = (int)value;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         case FUSE_OPT_LATENT_IMPL:
         case FUSE_OPT_LATENT_THREADS:
@@ -1617,8 +1595,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
                 latent_tma_shape(c);
                 return fail(c, FUSE_EINVAL, "latent launch option out of range");
             }
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         }
         case FUSE_OPT_FFT_ROWS: {
@@ -1629,8 +1606,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             c->fr_rpb = rpb;
             c->fr_tpr = 256 / rpb;
             c->fr_smem = 2 * (size_t)rpb * c->W * csz;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         }
         case FUSE_OPT_FFT_COLS: {
@@ -1641,8 +1617,7 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             c->fc_cw = cw;
             c->fc_tpc = 256 / cw;
             c->fc_smem = (size_t)cw * (2 * c->H + 1) * csz;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         }
         case FUSE_OPT_HALF_WINDOW: {
@@ -1681,15 +1656,13 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             ++c->epoch;
             c->have_state = false;
             c->have_x = false;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         }
         case FUSE_OPT_WAIT_LIMIT:
             if (value < 1) return fail(c, FUSE_EINVAL, "wait limit must be positive");
             c->wait_limit = (unsigned)value;
-            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            drop_graphs(c);
             return FUSE_OK;
         default: return fail(c, FUSE_EINVAL, "unknown option");
     }
@@ -1793,8 +1766,7 @@ fuse_status fuse_autotune(fuse_ctx* c, const void* Yl, const void* Yh, int iters
             fuse_set_option(c, FUSE_OPT_FFT_COLS, best_c);
         }
     }
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    drop_graphs(c);
     c->have_state = false;
     c->have_x = false;
     return FUSE_OK;
@@ -1915,11 +1887,12 @@ fuse_status fuse_batch_solve(fuse_batch* b, const void* const* Yl, const void* c
         if (st == FUSE_OK)
             st = f64 ? Impl<double>::band_mix(c, b->stream, Yh[i], c->D9b, c->Mh, c->n, c->Lh, c->Ls)
                      : Impl<float>::band_mix(c, b->stream, Yh[i], c->D9b, c->Mh, c->n, c->Lh, c->Ls);
-        if (st == FUSE_OK) st = zero_state(c, b->stream);
+        // with at least one iteration the first batched latent pass takes the state as zero
+        if (st == FUSE_OK) st = zero_state(c, b->stream, iters == 0);
         if (st != FUSE_OK) return bfail(b, st, "problem " + std::to_string(i) + ": " + c->err);
         c->have_state = true;
     }
-    fuse_status st = batch_run(b, iters);
+    fuse_status st = batch_run(b, iters, iters > 0);
     if (st != FUSE_OK) return st;
     for (int i = 0; i < n; ++i) {
         fuse_ctx* c = b->ctx[i];
@@ -1934,6 +1907,53 @@ fuse_status fuse_batch_solve(fuse_batch* b, const void* const* Yl, const void* c
         }
     }
     return FUSE_OK;
+}
+
+fuse_status fuse_batch_run_host(fuse_batch* b, const void* const* Yl_h, const void* const* Yh_h,
+                                const void* const* G_h, int iters, void* const* X_h, void* const* Z_h) {
+    if (!b || !Yl_h || !Yh_h) return FUSE_EINVAL;
+    if (b->sticky != FUSE_OK) return FUSE_ESTATE;
+    if (iters < 0) return bfail(b, FUSE_EINVAL, "iters must be >= 0");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, FUSE_ECUDA, "cudaSetDevice");
+    const int n = (int)b->ctx.size();
+    std::vector<const void*> yl(n), yh(n);
+    std::vector<void*> xo(n, nullptr), zo(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        fuse_ctx* c = b->ctx[i];
+        if (!Yl_h[i] || !Yh_h[i]) return bfail(b, FUSE_EINVAL, "NULL input of a problem");
+        if (c->sticky != FUSE_OK) return bfail(b, FUSE_ESTATE, "problem " + std::to_string(i) + " holds an error");
+        const void* g = G_h ? G_h[i] : nullptr;
+        if (!g && c->Lg != c->Lh)
+            return bfail(b, FUSE_EINVAL, "problem " + std::to_string(i) + ": guide defaults to Y_h but L_guide != L_h");
+        const size_t bl = (size_t)c->Ll * c->nl * c->esz, bhh = (size_t)c->Lh * c->n * c->esz;
+        const size_t bg = (size_t)c->Lg * c->n * c->esz;
+        const size_t bx = (size_t)c->Ls * c->n * c->esz, bz = (size_t)c->Ll * c->n * c->esz;
+        fuse_status st = FUSE_OK;
+        if (st == FUSE_OK && !c->sYl) st = dalloc(c, &c->sYl, bl);
+        if (st == FUSE_OK && !c->sYh) st = dalloc(c, &c->sYh, bhh);
+        if (st == FUSE_OK && g && !c->sG) st = dalloc(c, &c->sG, bg);
+        if (st == FUSE_OK && X_h && X_h[i] && !c->sX) st = dalloc(c, &c->sX, bx);
+        if (st == FUSE_OK && Z_h && Z_h[i] && !c->sZ) st = dalloc(c, &c->sZ, bz);
+        if (st != FUSE_OK) return bfail(b, st, "problem " + std::to_string(i) + ": " + c->err);
+        BCK(b, cudaMemcpyAsync(c->sYl, Yl_h[i], bl, cudaMemcpyHostToDevice, b->stream));
+        BCK(b, cudaMemcpyAsync(c->sYh, Yh_h[i], bhh, cudaMemcpyHostToDevice, b->stream));
+        if (g) BCK(b, cudaMemcpyAsync(c->sG, g, bg, cudaMemcpyHostToDevice, b->stream));
+        c->stream = b->stream;
+        st = weights_impl(c, g ? c->sG : c->sYh);
+        if (st != FUSE_OK) return bfail(b, st, "problem " + std::to_string(i) + ": " + c->err);
+        yl[i] = c->sYl;
+        yh[i] = c->sYh;
+        if (X_h && X_h[i]) xo[i] = c->sX;
+        if (Z_h && Z_h[i]) zo[i] = c->sZ;
+    }
+    fuse_status st = fuse_batch_solve(b, yl.data(), yh.data(), iters, xo.data(), zo.data());
+    if (st != FUSE_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        fuse_ctx* c = b->ctx[i];
+        if (xo[i]) BCK(b, cudaMemcpyAsync(X_h[i], xo[i], (size_t)c->Ls * c->n * c->esz, cudaMemcpyDeviceToHost, b->stream));
+        if (zo[i]) BCK(b, cudaMemcpyAsync(Z_h[i], zo[i], (size_t)c->Ll * c->n * c->esz, cudaMemcpyDeviceToHost, b->stream));
+    }
+    return fuse_batch_sync(b);
 }
 
 fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value) {
@@ -2082,8 +2102,7 @@ fuse_status fuse_set_mask(fuse_ctx* c, const void* mask) {
         c->mask = c->mask_buf;
     }
     // the pixel launches carry the mask pointer: drop the captured iteration graph
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    drop_graphs(c);
     ++c->epoch;
     return FUSE_OK;
 }

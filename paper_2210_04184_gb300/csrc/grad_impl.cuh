@@ -218,21 +218,13 @@ struct GradImpl {
     static constexpr int VEC = 16 / sizeof(T);
 
     static fuse_status set_attrs(fuse_ctx* c) {
-        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = cudaSuccess;
-        with_k(c->K, [&](auto k) {
-            constexpr int K = decltype(k)::value;
-            if constexpr (sizeof(T) == 8) {
-                e = cudaFuncSetAttribute(latent_bwd_kernel<T, double, K, VEC>, A, kMaxSmem);
-                if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, double, K, VEC>, A, kMaxSmem);
-            } else {
-                e = cudaFuncSetAttribute(latent_bwd_kernel<T, float, K, VEC>, A, kMaxSmem);
-                if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_kernel<T, __nv_bfloat16, K, VEC>, A, kMaxSmem);
-                if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, float, K, VEC>, A, kMaxSmem);
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(latent_bwd_tma_kernel<T, __nv_bfloat16, K, VEC>, A, kMaxSmem);
-            }
-        });
+        cudaError_t e;
+        if constexpr (sizeof(T) == 8) {
+            e = latent_bwd_set_smem<T, double>(c->K, kMaxSmem);
+        } else {
+            e = latent_bwd_set_smem<T, float>(c->K, kMaxSmem);
+            if (e == cudaSuccess) e = latent_bwd_set_smem<T, __nv_bfloat16>(c->K, kMaxSmem);
+        }
         CK(c, e);
         return FUSE_OK;
     }
@@ -275,17 +267,14 @@ struct GradImpl {
                                          (T*)g->planesB, g->lat_part, c->H, c->W, c->Ls, c->S, g->tb_Ty,
                                          g->tb_ncons, g->tb_D, (T)(c->lam2 / c->rho), c->d_err, c->wait_limit,
                                          c->half};
-            with_k(c->K, [&](auto k) {
-                latent_bwd_tma_kernel<T, WT, decltype(k)::value, VEC><<<grid, g->tb_ncons + 32, g->tb_smem, s>>>(a);
-            });
+            latent_bwd_tma_launch<T, WT>(a, c->K, grid, (unsigned)(g->tb_ncons + 32), g->tb_smem, s);
             return;
         }
         dim3 grid((unsigned)((c->H + c->lat_Ty - 1) / c->lat_Ty), (unsigned)c->Ls, rowsW);
-        with_k(c->K, [&](auto k) {
-            latent_bwd_kernel<T, WT, decltype(k)::value, VEC><<<grid, (c->lat_threads + 31) / 32 * 32, c->lat_smem, s>>>(
-                (const T*)Xt, (const WT*)c->omega, (const T*)Sin, (T*)g->Sb, (const T*)g->Cb, (T*)g->planesB,
-                g->lat_part, c->H, c->W, c->Ls, c->S, c->lat_Ty, (T)(c->lam2 / c->rho), c->half);
-        });
+        latent_bwd_reg_launch<T, WT>((const T*)Xt, (const WT*)c->omega, (const T*)Sin, (T*)g->Sb, (const T*)g->Cb,
+                                     (T*)g->planesB, g->lat_part, c->H, c->W, c->Ls, c->S, c->lat_Ty,
+                                     (T)(c->lam2 / c->rho), c->half, c->K, grid,
+                                     (unsigned)((c->lat_threads + 31) / 32 * 32), c->lat_smem, s);
     }
 
     template <typename WT>
@@ -295,11 +284,8 @@ struct GradImpl {
         dim3 grid((unsigned)((c->n + 255) / 256), kept);
         const T coef = (T)(c->lam2 / c->rho);
         const T scale = (T)((c->half ? 2.0 : 1.0) * c->lam2 / c->rho);
-        with_k(c->K, [&](auto k) {
-            omega_bwd_kernel<T, WT, decltype(k)::value><<<grid, 256, 0, s>>>(
-                (const T*)Xt, (const WT*)c->omega, (const T*)Sin, (const T*)g->Sb, (const T*)g->Cb, (T*)g->omb,
-                c->H, c->W, c->Ls, c->S, coef, scale, c->half);
-        });
+        omega_bwd_launch<T, WT>((const T*)Xt, (const WT*)c->omega, (const T*)Sin, (const T*)g->Sb, (const T*)g->Cb,
+                                (T*)g->omb, c->H, c->W, c->Ls, c->S, coef, scale, c->half, c->K, grid, s);
     }
 
     static fuse_status omega_bwd_any(fuse_ctx* c, cudaStream_t s, const void* Xt, const void* Sin) {
@@ -334,10 +320,7 @@ struct GradImpl {
                                 (const T*)c->F, (const T*)g->Krho, (const T*)g->Klam, (const T*)g->Kmu,
                                 g->px_part, c->H, c->W, c->Ls, c->d, (T)c->rho, (const uint8_t*)c->mask};
         const unsigned blocks = (unsigned)((c->n + 127) / 128);
-        with_maxls(c->Ls, [&](auto m) {
-            constexpr int M = decltype(m)::value;
-            if constexpr (M > 0) pixel_bwd_kernel<T, M><<<blocks, 128, 0, s>>>(a);
-        });
+        pixel_bwd_launch<T>(a, blocks, s);
         c->launches_all++;
         CKL(c, "pixel_bwd_kernel");
         return FUSE_OK;

@@ -160,6 +160,8 @@ struct LatentArgs {
     unsigned limit;
     int half;
     int bpb;            // bands per block: the ring keeps streaming across them
+    int zero_in;        // 1: the entering state is zero (first iteration of a cold solve): nothing
+                        // is read, the pass only writes the new state and the adjoint sums
 };
 
 __device__ __forceinline__ void consumer_barrier(int ncons) {
@@ -206,6 +208,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int per_band = nt2 * NP;
     const int nq = nb * per_band;
     const unsigned bytes = (unsigned)(rows * W * (int)sizeof(ST));
+    const bool zin = args.zero_in != 0;
 
     if (tid == 0) {
         for (int s = 0; s < D; ++s) {
@@ -219,7 +222,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
 
     if (tid >= ncons) {
         // ---------------- producer warp: one lane issues the bulk copies ----------------
-        if (tid == ncons) {
+        if (tid == ncons && !zin) {
             const uint64_t pol = l2_evict_first_policy();
             int issued = 0;
             for (int q = 0; q < nq; ++q) {
@@ -287,11 +290,18 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                         mu[j] = active ? coef * (T)wload(orow + wrap1(x0 - K + j, W)) : T(0);
 #pragma unroll
                     for (int k2 = 0; k2 < PS; ++k2) {
-                        const unsigned lim = s_abort ? 64u : limit;
-                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (!zin) {
+                            const unsigned lim = s_abort ? 64u : limit;
+                            if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        }
                         if (active) {
                             T sv[VEC];
-                            vload<T, VEC>(ring + (size_t)slot * tile + (size_t)r * W + x0, sv);
+                            if (zin) {
+#pragma unroll
+                                for (int j = 0; j < VEC; ++j) sv[j] = T(0);
+                            } else {
+                                vload<T, VEC>(ring + (size_t)slot * tile + (size_t)r * W + x0, sv);
+                            }
 #pragma unroll
                             for (int j = 0; j < VEC; ++j) {
                                 const T u = sv[j] - delta[j];
@@ -302,8 +312,10 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                             }
                             vstore_stream<T, VEC>(gp, sv);
                         }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        if (!zin) {
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&empty[slot]);
+                        }
                         gp += kstride;
                         if (++slot == D) { slot = 0; par ^= 1u; }
                     }
@@ -320,10 +332,14 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                     }
 #pragma unroll
                     for (int k2 = 0; k2 < PS; ++k2) {
-                        const unsigned lim = s_abort ? 64u : limit;
-                        if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (!zin) {
+                            const unsigned lim = s_abort ? 64u : limit;
+                            if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        }
                         if (active) {
-                            const int4 w = *reinterpret_cast<const int4*>(ring + (size_t)slot * tile + (size_t)r * W + x0);
+                            // code 0 stands for 0
+                            const int4 w = zin ? make_int4(0, 0, 0, 0)
+                                               : *reinterpret_cast<const int4*>(ring + (size_t)slot * tile + (size_t)r * W + x0);
                             const uint32_t wd[4] = {(uint32_t)w.x, (uint32_t)w.y, (uint32_t)w.z, (uint32_t)w.w};
                             uint32_t out[4];
 #pragma unroll
@@ -347,8 +363,10 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                             }
                             __stcs(reinterpret_cast<int4*>(gp), make_int4((int)out[0], (int)out[1], (int)out[2], (int)out[3]));
                         }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&empty[slot]);
+                        if (!zin) {
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&empty[slot]);
+                        }
                         gp += kstride;
                         if (++slot == D) { slot = 0; par ^= 1u; }
                     }
@@ -388,14 +406,16 @@ __global__ void __launch_bounds__(288, 2) latent_tma_kernel(LatentArgs<T, WT> ar
 
 // One launch over many problems (batched uneven sizes): blocks are mapped to (problem, block)
 // by the segment table; every problem's launch shape fits the common block size and shared
-// memory size of the launch.
+// memory size of the launch.  zero_in applies to every problem (see LatentArgs).
 template <typename T, typename WT, int K, int VEC, typename ST = T>
 __global__ void __launch_bounds__(288, 2)
-latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
+latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
+                        int zero_in) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     int prob, bx, by, bz;
     segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
-    const LatentArgs<T, WT> a = args[prob];
+    LatentArgs<T, WT> a = args[prob];
+    a.zero_in = zero_in;
     latent_tma_body<T, WT, K, VEC, ST>(a, bx, by, bz, smem_tma);
 }
 

@@ -24,52 +24,23 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_phi_scratch[kPhiStaticPartials];
 
 // Per-device address of g_phi_scratch (host code only sees a host-side stand-in for the
-// symbol, so the device address is looked up once per device with that device current).
+// symbol, so the device address is looked up with that device current).  A successful lookup is
+// kept; a failed one is not, so a later call (for example one made outside a stream capture)
+// tries again.
 double* g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_status[kMaxDevices] = {};
+std::mutex g_scratch_mu;
 
-double* scratch_for(int dev, cudaError_t* status) {
-    std::call_once(g_scratch_once[dev], [dev] {
+double* scratch_for(int dev) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
         void* p = nullptr;
-        g_scratch_status[dev] = cudaGetSymbolAddress(&p, g_phi_scratch);
-        g_scratch_ptr[dev] = g_scratch_status[dev] == cudaSuccess ? static_cast<double*>(p) : nullptr;
-    });
-    *status = g_scratch_status[dev];
-    return g_scratch_ptr[dev];
-}
-
-// The regulariser kernel of fuse_objective with its partial sums written to the static array:
-// part[blockIdx.y * gridDim.x + blockIdx.x] = sum over the block's pixels i of
-// omega_tau(i) sum_{k, c} |D_{tau k} X(i, c)|, tau = blockIdx.y (eq. regfilt1).
-template <typename T, typename WT>
-__global__ void __launch_bounds__(256) phi_static_partial_kernel(const T* __restrict__ X,
-                                                                const WT* __restrict__ omega, int H, int W,
-                                                                int Ls, int K, int S, double* __restrict__ part) {
-    const size_t n = (size_t)H * W;
-    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int side = 2 * S + 1;
-    const int tidx = blockIdx.y;
-    const int cell = tidx >= (side * side) / 2 ? tidx + 1 : tidx;
-    const int t1 = cell / side - S, t2 = cell % side - S;
-    double v[1] = {0.0};
-    if (p < n) {
-        const int y = (int)(p / W), x = (int)(p - (size_t)y * W);
-        double acc = 0.0;
-        for (int c = 0; c < Ls; ++c) {
-            const T* Xc = X + (size_t)c * n;
-            T sc = T(0);
-            for (int k1 = -K; k1 <= K; ++k1)
-                for (int k2 = -K; k2 <= K; ++k2) {
-                    const T a = Xc[(size_t)fuse::wrapn(y - k1, H) * W + fuse::wrapn(x - k2, W)];
-                    const T b = Xc[(size_t)fuse::wrapn(y - t1 - k1, H) * W + fuse::wrapn(x - t2 - k2, W)];
-                    sc += a > b ? a - b : b - a;
-                }
-            acc += (double)sc;
+        if (cudaGetSymbolAddress(&p, g_phi_scratch) != cudaSuccess) {
+            cudaGetLastError();              // leave no pending error for the caller's next check
+            return nullptr;
         }
-        v[0] = (double)fuse::wload(omega + (size_t)tidx * n + p) * acc;
+        g_scratch_ptr[dev] = static_cast<double*>(p);
     }
-    fuse::block_sum<1>(v, part + (size_t)blockIdx.y * gridDim.x + blockIdx.x);
+    return g_scratch_ptr[dev];
 }
 
 // Sums the partial sums in a fixed order (deterministic) into out[0].
@@ -102,20 +73,21 @@ extern "C" fuse_status fuse_phi_static(const void* X_dev, const void* omega_dev,
         cudaGetLastError();
         return FUSE_ECUDA;
     }
-    cudaError_t e = cudaSuccess;
-    double* part = scratch_for(dev, &e);
+    double* part = scratch_for(dev);
     if (!part) return FUSE_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     dim3 grid((unsigned)nb, (unsigned)nW);
-    // every partial slot in [0, nb*nW) is written before the reduction reads it
+    // the regulariser kernel of fuse_objective, its partial sums written to the static array:
+    // part[tau * nb + b] = sum over block b's pixels i of omega_tau(i) sum_{k, c} |D_{tau k} X(i, c)|;
+    // every slot in [0, nb*nW) is written before the reduction reads it
     if (f64) {
-        phi_static_partial_kernel<double, double><<<grid, 256, 0, s>>>(
+        fuse::obj_phi_kernel<double, double><<<grid, 256, 0, s>>>(
             static_cast<const double*>(X_dev), static_cast<const double*>(omega_dev), H, W, L_s, K, S, part);
     } else if (wdtype == FUSE_BF16) {
-        phi_static_partial_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>(
+        fuse::obj_phi_kernel<float, __nv_bfloat16><<<grid, 256, 0, s>>>(
             static_cast<const float*>(X_dev), static_cast<const __nv_bfloat16*>(omega_dev), H, W, L_s, K, S, part);
     } else {
-        phi_static_partial_kernel<float, float><<<grid, 256, 0, s>>>(
+        fuse::obj_phi_kernel<float, float><<<grid, 256, 0, s>>>(
             static_cast<const float*>(X_dev), static_cast<const float*>(omega_dev), H, W, L_s, K, S, part);
     }
     if (cudaGetLastError() != cudaSuccess) return FUSE_ECUDA;

@@ -65,13 +65,4 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
-// Self-check of the bounded-wait machinery: waits on a barrier that nothing ever completes.
-// The wait must give up after `limit` polls and set bit `code` in *err.
-__global__ void wait_selftest_kernel(int* err, unsigned limit, int code) {
-    __shared__ uint64_t bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) mbar_wait(&bar, 0u, limit, err, code);
-}
-
 }  // namespace fuse

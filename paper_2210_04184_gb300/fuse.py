@@ -93,6 +93,8 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
         "fuse_batch_solve": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP),
                                    ctypes.POINTER(_VP)]),
+        "fuse_batch_run_host": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
+                                      ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
         "fuse_batch_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
         "fuse_batch_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
         "fuse_batch_sync": (_ST, [_VP]),
@@ -315,6 +317,13 @@ def fuse_batch_solve(b, Yl_devs, Yh_devs, iters: int, X_outs=None, Z_outs=None):
     xo = _ptrs(X_outs) if X_outs is not None else None
     zo = _ptrs(Z_outs) if Z_outs is not None else None
     _bcheck(load().fuse_batch_solve(b, _ptrs(Yl_devs), _ptrs(Yh_devs), iters, xo, zo), b)
+
+
+def fuse_batch_run_host(b, Yl_hosts, Yh_hosts, guide_hosts, iters: int, X_hosts=None, Z_hosts=None):
+    go = _ptrs(guide_hosts) if guide_hosts is not None else None
+    xo = _ptrs(X_hosts) if X_hosts is not None else None
+    zo = _ptrs(Z_hosts) if Z_hosts is not None else None
+    _bcheck(load().fuse_batch_run_host(b, _ptrs(Yl_hosts), _ptrs(Yh_hosts), go, iters, xo, zo), b)
 
 
 def fuse_batch_set_option(b, option: int, value: int):
@@ -562,6 +571,24 @@ class FusionBatch:
         fuse_batch_solve(self.b, [y.data_ptr() for y in yl], [y.data_ptr() for y in yh], iters,
                          [x.data_ptr() for x in Xs] if Xs else None, [z.data_ptr() for z in Zs] if Zs else None)
         self._keep = (yl, yh)
+        return Xs, Zs
+
+    def run_host(self, Yls, Yhs, iters, want_X=False, want_Z=True, guides=None):
+        """End to end on host tensors (pinned CPU tensors of the contexts' dtype): inputs copied
+        in, weights, batched solve from zero, X and/or Z copied back (fuse_batch_run_host)."""
+        t = self.torch
+        for f, a, b in zip(self.fusions, Yls, Yhs):
+            if a.device.type != "cpu" or b.device.type != "cpu" or a.dtype != f.tdtype or b.dtype != f.tdtype:
+                raise ValueError(f"expected CPU tensors of {f.tdtype}")
+            if not (a.is_contiguous() and b.is_contiguous()):
+                raise ValueError("expected contiguous tensors")
+            if tuple(a.shape) != (f.L_l, f.H // f.ratio, f.W // f.ratio) or tuple(b.shape) != (f.L_h, f.H, f.W):
+                raise ValueError("input shape does not match its context")
+        Xs = [t.empty((f.L_s, f.H, f.W), dtype=f.tdtype).pin_memory() for f in self.fusions] if want_X else None
+        Zs = [t.empty((f.L_l, f.H, f.W), dtype=f.tdtype).pin_memory() for f in self.fusions] if want_Z else None
+        gp = [g.data_ptr() for g in guides] if guides is not None else None
+        fuse_batch_run_host(self.b, [a.data_ptr() for a in Yls], [b.data_ptr() for b in Yhs], gp, iters,
+                            [x.data_ptr() for x in Xs] if Xs else None, [z.data_ptr() for z in Zs] if Zs else None)
         return Xs, Zs
 
     def set_option(self, option, value):

@@ -6,6 +6,9 @@
   oracle (the third is the first with a nonzero latent state), and after the full 100
   iterations the invariant |Sigma'| <= mu on sampled state entries;
 - HS+PAN parameters (128 bands -> 20, 11x11 blur, K = 2, S = 5) on a 64x64 crop: 8 iterations.
+- at the workloads' own iteration counts against the oracle, element by element: HS+MS at its
+  full size for all 100 iterations (X, Z and sampled latent state), and the HS+PAN parameters on
+  a 128 x 128 crop for all 200 iterations (its full size needs 252 GB of oracle state).
 """
 import os
 
@@ -225,3 +228,68 @@ def test_hspan_full_size_fixed_point_state():
     torch.cuda.empty_cache()
     _, Z64, _ = _gpu(p, p.iters, "f64", "f64")
     assert rel(Zq, Z64) <= 1e-4
+
+
+def _kept_offsets(S):
+    return [t for t, tau in enumerate(nlpr.search_offsets(S)) if tau[0] > 0 or (tau[0] == 0 and tau[1] > 0)]
+
+
+def _full_run_parity(p, iters, seed):
+    """FP32 iterates with BF16 weights (the oracle's FP64 weights rounded to BF16 and given to both
+    sides) after `iters` iterations from zero: X and Z element by element within 1e-5 relative
+    Frobenius of the FP64 oracle, and 4000 sampled entries of the latent state against the
+    oracle's Sigma (stored re-indexed by the source pixel on the GPU:
+    Sig'[tau][k][c][m] = Sigma_{tau k}(m + k))."""
+    from oracle import cloops
+    om = nlpr.round_bf16(cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h))
+    X, Z, f = _gpu(p, iters, "f32", "bf16", omega=om)
+    st = f.get_state().cpu()
+    f.close()
+    torch.cuda.empty_cache()
+    Xo, sto, _ = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S,
+                           p.lam1, p.lam2, p.rho, om, iters, fast=True, inplace=True)
+    Xo = nlpr.to_lhw(Xo)
+    assert rel(X, Xo) <= 1e-5
+    assert rel(Z, np.einsum("chw,cl->lhw", Xo, p.E)) <= 1e-5
+    n, Ls = p.H * p.W, p.L_s
+    img = n * Ls
+    kept = _kept_offsets(p.S)
+    poffs = nlpr.patch_offsets(p.K)
+    sig = st[5 * img * 4:(5 * img + len(kept) * len(poffs) * img) * 4].view(torch.float32)
+    sig = sig.reshape(len(kept), len(poffs), Ls, p.H, p.W).numpy()
+    rng = np.random.default_rng(seed)
+    scale = float(np.abs(sto.Sig).max())
+    nz = 0
+    for _ in range(4000):
+        j = int(rng.integers(len(kept))); kk = int(rng.integers(len(poffs)))
+        c = int(rng.integers(Ls)); y = int(rng.integers(p.H)); x = int(rng.integers(p.W))
+        k = poffs[kk]
+        want = sto.Sig[kept[j], kk, (y + k[0]) % p.H, (x + k[1]) % p.W, c]
+        got = float(sig[j, kk, c, y, x])
+        # each entry is -clamp(v, -mu, mu) with v a difference of X values: 1-Lipschitz in X
+        assert abs(got - want) <= 1e-5 * scale + 1e-5 * float(np.abs(Xo).max()), (got, want)
+        nz += want != 0.0
+    assert nz > 0
+
+
+def test_hsms_full_size_all_iterations():
+    # the benchmarked single-problem workload at its size and its 100 iterations
+    p, meta = synth.workload("hsms_256")
+    need = 2 * 48 * 25 * 20 * 256 * 256 * 8 / 2 ** 30 + 6
+    if _host_gib() < need * 1.2:
+        pytest.skip(f"host has {_host_gib():.0f} GiB available, the oracle needs {need:.0f}")
+    _full_run_parity(p, p.iters, 11)
+
+
+def test_hspan_crop_all_iterations():
+    # every HS+PAN parameter (128 bands -> L_s 20, 11x11 blur sigma 2, 30 dB, K = 2, S = 5,
+    # 120 offsets) and its 200 iterations on a 128 x 128 crop, with the workload's BF16 weights
+    spec = dict(synth.WORKLOADS["hspan_512"])
+    for k in ("dtype", "wdtype", "cfg", "H", "W"):
+        spec.pop(k)
+    p = synth.make_problem(H=128, W=128, seed=synth.SEED_BASE + 2, **spec)
+    assert p.iters == 200 and p.S == 5 and p.K == 2 and p.L_s == 20
+    need = 2 * 120 * 25 * 20 * 128 * 128 * 8 / 2 ** 30 + 4
+    if _host_gib() < need * 1.2:
+        pytest.skip(f"host has {_host_gib():.0f} GiB available, the oracle needs {need:.0f}")
+    _full_run_parity(p, p.iters, 12)

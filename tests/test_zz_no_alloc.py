@@ -1,7 +1,8 @@
 """fuse_phi_static: the regulariser value without any device allocation, for callers that may
 not allocate (e.g. while their stream is captured into a CUDA graph, or under a host-owned GPU
 memory budget).  Checked through the C-ABI against fuse_objective's regulariser term on two
-calls in a row (the second call finds the previous call's partial sums in the shared array)."""
+calls in a row (the second call finds the previous call's partial sums in the shared array), and
+against the FP64 oracle's phi (eq. reg1) evaluated on the same X and weights copied to the host."""
 import numpy as np
 import pytest
 
@@ -10,6 +11,7 @@ from paper_2210_04184_gb300 import synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
+from oracle import nlpr  # noqa: E402
 from paper_2210_04184_gb300 import build as _build  # noqa: E402
 from paper_2210_04184_gb300 import fuse  # noqa: E402
 from paper_2210_04184_gb300.fuse import Fusion, FuseError  # noqa: E402
@@ -40,6 +42,9 @@ def test_phi_static_matches_objective_twice(dtype, wdtype):
         torch.cuda.synchronize()
         phi = float(out.item())
         assert abs(p.lam2 * phi - obj[2]) <= 1e-5 * abs(obj[2])
+    # the oracle's phi on the GPU's own X and weights (FP32: per-pixel sums in FP32, 1e-5; FP64: 1e-11)
+    ref = nlpr.nlpr(nlpr.to_hwl(X.double().cpu().numpy()), om.double().cpu().numpy(), p.K, p.S)
+    assert abs(phi - ref) <= (1e-11 if dtype == "f64" else 1e-5) * abs(ref)
     f.close()
 
 
