@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch64")
     ap.add_argument("--problems", type=int, default=64, help="problems of the batch workload")
+    ap.add_argument("--batch-shape", default=None,
+                    help="latent launch shape of the batch as THREADS,STAGES,BANDS (skips the batch tuner)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the single-problem secondary line")
     ap.add_argument("--iters", type=int, default=None, help="override the workload's iteration count")
     ap.add_argument("--no-e2e", action="store_true")
@@ -238,13 +240,14 @@ def batch_config(ps, iters, world):
             "latent_state": "half window (one offset of each +-tau pair)"}
 
 
-def cpu_baseline(p, target_s=15.0):
-    """The FP64 oracle timed on the host cores on a bounded crop of the same workload
-    (same bands, subspace, patch and window; a 48 x 48 image; weights plus n iterations,
-    n sized from a one-iteration probe so the sample takes about target_s seconds)."""
+def cpu_baseline(p, target_s=15.0, crop=48):
+    """The FP64 oracle timed on the host cores on a bounded sample of the same workload: a
+    crop x crop problem with the same bands, subspace, blur, patch and window (for the batch
+    workload, one problem of its smallest size), weights plus n iterations, n sized from a
+    one-iteration probe so the sample takes about target_s seconds (at most the workload's
+    iteration count)."""
     from oracle import nlpr
     from paper_2210_04184_gb300 import synth
-    crop = 48
     q = synth.make_problem(H=crop, W=crop, L_l=p.L_l, L_h=p.L_h, L_s=p.L_s, d=p.d,
                            blur_size=p.blur.shape[0], blur_sigma=1.7, K=p.K, S=p.S, lam1=p.lam1,
                            lam2=p.lam2, rho=p.rho, h=p.h, seed=1, kind="hsms")
@@ -258,12 +261,12 @@ def cpu_baseline(p, target_s=15.0):
 
     run(1)                      # first touch of the oracle's arrays
     probe = run(1)
-    n = int(max(1, min(100, target_s / max(probe, 1e-3))))
+    n = int(max(1, min(p.iters, target_s / max(probe, 1e-3))))
     dt = run(n)
     value = crop * crop / 1e6 * q.L_s * n / dt
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{crop}x{crop} crop, {q.L_l} bands, L_s={q.L_s}, K={q.K}, S={q.S}, "
+            "sample": f"{crop}x{crop} problem, {q.L_l} bands, L_s={q.L_s}, K={q.K}, S={q.S}, "
                       f"weights + {n} iterations, FP64 NumPy + C/OpenMP loops, {dt:.1f}s"}
 
 
@@ -283,8 +286,9 @@ def run_reference(a, rank, world):
         config = _config(p, meta, a.workload, a.gpus)
     samples = []
     cb = None
+    crop = min(q.H for q in ps) if a.workload == "batch64" else 48
     for i in range(a.warmup + a.steps):
-        cb = cpu_baseline(p, target_s=8.0 if i >= a.warmup else 2.0)
+        cb = cpu_baseline(p, target_s=8.0 if i >= a.warmup else 2.0, crop=crop)
         if i >= a.warmup:
             samples.append(cb["value"])
     value = statistics.median(samples)
@@ -449,8 +453,15 @@ def run_batch(a, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     for f, h in zip(fs, yh):
         fuse_weights(f.ctx, h.data_ptr())
-    if not a.no_autotune:
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_LATENT_BANDS
+    if a.batch_shape:
+        th, sg, bd = (int(v) for v in a.batch_shape.split(","))
+        batch.set_option(FUSE_OPT_LATENT_THREADS, th)
+        batch.set_option(FUSE_OPT_LATENT_STAGES, sg)
+        batch.set_option(FUSE_OPT_LATENT_BANDS, bd)
+    elif not a.no_autotune:
         batch.autotune(yl, yh, iters=1)            # launch shapes only; results are unchanged
+    shape = batch.latent_shape()
     Zs = None
 
     def step():
@@ -551,7 +562,7 @@ def run_batch(a, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": batch_config(ps, iters, world),
+        "config": dict(batch_config(ps, iters, world), latent_shape=shape),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": latent_traffic("batch", px), "kernel": "latent_tma_batch_kernel",
                      "algorithmic_bytes_per_launch": lb, "avg_launch_ms": per_launch_ms, "launches": lat_n,
@@ -567,7 +578,7 @@ def run_batch(a, rank, world, local_rank):
     if not a.no_secondary and world == 1:
         out["hsms_256"] = single_problem(a, "hsms_256", 0, None)
     if not a.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(ps[0])
+        out["cpu_baseline"] = cpu_baseline(ps[0], crop=min(p.H for p in ps))
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()

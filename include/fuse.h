@@ -101,7 +101,7 @@ enum {
                                     pass (W % 8 == 0) only; not with the reverse pass.  Switching
                                     reallocates the state and clears it.  A batch takes the
                                     format of its contexts (all the same). */
-    FUSE_OPT_X_UPDATE = 14       /* X update: 0 (default) the paper's splitting (P1 = B X, the X
+    FUSE_OPT_X_UPDATE = 14,      /* X update: 0 (default) the paper's splitting (P1 = B X, the X
                                     system diagonal in the DFT basis, eq. inv); 1 = a variant that
                                     is not the paper's: only P2 = X and Q = D X are split, so the X
                                     system keeps the data term,
@@ -115,6 +115,13 @@ enum {
                                     deviation <= 1e-6) and H, W with 2H+1 complex values per
                                     column fitting shared memory; not with the reverse pass or a
                                     batch (FUSE_EUNSUPPORTED).  Switching clears the ADMM state. */
+    FUSE_OPT_RESIDUALS = 15      /* 1: every fuse_solve with iters >= 1 runs its last iteration as a
+                                    monitored one (directly launched, about 1.5 times the work of
+                                    an iteration) whose ADMM residual norms fuse_residuals returns;
+                                    0 (default): off.  Needs the bulk-copy latent pass, the state in
+                                    the iterate type and the paper's splitting (FUSE_EUNSUPPORTED
+                                    otherwise).  The first switch to 1 allocates 4 images and 2
+                                    adjoint-plane arrays of workspace. */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -199,6 +206,19 @@ fuse_status fuse_run_host(fuse_ctx* ctx, const void* Yl_host, const void* Yh_hos
  * out[3] = ||X||_F^2.  Y_l, Y_h as in fuse_solve.  Synchronous; sums in FP64.
  * Errors: FUSE_ESTATE (no solve yet), FUSE_ENONFINITE (a term is not finite). */
 fuse_status fuse_objective(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, double out[4]);
+
+/* ADMM residual norms of the last iteration of the last fuse_solve, which must have run with
+ * FUSE_OPT_RESIDUALS = 1 (else FUSE_ESTATE; also after any later call that changed inputs or
+ * state).  In the scaled form of the splitting of eq. fusionoptim (A X = z, A = (B; I; D_{tau k}),
+ * z = (P1, P2, Q), Sec. IV), for the iteration (X, z) -> (X', z'):
+ *   out[0] = primal ||A X' - z'|| = sqrt(||B X' - P1'||^2 + ||X' - P2'||^2 + sum ||D X' - Q'||^2),
+ *            which by the dual updates (eqs. dualvar1_main..dualvar3_main) is the change of the
+ *            scaled duals ||(Lambda1, Lambda2, Sigma) - (Lambda1', Lambda2', Sigma')||;
+ *   out[1] = dual rho ||A^T (z' - z)|| = rho ||B^T (P1' - P1) + (P2' - P2) + sum D^T (Q' - Q)||,
+ * over the full search window, summed in FP64 (the paper monitors the objective; these are the
+ * standard ADMM stopping quantities).  Synchronous.  Errors: FUSE_ESTATE, FUSE_EINVAL (NULL),
+ * FUSE_ENONFINITE (a norm is not finite: the iterates diverged or an input held a NaN). */
+fuse_status fuse_residuals(fuse_ctx* ctx, double out[2]);
 
 /* General sampling operator: S keeps the pixels where mask is nonzero instead of the regular
  * lattice (for example a random inpainting mask).  Needs ratio 1 (FUSE_EINVAL otherwise); Y_l
@@ -384,6 +404,9 @@ fuse_status fuse_batch_run_host(fuse_batch* b, const void* const* Yl_host, const
 /* FUSE_OPT_PROFILE, FUSE_OPT_GRAPH, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES,
  * FUSE_OPT_LATENT_BANDS. */
 fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value);
+
+/* Current value of a batch option (the options of fuse_batch_set_option).  Errors: FUSE_EINVAL. */
+fuse_status fuse_batch_get_option(fuse_batch* b, int option, long long* value);
 
 /* Launch-shape tuner of a batch (latent pass: consumer threads, ring slots, bands per block),
  * timing `iters` batched iterations per candidate; inputs as in fuse_batch_solve.  Synchronous. */

@@ -17,6 +17,7 @@
 #include "k_fft.cuh"
 #include "k_grad.cuh"
 #include "k_latent.cuh"
+#include "k_monitor.cuh"
 #include "k_objective.cuh"
 #include "k_pixel.cuh"
 #include "k_stencil.cuh"
@@ -41,6 +42,8 @@ __global__ void wait_selftest_kernel(int* err, unsigned limit, int code) {
 namespace {
 
 constexpr int kMaxSmem = 200 * 1024;
+// blocks of the grid-stride reduction kernels of the residual monitor (fixed: deterministic sums)
+constexpr int kMonBlocks = 4 * 152;
 
 struct Event2 { cudaEvent_t a, b; };
 
@@ -161,6 +164,15 @@ struct fuse_ctx {
     void *sbq = nullptr, *sbp = nullptr, *sbk = nullptr;
     int fa_m = 1, fa_tpc = 32;
     size_t fa_smem = 0;
+    // residual monitor (FUSE_OPT_RESIDUALS): copies of Lambda1, U1, Lambda2, U2 and of the adjoint
+    // planes entering the last iteration of a solve, the monitoring latent pass's planes, FP64
+    // block sums ([latent blocks (room for mon_lat_cap)] [pixel pass] [dual image]); mon_epoch: the
+    // context epoch of the last monitored iteration, mon_lat: its latent block count
+    int monitor = 0;
+    void *mL1 = nullptr, *mU1 = nullptr, *mL2 = nullptr, *mU2 = nullptr, *mPo = nullptr, *mPm = nullptr;
+    double* mon_part = nullptr;
+    size_t mon_lat_cap = 0, mon_lat = 0;
+    long long mon_epoch = -1;
 };
 
 namespace {
@@ -416,14 +428,22 @@ bool latent_tma_shape(fuse_ctx* c) {
     return true;
 }
 
+// Dynamic shared-memory cap of the monitoring latent kernels of this context's types.
+bool set_monitor_smem(fuse_ctx* c) {
+    cudaError_t e;
+    if (c->dtype == FUSE_F64) e = latent_set_smem<double, double>(c->K, kMaxSmem);
+    else if (c->wdtype == FUSE_BF16) e = latent_set_smem<float, __nv_bfloat16>(c->K, kMaxSmem);
+    else e = latent_set_smem<float, float>(c->K, kMaxSmem);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------------------
 // typed launch sequence
 // ---------------------------------------------------------------------------------------
 
 template <typename T>
 struct Impl {
-    static constexpr int VEC = 16 / sizeof(T);
-    static constexpr int TVEC = 32 / sizeof(T);        // pixels per thread of the bulk-copy pass
 
     // ---- argument blocks of the iteration kernels ----
     static StencilArgs<T> st_args(fuse_ctx* c, const void* in, void* out, const void* taps) {
@@ -530,10 +550,45 @@ struct Impl {
 
     static void latent_any(fuse_ctx* c, cudaStream_t s, bool zero_in);
 
+    // The monitoring latent pass (bulk-copy kernel, state in the iterate type) and the residual
+    // sums of the iteration that ran it (k_monitor.cuh).
+    template <typename WT>
+    static void latent_monitor(fuse_ctx* c, cudaStream_t s, bool zero_in) {
+        const unsigned rowsW = (unsigned)(c->half ? c->S + 1 : 2 * c->S + 1);
+        dim3 grid((unsigned)((c->H + c->lt_Ty - 1) / c->lt_Ty), (unsigned)((c->Ls + c->lat_bpb - 1) / c->lat_bpb),
+                  rowsW);
+        LatentArgs<T, WT> a = lat_args<WT>(c, c->lt_Ty, c->lt_ncons, c->lat_stages, c->lat_bpb, zero_in);
+        a.mplanes = (T*)c->mPm;
+        a.mpart = c->mon_part;
+        c->mon_lat = (size_t)grid.x * grid.y * grid.z;
+        const size_t smem = c->lt_smem + (size_t)(2 * c->S + 1) * c->lt_Ty * c->W * sizeof(T);
+        latent_monitor_launch<T, WT>(a, c->K, grid, (unsigned)(c->lt_ncons + 32), smem, s);
+    }
+
+    static fuse_status monitor_sums(fuse_ctx* c, cudaStream_t s) {
+        const size_t cnt = c->n * c->Ls;
+        double* pix = c->mon_part + c->mon_lat_cap;
+        monitor_pixel_kernel<T><<<kMonBlocks, 256, 0, s>>>((const T*)c->Lam1, (const T*)c->U1, (const T*)c->Lam2,
+                                                           (const T*)c->U2, (const T*)c->mL1, (T*)c->mU1,
+                                                           (const T*)c->mL2, (T*)c->mU2, cnt, pix);
+        CKL(c, "monitor_pixel_kernel");
+        sub_kernel<T><<<kMonBlocks, 256, 0, s>>>((T*)c->mPm, (const T*)c->mPo, c->plane_bytes / sizeof(T));
+        CKL(c, "sub_kernel");
+        // B^T dP1 + dP2 + sum D^T dQ into C (free until the next iteration forms it)
+        const StencilArgs<T> a{(const T*)c->mU1, (T*)c->C, (const T*)c->tapsT, c->bw, c->H, c->W,
+                               (const T*)c->mU2, (const T*)c->mPm, c->S, c->half};
+        stencil_launch<1>(c, s, a);
+        CKL(c, "stencil_kernel (dual residual)");
+        sumsq_kernel<T><<<kMonBlocks, 256, 0, s>>>((const T*)c->C, cnt, pix + kMonBlocks);
+        CKL(c, "sumsq_kernel");
+        c->launches_all += 4;
+        return FUSE_OK;
+    }
+
     // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.  With xmode 1 (S B
     // kept in the X system): C = G + U2 + R with the fixed data term G in U1, the column pass
     // solves the alias classes, and there is no B X and no P1.  zero_in: see latent().
-    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed, bool zero_in = false) {
+    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed, bool zero_in = false, bool monitor = false) {
         if (c->xmode == 1) {
             dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
             rhs_sum_kernel<T><<<grid, dim3(ST_TX, ST_BY), 0, s>>>(st_args(c, c->U1, c->C, nullptr));
@@ -577,10 +632,18 @@ struct Impl {
             CK(c, cudaEventRecord(e.a, s));
             latent_any(c, s, zero_in);
             CK(c, cudaEventRecord(e.b, s));
+        } else if (monitor) {
+            if constexpr (sizeof(T) == 8) {
+                latent_monitor<double>(c, s, zero_in);
+            } else {
+                if (c->wdtype == FUSE_BF16) latent_monitor<__nv_bfloat16>(c, s, zero_in);
+                else latent_monitor<float>(c, s, zero_in);
+            }
         } else {
             latent_any(c, s, zero_in);
         }
         CKL(c, "latent kernel");
+        if (monitor) return monitor_sums(c, s);
         return FUSE_OK;
     }
 
@@ -707,7 +770,40 @@ fuse_status launch_loop(fuse_ctx* c, int len, bool cold) {
 // Runs `iters` iterations: the whole loop replayed from captured graphs of up to kGraphIters
 // iterations, or launched directly when profiling or with graphs switched off.  cold: the state
 // entering the first iteration is zero and its latent pass reads none of it.
+fuse_status run_iterations_plain(fuse_ctx* c, int iters, bool cold);
+
+// The last iteration of a monitored solve: the entering Lambda1, U1, Lambda2, U2 and adjoint
+// planes are copied aside, then the iteration runs with the monitoring latent pass and the
+// residual sums (directly launched).
+fuse_status monitored_iteration(fuse_ctx* c, bool zero_in) {
+    if (c->lat_impl != 1 || c->sfmt != 0 || c->xmode != 0)
+        return fail(c, FUSE_EUNSUPPORTED, "the residual monitor needs the bulk-copy latent pass, the state in the "
+                                          "iterate type and the paper's splitting");
+    if (c->lt_smem + (size_t)(2 * c->S + 1) * c->lt_Ty * c->W * c->esz > (size_t)kMaxSmem)
+        return fail(c, FUSE_EUNSUPPORTED, "the monitoring latent pass does not fit shared memory");
+    const size_t img = c->n * c->Ls * c->esz;
+    cudaStream_t s = c->stream;
+    CK(c, cudaMemcpyAsync(c->mL1, c->Lam1, img, cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaMemcpyAsync(c->mU1, c->U1, img, cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaMemcpyAsync(c->mL2, c->Lam2, img, cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaMemcpyAsync(c->mU2, c->U2, img, cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaMemcpyAsync(c->mPo, c->planes, c->plane_bytes, cudaMemcpyDeviceToDevice, s));
+    fuse_status st = c->dtype == FUSE_F64 ? Impl<double>::iterate(c, s, false, zero_in, true)
+                                          : Impl<float>::iterate(c, s, false, zero_in, true);
+    if (st != FUSE_OK) return st;
+    c->launches_all += iteration_launches(c);
+    c->launches_latent += 1;
+    return FUSE_OK;
+}
+
 fuse_status run_iterations(fuse_ctx* c, int iters, bool cold = false) {
+    if (iters <= 0 || !c->monitor) return run_iterations_plain(c, iters, cold);
+    fuse_status st = run_iterations_plain(c, iters - 1, cold);
+    if (st != FUSE_OK) return st;
+    return monitored_iteration(c, cold && iters == 1);
+}
+
+fuse_status run_iterations_plain(fuse_ctx* c, int iters, bool cold) {
     if (iters <= 0) return FUSE_OK;
     const bool f64 = c->dtype == FUSE_F64;
     if (c->profile || !c->use_graph) {
@@ -756,6 +852,7 @@ fuse_status solve_impl(fuse_ctx* c, const void* Yl, const void* Yh, int iters, i
     }
     st = run_iterations(c, iters, cold);
     if (st != FUSE_OK) return st;
+    if (c->monitor && iters > 0) c->mon_epoch = c->epoch;
     c->have_x = true;
     const size_t img = c->n * c->Ls * c->esz;
     if (Xo) CK(c, cudaMemcpyAsync(Xo, c->X, img, cudaMemcpyDeviceToDevice, c->stream));
@@ -1524,6 +1621,30 @@ fuse_status fuse_objective(fuse_ctx* c, const void* Yl, const void* Yh, double o
     return c->dtype == FUSE_F64 ? Impl<double>::objective(c, Yl, Yh, out) : Impl<float>::objective(c, Yl, Yh, out);
 }
 
+fuse_status fuse_residuals(fuse_ctx* c, double out[2]) {
+    fuse_status st = guard(c);
+    if (st != FUSE_OK) return st;
+    if (!out) return fail(c, FUSE_EINVAL, "NULL argument");
+    if (!c->monitor || !c->mon_part || c->mon_epoch != c->epoch)
+        return fail(c, FUSE_ESTATE, "no monitored iteration since the last change of inputs or state");
+    const size_t np = c->mon_lat_cap + 2 * kMonBlocks;
+    std::vector<double> h(np);
+    CK(c, cudaMemcpyAsync(h.data(), c->mon_part, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    double lat = 0.0, pix = 0.0, dual = 0.0;
+    for (size_t b = 0; b < c->mon_lat; ++b) lat += h[b];
+    for (int b = 0; b < kMonBlocks; ++b) {
+        pix += h[c->mon_lat_cap + b];
+        dual += h[c->mon_lat_cap + kMonBlocks + b];
+    }
+    // half-window mode: the -tau offsets' latent variables are images of the kept ones under an
+    // orthogonal map, so their squared norms are equal
+    out[0] = std::sqrt(pix + (c->half ? 2.0 : 1.0) * lat);
+    out[1] = c->rho * std::sqrt(dual);
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1])) return fail(c, FUSE_ENONFINITE, "residual is not finite");
+    return FUSE_OK;
+}
+
 fuse_status fuse_state_bytes(fuse_ctx* c, size_t* bytes) {
     if (!c || !bytes) return FUSE_EINVAL;
     *bytes = 5 * c->n * c->Ls * c->esz + c->sig_bytes + c->plane_bytes;
@@ -1659,6 +1780,27 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             drop_graphs(c);
             return FUSE_OK;
         }
+        case FUSE_OPT_RESIDUALS: {
+            if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "residual monitor is 0 or 1");
+            if (value == 1 && (c->xmode != 0 || c->sfmt != 0 || c->lat_impl != 1))
+                return fail(c, FUSE_EUNSUPPORTED, "the residual monitor needs the bulk-copy latent pass, the state "
+                                                  "in the iterate type and the paper's splitting");
+            if (value == 1 && !c->mon_part) {
+                const size_t img = c->n * c->Ls * c->esz;
+                void** imgs[] = {&c->mL1, &c->mU1, &c->mL2, &c->mU2};
+                for (void** q : imgs)
+                    if ((st = dalloc(c, q, img)) != FUSE_OK) return st;
+                if ((st = dalloc(c, &c->mPo, c->plane_bytes)) != FUSE_OK) return st;
+                if ((st = dalloc(c, &c->mPm, c->plane_bytes)) != FUSE_OK) return st;
+                // latent blocks are at most H * L_s * (2S+1) (one row and one band per block)
+                c->mon_lat_cap = (size_t)c->H * c->Ls * (2 * c->S + 1);
+                if ((st = dalloc(c, (void**)&c->mon_part, (c->mon_lat_cap + 2 * kMonBlocks) * sizeof(double))) != FUSE_OK)
+                    return st;
+                if (!set_monitor_smem(c)) return fail(c, FUSE_ECUDA, "cudaFuncSetAttribute (monitoring latent pass)");
+            }
+            c->monitor = (int)value;
+            return FUSE_OK;
+        }
         case FUSE_OPT_WAIT_LIMIT:
             if (value < 1) return fail(c, FUSE_EINVAL, "wait limit must be positive");
             c->wait_limit = (unsigned)value;
@@ -1697,8 +1839,10 @@ static fuse_status time_iterations(fuse_ctx* c, int iters, double* ms) {
     CK(c, cudaEventCreate(&a));
     CK(c, cudaEventCreate(&b));
     const bool g = c->use_graph, pr = c->profile;
+    const int mon = c->monitor;
     c->use_graph = false;
     c->profile = false;
+    c->monitor = 0;
     fuse_status st = run_iterations(c, 1);                 // warm-up
     if (st == FUSE_OK) {
         cudaEventRecord(a, c->stream);
@@ -1707,6 +1851,7 @@ static fuse_status time_iterations(fuse_ctx* c, int iters, double* ms) {
     }
     c->use_graph = g;
     c->profile = pr;
+    c->monitor = mon;
     float t = 0.f;
     if (st == FUSE_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&t, a, b) == cudaSuccess)
         *ms = t;
@@ -1789,6 +1934,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_GRAD_SEGMENT: *value = c->grad_seg; return FUSE_OK;
         case FUSE_OPT_GRAD_WEIGHTS: *value = c->grad_weights; return FUSE_OK;
         case FUSE_OPT_X_UPDATE: *value = c->xmode; return FUSE_OK;
+        case FUSE_OPT_RESIDUALS: *value = c->monitor; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }
@@ -1987,6 +2133,18 @@ fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value) {
             return FUSE_OK;
         }
         default: return bfail(b, FUSE_EINVAL, "unknown batch option");
+    }
+}
+
+fuse_status fuse_batch_get_option(fuse_batch* b, int option, long long* value) {
+    if (!b || !value) return FUSE_EINVAL;
+    switch (option) {
+        case FUSE_OPT_PROFILE: *value = b->profile; return FUSE_OK;
+        case FUSE_OPT_GRAPH: *value = b->use_graph; return FUSE_OK;
+        case FUSE_OPT_LATENT_THREADS: *value = b->lat_target; return FUSE_OK;
+        case FUSE_OPT_LATENT_STAGES: *value = b->lat_stages; return FUSE_OK;
+        case FUSE_OPT_LATENT_BANDS: *value = b->lat_bpb; return FUSE_OK;
+        default: return FUSE_EINVAL;
     }
 }
 

@@ -162,6 +162,10 @@ struct LatentArgs {
     int bpb;            // bands per block: the ring keeps streaming across them
     int zero_in;        // 1: the entering state is zero (first iteration of a cold solve): nothing
                         // is read, the pass only writes the new state and the adjoint sums
+    // monitoring instance only (latent_tma_monitor_kernel): adjoint planes of Q' + Sigma (same
+    // layout as `planes`) and one FP64 sum of (Sigma' - Sigma)^2 per block
+    T* mplanes;
+    double* mpart;
 };
 
 __device__ __forceinline__ void consumer_barrier(int ncons) {
@@ -172,7 +176,11 @@ __device__ __forceinline__ void consumer_barrier(int ncons) {
 // tau1 row `row`.  The bands are processed one after the other while the producer keeps the
 // ring full; between bands the consumers meet at a named barrier (the producer never waits on
 // it) to form and store that band's adjoint partial sums.
-template <typename T, typename WT, int K, int VEC, typename ST>
+// MON (monitoring instance, the last iteration of a solve whose residuals are wanted) also forms
+// the adjoint sums of Q' + Sigma = v + Sigma' + Sigma (into args.mplanes, from a second Hs
+// region) and the block's sum of (Sigma' - Sigma)^2 (into args.mpart): the latent parts of the
+// ADMM dual and primal residuals (Sec. IV, eq. dualvar3_main: D X - Q' = Sigma - Sigma').
+template <typename T, typename WT, int K, int VEC, typename ST, bool MON = false>
 __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, int bx, int g, int row,
                                                 unsigned char* smem_tma) {
     const T* __restrict__ X = args.X;
@@ -191,7 +199,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int tile = Ty * W;
     ST* ring = reinterpret_cast<ST*>(smem_tma);               // [D][Ty][W] of the storage type
     T* Hs = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [(2S+1)][Ty][W]
-    uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)side * tile);
+    constexpr int NHS = MON ? 2 : 1;                           // MON: Hs2 = Hs + side * tile
+    uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)NHS * side * tile);
     uint64_t* empty = full + D;
     __shared__ volatile int s_abort;
 
@@ -262,6 +271,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const size_t kstride = (size_t)Ls * n;
     int slot = 0;
     unsigned par = 0;
+    T* Hs2 = Hs + (size_t)side * tile;                   // MON only
+    double dsq = 0.0;                                    // MON only: sum of (Sigma' - Sigma)^2
     for (int item = 0; item < nb; ++item) {
         const int c = c0 + item;
         const T* Xc = X + (size_t)c * n;
@@ -273,9 +284,11 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
         for (int jt = 0; jt < nt2; ++jt) {
             const int t2 = tm.t2_of(t1, jt);
             T Hacc[VEC], delta[VEC];
+            T Macc[MON ? VEC : 1];
 #pragma unroll
             for (int j = 0; j < VEC; ++j) {
                 Hacc[j] = T(0);
+                if constexpr (MON) Macc[j] = T(0);
                 delta[j] = active ? Xm[j] - Xc[xsrow + wrap1(x0 + j - t2, W)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
@@ -308,6 +321,11 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                                 const T m = mu[j + k2];
                                 const T s2 = tmin(tmax(u, -m), m);
                                 Hacc[j] += T(2) * s2 - u;
+                                if constexpr (MON) {
+                                    Macc[j] += s2 + sv[j] - u;              // Q' + Sigma
+                                    const double dd = (double)(s2 - sv[j]);
+                                    dsq += dd * dd;
+                                }
                                 sv[j] = s2;
                             }
                             vstore_stream<T, VEC>(gp, sv);
@@ -375,6 +393,10 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             if (owner) {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
+                if constexpr (MON) {
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) Hs2[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Macc[j];
+                }
             }
         }
         consumer_barrier(ncons);                 // every H_tau of this band is in Hs
@@ -393,8 +415,37 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             }
             vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
             vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
+            if constexpr (MON) {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) { A[j] = T(0); V[j] = T(0); }
+                for (int jt = 0; jt < nt2; ++jt) {
+                    const int t2 = tm.t2_of(t1, jt);
+                    const T* hrow = Hs2 + ((size_t)(t2 + S) * Ty + r) * W;
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        A[j] += hrow[x0 + j];
+                        V[j] += hrow[wrap1(x0 + j + t2, W)];
+                    }
+                }
+                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
+                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
+            }
         }
         if (item + 1 < nb) consumer_barrier(ncons);   // Hs is read before the next band rewrites it
+    }
+    if constexpr (MON) {
+        // the block's sum of (Sigma' - Sigma)^2 over its consumers, in a fixed order
+        __shared__ double s_red[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dsq += __shfl_down_sync(0xffffffffu, dsq, o);
+        consumer_barrier(ncons);                 // the last band's reads of Hs are done
+        if (lane == 0) s_red[tid >> 5] = dsq;
+        consumer_barrier(ncons);
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < ncons / 32; ++w) t += s_red[w];
+            args.mpart[blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = t;
+        }
     }
 }
 
@@ -402,6 +453,14 @@ template <typename T, typename WT, int K, int VEC, typename ST = T>
 __global__ void __launch_bounds__(288, 2) latent_tma_kernel(LatentArgs<T, WT> args) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     latent_tma_body<T, WT, K, VEC, ST>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
+}
+
+// The monitoring instance (state in the iterate type): the same update, plus the latent parts of
+// the ADMM residuals (see latent_tma_body); needs (2S+1) Ty W more elements of shared memory.
+template <typename T, typename WT, int K, int VEC>
+__global__ void __launch_bounds__(288, 1) latent_tma_monitor_kernel(LatentArgs<T, WT> args) {
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    latent_tma_body<T, WT, K, VEC, T, true>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
 }
 
 // One launch over many problems (batched uneven sizes): blocks are mapped to (problem, block)

@@ -30,6 +30,10 @@ void latent_tma_batch_launch(const LatentArgs<T, WT>* args, const Segment* seg, 
 template <typename T, typename WT>
 void latent_reg_launch(const T* X, const WT* omega, const T* Sig, T* Sout, T* planes, int H, int W, int Ls, int S,
                        int Ty, T coef, int half, int K, dim3 grid, unsigned threads, size_t smem, cudaStream_t s);
+// Monitoring latent pass (state in the iterate type): also the latent parts of the residuals.
+template <typename T, typename WT>
+void latent_monitor_launch(const LatentArgs<T, WT>& a, int K, dim3 grid, unsigned threads, size_t smem,
+                           cudaStream_t s);
 // Dynamic shared-memory cap of the single-problem and batched latent kernels for patch size K.
 template <typename T, typename WT>
 cudaError_t latent_set_smem(int K, int bytes);
@@ -82,6 +86,8 @@ cudaError_t latent_bwd_set_smem(int K, int bytes);
                                                         bool, unsigned, unsigned, size_t, cudaStream_t);       \
     extern template void latent_reg_launch<T, WT>(const T*, const WT*, const T*, T*, T*, int, int, int, int, int, \
                                                   T, int, int, dim3, unsigned, size_t, cudaStream_t);          \
+    extern template void latent_monitor_launch<T, WT>(const LatentArgs<T, WT>&, int, dim3, unsigned, size_t,    \
+                                                      cudaStream_t);                                           \
     extern template cudaError_t latent_set_smem<T, WT>(int, int);                                             \
     extern template cudaError_t latent_batch_set_smem<T, WT>(int, int);                                       \
     extern template void latent_bwd_tma_launch<T, WT>(const LatentBwdArgs<T, WT>&, int, dim3, unsigned, size_t, \

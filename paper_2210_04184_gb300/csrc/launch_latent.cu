@@ -40,6 +40,13 @@ void latent_tma_batch_launch(const LatentArgs<T, WT>* args, const Segment* seg, 
 }
 
 template <typename T, typename WT>
+void latent_monitor_launch(const LatentArgs<T, WT>& a, int K, dim3 grid, unsigned threads, size_t smem,
+                           cudaStream_t s) {
+    constexpr int TVEC = 32 / sizeof(T);
+    with_k(K, [&](auto k) { latent_tma_monitor_kernel<T, WT, decltype(k)::value, TVEC><<<grid, threads, smem, s>>>(a); });
+}
+
+template <typename T, typename WT>
 void latent_reg_launch(const T* X, const WT* omega, const T* Sig, T* Sout, T* planes, int H, int W, int Ls, int S,
                        int Ty, T coef, int half, int K, dim3 grid, unsigned threads, size_t smem, cudaStream_t s) {
     constexpr int VEC = 16 / sizeof(T);
@@ -58,6 +65,7 @@ cudaError_t latent_set_smem(int K, int bytes) {
         constexpr int KK = decltype(k)::value;
         e = cudaFuncSetAttribute(latent_kernel<T, WT, KK, VEC>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, KK, TVEC>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_monitor_kernel<T, WT, KK, TVEC>, A, bytes);
         if constexpr (sizeof(T) == 4) {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(latent_tma_kernel<T, WT, KK, TVEC, int16_t>, A, bytes);
         }
@@ -85,6 +93,8 @@ cudaError_t latent_batch_set_smem(int K, int bytes) {
                                            cudaStream_t);                                                      \
     template void latent_tma_batch_launch<T, WT>(const LatentArgs<T, WT>*, const Segment*, int, int, int, bool,  \
                                                  unsigned, unsigned, size_t, cudaStream_t);                    \
+    template void latent_monitor_launch<T, WT>(const LatentArgs<T, WT>&, int, dim3, unsigned, size_t,            \
+                                               cudaStream_t);                                                  \
     template void latent_reg_launch<T, WT>(const T*, const WT*, const T*, T*, T*, int, int, int, int, int, T,    \
                                            int, int, dim3, unsigned, size_t, cudaStream_t);                    \
     template cudaError_t latent_set_smem<T, WT>(int, int);                                                      \

@@ -24,7 +24,7 @@ FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
 FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
 FUSE_OPT_HALF_WINDOW, FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS = 7, 8, 9, 10
 FUSE_OPT_GRAD_SEGMENT, FUSE_OPT_GRAD_WEIGHTS, FUSE_OPT_STATE_FORMAT = 11, 12, 13
-FUSE_OPT_X_UPDATE = 14
+FUSE_OPT_X_UPDATE, FUSE_OPT_RESIDUALS = 14, 15
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -72,6 +72,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_solve": (_ST, [_VP, _VP, _VP, _I, _I, _VP, _VP]),
         "fuse_run_host": (_ST, [_VP, _VP, _VP, _VP, _I, _VP, _VP]),
         "fuse_objective": (_ST, [_VP, _VP, _VP, _D]),
+        "fuse_residuals": (_ST, [_VP, _D]),
         "fuse_state_bytes": (_ST, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
         "fuse_get_state": (_ST, [_VP, _VP]),
         "fuse_set_state": (_ST, [_VP, _VP]),
@@ -96,6 +97,7 @@ def load(path: str | pathlib.Path | None = None):
         "fuse_batch_run_host": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                                       ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
         "fuse_batch_set_option": (_ST, [_VP, _I, ctypes.c_longlong]),
+        "fuse_batch_get_option": (_ST, [_VP, _I, ctypes.POINTER(ctypes.c_longlong)]),
         "fuse_batch_profile": (_ST, [_VP, _I, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
         "fuse_batch_sync": (_ST, [_VP]),
         "fuse_batch_destroy": (_ST, [_VP]),
@@ -191,6 +193,12 @@ def fuse_objective(ctx, Yl_dev: int, Yh_dev: int) -> np.ndarray:
     out = np.zeros(4)
     _check(load().fuse_objective(ctx, _VP(Yl_dev), _VP(Yh_dev), out.ctypes.data_as(_D)), ctx)
     return out
+
+
+def fuse_residuals(ctx) -> tuple[float, float]:
+    out = np.zeros(2)
+    _check(load().fuse_residuals(ctx, out.ctypes.data_as(_D)), ctx)
+    return float(out[0]), float(out[1])
 
 
 def fuse_state_bytes(ctx) -> int:
@@ -330,6 +338,12 @@ def fuse_batch_set_option(b, option: int, value: int):
     _bcheck(load().fuse_batch_set_option(b, option, value), b)
 
 
+def fuse_batch_get_option(b, option: int) -> int:
+    v = ctypes.c_longlong(0)
+    _bcheck(load().fuse_batch_get_option(b, option, ctypes.byref(v)), b)
+    return v.value
+
+
 def fuse_batch_profile(b, which: int, reset: bool = False):
     ms = ctypes.c_double(0.0)
     n = ctypes.c_longlong(0)
@@ -441,6 +455,12 @@ class Fusion:
         yh = self._t(Yh, (self.L_h, self.H, self.W))
         self._sync_stream()
         return fuse_objective(self.ctx, yl.data_ptr(), yh.data_ptr())
+
+    def residuals(self):
+        """(primal, dual) ADMM residual norms of the last iteration of the last solve (run with
+        FUSE_OPT_RESIDUALS = 1)."""
+        self._sync_stream()
+        return fuse_residuals(self.ctx)
 
     def get_state(self):
         nb = fuse_state_bytes(self.ctx)
@@ -593,6 +613,12 @@ class FusionBatch:
 
     def set_option(self, option, value):
         fuse_batch_set_option(self.b, option, value)
+
+    def latent_shape(self):
+        """The batch's latent launch shape (consumer threads, ring slots, bands per block)."""
+        return {k: fuse_batch_get_option(self.b, v) for k, v in
+                (("latent_threads", FUSE_OPT_LATENT_THREADS), ("latent_stages", FUSE_OPT_LATENT_STAGES),
+                 ("latent_bands", FUSE_OPT_LATENT_BANDS))}
 
     def profile(self, which=FUSE_K_LATENT, reset=False):
         return fuse_batch_profile(self.b, which, reset)
