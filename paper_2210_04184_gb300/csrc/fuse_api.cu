@@ -419,7 +419,8 @@ bool latent_tma_shape(fuse_ctx* c) {
     const int ncons = ((tpr * Ty + 31) / 32) * 32;
     if (ncons + 32 > 288) return false;
     const size_t ssz = c->sfmt ? 2 : c->esz;     // bytes of one stored state element
-    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz + (size_t)(2 * c->S + 1) * Ty * c->W * c->esz +
+    // ring, two H tiles, the X tiles Xs and Xo and the V tile (see latent_tma_body), mbarriers
+    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz + 5 * (size_t)Ty * c->W * c->esz +
                         2 * (size_t)c->lat_stages * 8;
     if (smem > (size_t)kMaxSmem || c->lat_stages < 1) return false;
     c->lt_Ty = Ty;
@@ -561,7 +562,7 @@ struct Impl {
         a.mplanes = (T*)c->mPm;
         a.mpart = c->mon_part;
         c->mon_lat = (size_t)grid.x * grid.y * grid.z;
-        const size_t smem = c->lt_smem + (size_t)(2 * c->S + 1) * c->lt_Ty * c->W * sizeof(T);
+        const size_t smem = c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * sizeof(T);     // two more tiles
         latent_monitor_launch<T, WT>(a, c->K, grid, (unsigned)(c->lt_ncons + 32), smem, s);
     }
 
@@ -779,7 +780,7 @@ fuse_status monitored_iteration(fuse_ctx* c, bool zero_in) {
     if (c->lat_impl != 1 || c->sfmt != 0 || c->xmode != 0)
         return fail(c, FUSE_EUNSUPPORTED, "the residual monitor needs the bulk-copy latent pass, the state in the "
                                           "iterate type and the paper's splitting");
-    if (c->lt_smem + (size_t)(2 * c->S + 1) * c->lt_Ty * c->W * c->esz > (size_t)kMaxSmem)
+    if (c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * c->esz > (size_t)kMaxSmem)
         return fail(c, FUSE_EUNSUPPORTED, "the monitoring latent pass does not fit shared memory");
     const size_t img = c->n * c->Ls * c->esz;
     cudaStream_t s = c->stream;
@@ -1004,6 +1005,7 @@ struct fuse_batch {
     int device = 0;
     fuse_dtype dtype = FUSE_F32, wdtype = FUSE_F32;
     int K = 0, S = 0, Ls = 0, bh = 1, bw = 1, half = 1, sfmt = 0;
+    bool same_taps = false;     // every problem has the same blur taps
     // launch shapes shared by all problems
     int lat_target = 256, lat_stages = 6, lat_ncons = 0, lat_bpb = 2;
     size_t lat_smem = 0, st_smem = 0, fr_smem = 0, fc_smem = 0, px_smem = 0;
@@ -1091,7 +1093,7 @@ struct BatchImpl {
             fuse_ctx* c = b->ctx[i];
             la[i] = Impl<T>::template lat_args<WT>(c, Ty[i], b->lat_ncons, b->lat_stages, b->lat_bpb);
             const size_t ssz = b->sfmt ? 2 : esz;
-            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz + (size_t)side * Ty[i] * c->W * esz +
+            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz + 5 * (size_t)Ty[i] * c->W * esz +
                               2 * (size_t)b->lat_stages * 8;
             if (sm > b->lat_smem) b->lat_smem = sm;
         }
@@ -1177,13 +1179,16 @@ struct BatchImpl {
     // One batched ADMM iteration: 7 launches cover every problem.  zero_in: the latent state of
     // every problem is zero on entry (first iteration of the solve) and is not read.
     static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false) {
+        // square blurs shared by every problem: taps in the argument space (from problem 0)
+        const fuse_ctx* c0 = b->ctx[0];
+        const bool sq = b->bh == b->bw && b->same_taps;
         stencil_batch_launch<T, 1>((const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg, b->bh,
-                                   (unsigned)b->st_blocks, b->st_smem, s);
+                                   sq ? c0->htapsT.data() : nullptr, (unsigned)b->st_blocks, b->st_smem, s);
         fft_batch_kernel<T, 0><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
         fft_batch_kernel<T, 1><<<b->fc_blocks, 256, b->fc_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fc_seg, b->fc_nseg);
         fft_batch_kernel<T, 2><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
         stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
-                                   (unsigned)b->st_blocks, b->st_smem, s);
+                                   sq ? c0->htapsB.data() : nullptr, (unsigned)b->st_blocks, b->st_smem, s);
         pixel_batch_launch<T>((const PixelArgs<T>*)b->d_px, b->d_px_seg, b->px_nseg, b->Ls, (unsigned)b->px_blocks,
                               b->px_smem, s);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1996,6 +2001,9 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
     b->dtype = c0->dtype; b->wdtype = c0->wdtype;
     b->K = c0->K; b->S = c0->S; b->Ls = c0->Ls; b->bh = c0->bh; b->bw = c0->bw; b->half = c0->half;
     b->sfmt = c0->sfmt;
+    b->same_taps = true;
+    for (fuse_ctx* c : b->ctx)
+        if (c->htapsT != c0->htapsT) b->same_taps = false;
     b->fc_cw = c0->dtype == FUSE_F64 ? 4 : 8;
     if (cudaSetDevice(b->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -172,14 +172,40 @@ __device__ __forceinline__ void consumer_barrier(int ncons) {
     asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
 }
 
+// The weights of one row of the patch window for a thread's VEC pixels: omega at columns
+// x0 - K .. x0 + VEC - 1 + K of one weight row (circular), the middle VEC in one aligned vector
+// load and the K on each side as single loads.  Loaded one row ahead of its use.
+template <typename WT, int VEC, int K>
+struct WRow {
+    vecT<WT, VEC> mid;
+    WT lo[K > 0 ? K : 1], hi[K > 0 ? K : 1];
+    __device__ __forceinline__ void load(const WT* __restrict__ row, int x0, int W) {
+        mid = *reinterpret_cast<const vecT<WT, VEC>*>(row + x0);
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            lo[i] = row[wrap1(x0 - K + i, W)];
+            hi[i] = row[wrap1(x0 + VEC + i, W)];
+        }
+    }
+    // weight at column x0 - K + j (j in [0, VEC + 2K))
+    __device__ __forceinline__ auto get(int j) const {
+        return wconv(j < K ? lo[j] : (j < K + VEC ? mid.v[j - K] : hi[j - K - VEC]));
+    }
+};
+
 // Block (bx, g, row) of one problem: rows [bx*Ty, bx*Ty + Ty), bands [g*bpb, g*bpb + bpb),
 // tau1 row `row`.  The bands are processed one after the other while the producer keeps the
-// ring full; between bands the consumers meet at a named barrier (the producer never waits on
-// it) to form and store that band's adjoint partial sums.
+// ring full.  Per band the consumers stage their X values X(m) (Xo) and the row segment
+// X(m - (tau1, 0)) (Xs) in shared memory, so delta = X(m) - X(m - tau) comes from shared memory
+// for every tau2; per tau2 each consumer adds its H_tau to A in registers and publishes it in one
+// of two shared tiles (alternating), and after one named barrier (the producer never waits on it)
+// adds the shifted H_tau(m + (0, tau2)) of its row to its entries of the V tile (Vs).
+// Shared memory: ring [D][Ty][W] (storage type), then [2][Ty][W] H tiles, [Ty][W] Xs, Xo and Vs,
+// and with MON [2][Ty][W] tiles of the monitoring sums (all of T), then the 2D mbarriers.
 // MON (monitoring instance, the last iteration of a solve whose residuals are wanted) also forms
-// the adjoint sums of Q' + Sigma = v + Sigma' + Sigma (into args.mplanes, from a second Hs
-// region) and the block's sum of (Sigma' - Sigma)^2 (into args.mpart): the latent parts of the
-// ADMM dual and primal residuals (Sec. IV, eq. dualvar3_main: D X - Q' = Sigma - Sigma').
+// the adjoint sums of Q' + Sigma = v + Sigma' + Sigma (into args.mplanes) and the block's sum of
+// (Sigma' - Sigma)^2 (into args.mpart): the latent parts of the ADMM dual and primal residuals
+// (Sec. IV, eq. dualvar3_main: D X - Q' = Sigma - Sigma').
 template <typename T, typename WT, int K, int VEC, typename ST, bool MON = false>
 __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, int bx, int g, int row,
                                                 unsigned char* smem_tma) {
@@ -198,9 +224,13 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int side = 2 * S + 1;
     const int tile = Ty * W;
     ST* ring = reinterpret_cast<ST*>(smem_tma);               // [D][Ty][W] of the storage type
-    T* Hs = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [(2S+1)][Ty][W]
-    constexpr int NHS = MON ? 2 : 1;                           // MON: Hs2 = Hs + side * tile
-    uint64_t* full = reinterpret_cast<uint64_t*>(Hs + (size_t)NHS * side * tile);
+    T* Hb = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [2][Ty][W]
+    T* Xs = Hb + (size_t)2 * tile;                            // [Ty][W]
+    T* Xo = Xs + tile;                                        // [Ty][W]
+    T* Vs = Xo + tile;                                        // [Ty][W]
+    T* Mb = Vs + tile;                                        // MON only: [2][Ty][W]
+    constexpr int NT = MON ? 7 : 5;
+    uint64_t* full = reinterpret_cast<uint64_t*>(Hb + (size_t)NT * tile);
     uint64_t* empty = full + D;
     __shared__ volatile int s_abort;
 
@@ -266,46 +296,69 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int y = y0 + r;
     const bool owner = tid < tpr * Ty;
     const bool active = owner && r < rows;
-    const size_t xsrow = (size_t)wrap1(y - t1, H) * W;   // row of X(m - tau)
     const size_t pix = (size_t)y * W + x0;
     const size_t kstride = (size_t)Ls * n;
+    const size_t xsrow = (size_t)wrap1(y - t1, H) * W;   // row of X(m - tau) (active threads)
     int slot = 0;
     unsigned par = 0;
-    T* Hs2 = Hs + (size_t)side * tile;                   // MON only
+    unsigned lim = limit;                                // 64 polls once a wait has timed out
+    int hb = 0;                                          // H tile written next
     double dsq = 0.0;                                    // MON only: sum of (Sigma' - Sigma)^2
     for (int item = 0; item < nb; ++item) {
         const int c = c0 + item;
         const T* Xc = X + (size_t)c * n;
-        T Xm[VEC];
-        if (active) vload<T, VEC>(Xc + pix, Xm);
+        T* xo = Xo + (size_t)r * W + x0;
+        T* vs = Vs + (size_t)r * W + x0;
+        if (active) {
+            T xr[VEC];
+            vload<T, VEC>(Xc + pix, xr);
+            vstore<T, VEC>(xo, xr);
+            vload<T, VEC>(Xc + xsrow + x0, xr);
+            vstore<T, VEC>(Xs + (size_t)r * W + x0, xr);
 #pragma unroll
-        for (int j = 0; j < VEC; ++j)
-            if (!active) Xm[j] = T(0);
+            for (int j = 0; j < VEC; ++j) xr[j] = T(0);
+            vstore<T, VEC>(vs, xr);
+        }
+        consumer_barrier(ncons);                 // Xs holds the band's shifted rows
+        T A[VEC];
+        T A2[MON ? VEC : 1], V2[MON ? VEC : 1];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            A[j] = T(0);
+            if constexpr (MON) { A2[j] = T(0); V2[j] = T(0); }
+        }
+        WRow<WT, VEC, K> wr;
+        if (active) wr.load(omega + (size_t)tm.w_index(t1, tm.t2_of(t1, 0)) * n + (size_t)wrap1(y - K, H) * W, x0, W);
         for (int jt = 0; jt < nt2; ++jt) {
             const int t2 = tm.t2_of(t1, jt);
             T Hacc[VEC], delta[VEC];
             T Macc[MON ? VEC : 1];
+            if (active) vload<T, VEC>(xo, delta);
 #pragma unroll
             for (int j = 0; j < VEC; ++j) {
                 Hacc[j] = T(0);
                 if constexpr (MON) Macc[j] = T(0);
-                delta[j] = active ? Xm[j] - Xc[xsrow + wrap1(x0 + j - t2, W)] : T(0);
+                delta[j] = active ? delta[j] - Xs[(size_t)r * W + wrap1(x0 + j - t2, W)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
+            const WT* om_next = jt + 1 < nt2 ? omega + (size_t)tm.w_index(t1, tm.t2_of(t1, jt + 1)) * n : om;
             ST* gp = Sout + ((size_t)tm.s_index(t1, t2) * NP * Ls + c) * n + pix;
 #pragma unroll
             for (int k1 = 0; k1 < PS; ++k1) {
-                const WT* orow = om + (size_t)wrap1(y + k1 - K, H) * W;     // weight row y + k1
                 if constexpr (std::is_same<ST, T>::value) {
                     T mu[VEC + 2 * K];
 #pragma unroll
-                    for (int j = 0; j < VEC + 2 * K; ++j)
-                        mu[j] = active ? coef * (T)wload(orow + wrap1(x0 - K + j, W)) : T(0);
+                    for (int j = 0; j < VEC + 2 * K; ++j) mu[j] = active ? coef * (T)wr.get(j) : T(0);
+                    // the next weight row: row k1 + 1, or the first row of the next tau2
+                    if (active) {
+                        if (k1 + 1 < PS) wr.load(om + (size_t)wrap1(y + k1 + 1 - K, H) * W, x0, W);
+                        else if (jt + 1 < nt2) wr.load(om_next + (size_t)wrap1(y - K, H) * W, x0, W);
+                    }
 #pragma unroll
                     for (int k2 = 0; k2 < PS; ++k2) {
-                        if (!zin) {
-                            const unsigned lim = s_abort ? 64u : limit;
-                            if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (!zin && !mbar_wait(&full[slot], par, lim, err, 1)) {
+                            s_abort = 1;
+                            lim = 64u;
                         }
                         if (active) {
                             T sv[VEC];
@@ -340,19 +393,25 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 } else {
                     // 16-bit fixed point (see FixedCode): the update runs in code units of mu/32767,
                     // where the clamp bounds are +-32767 and the new code is the clamped value
-                    // rounded by one addition; G returns to real units through mu/32767.
+                    // rounded by one addition; G returns to real units through mu/32767.  Per
+                    // weight column: inv = 32767/mu (code units per real unit), sc = mu/32767.
                     static_assert(VEC == 8, "one 16-byte group of codes per thread and chunk");
-                    float mu[VEC + 2 * K];
+                    float inv[VEC + 2 * K], sc[VEC + 2 * K];
 #pragma unroll
                     for (int j = 0; j < VEC + 2 * K; ++j) {
-                        const float w = active ? (float)wload(orow + wrap1(x0 - K + j, W)) : 0.0f;
-                        mu[j] = fmaxf(coef * w, FixedCode::kMinMu);
+                        const float m = active ? fmaxf(coef * (float)wr.get(j), FixedCode::kMinMu) : 1.0f;
+                        inv[j] = __fdividef(FixedCode::kLevels, m);
+                        sc[j] = m * FixedCode::kStep;
+                    }
+                    if (active) {
+                        if (k1 + 1 < PS) wr.load(om + (size_t)wrap1(y + k1 + 1 - K, H) * W, x0, W);
+                        else if (jt + 1 < nt2) wr.load(om_next + (size_t)wrap1(y - K, H) * W, x0, W);
                     }
 #pragma unroll
                     for (int k2 = 0; k2 < PS; ++k2) {
-                        if (!zin) {
-                            const unsigned lim = s_abort ? 64u : limit;
-                            if (!mbar_wait(&full[slot], par, lim, err, 1)) s_abort = 1;
+                        if (!zin && !mbar_wait(&full[slot], par, lim, err, 1)) {
+                            s_abort = 1;
+                            lim = 64u;
                         }
                         if (active) {
                             // code 0 stands for 0
@@ -365,16 +424,14 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                                 // the two codes of a word are updated together with the paired
                                 // FP32 instructions (same rounding as the scalar ones)
                                 const int j0 = 2 * h, j1 = 2 * h + 1;
-                                const float2 m = make_float2(mu[j0 + k2], mu[j1 + k2]);
                                 const float2 q = FixedCode::decode2(wd[h]);
-                                const float2 inv = make_float2(__fdividef(FixedCode::kLevels, m.x),
-                                                               __fdividef(FixedCode::kLevels, m.y));
-                                const float2 uc = __ffma2_rn(make_float2(-delta[j0], -delta[j1]), inv, q);  // Sigma - D X
+                                const float2 uc = __ffma2_rn(make_float2(-delta[j0], -delta[j1]),
+                                                             make_float2(inv[j0 + k2], inv[j1 + k2]), q);  // Sigma - D X
                                 const float2 s2c = make_float2(fminf(fmaxf(uc.x, -FixedCode::kLevels), FixedCode::kLevels),
                                                                fminf(fmaxf(uc.y, -FixedCode::kLevels), FixedCode::kLevels));
                                 const float2 g2 = __ffma2_rn(make_float2(2.0f, 2.0f), s2c, make_float2(-uc.x, -uc.y));
-                                const float2 sc = __fmul2_rn(m, make_float2(FixedCode::kStep, FixedCode::kStep));
-                                const float2 hacc = __ffma2_rn(g2, sc, make_float2(Hacc[j0], Hacc[j1]));
+                                const float2 hacc = __ffma2_rn(g2, make_float2(sc[j0 + k2], sc[j1 + k2]),
+                                                               make_float2(Hacc[j0], Hacc[j1]));
                                 Hacc[j0] = hacc.x;
                                 Hacc[j1] = hacc.y;
                                 out[h] = FixedCode::pack2(s2c);
@@ -390,55 +447,52 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                     }
                 }
             }
+            // A += H_tau; publish H_tau so the row can form V(m) += H_tau(m + (0, tau2))
+            T* ht = Hb + (size_t)hb * tile + (size_t)r * W;
+            T* mt = Mb + (size_t)hb * tile + (size_t)r * W;
             if (owner) {
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) Hs[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Hacc[j];
-                if constexpr (MON) {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) Hs2[((size_t)(t2 + S) * Ty + r) * W + x0 + j] = Macc[j];
-                }
-            }
-        }
-        consumer_barrier(ncons);                 // every H_tau of this band is in Hs
-        if (active) {
-            T A[VEC], V[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) { A[j] = T(0); V[j] = T(0); }
-            for (int jt = 0; jt < nt2; ++jt) {
-                const int t2 = tm.t2_of(t1, jt);
-                const T* hrow = Hs + ((size_t)(t2 + S) * Ty + r) * W;
-#pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    A[j] += hrow[x0 + j];
-                    V[j] += hrow[wrap1(x0 + j + t2, W)];
-                }
-            }
-            vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
-            vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
-            if constexpr (MON) {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) { A[j] = T(0); V[j] = T(0); }
-                for (int jt = 0; jt < nt2; ++jt) {
-                    const int t2 = tm.t2_of(t1, jt);
-                    const T* hrow = Hs2 + ((size_t)(t2 + S) * Ty + r) * W;
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j) {
-                        A[j] += hrow[x0 + j];
-                        V[j] += hrow[wrap1(x0 + j + t2, W)];
+                    A[j] += Hacc[j];
+                    ht[x0 + j] = Hacc[j];
+                    if constexpr (MON) {
+                        A2[j] += Macc[j];
+                        mt[x0 + j] = Macc[j];
                     }
                 }
-                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
-                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V);
+            }
+            // the other H tile was last read before this barrier's previous crossing
+            consumer_barrier(ncons);
+            if (active) {
+                T v[VEC];
+                vload<T, VEC>(vs, v);
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    v[j] += ht[wrap1(x0 + j + t2, W)];
+                    if constexpr (MON) V2[j] += mt[wrap1(x0 + j + t2, W)];
+                }
+                vstore<T, VEC>(vs, v);
+            }
+            hb ^= 1;
+        }
+        if (active) {
+            T v[VEC];
+            vload<T, VEC>(vs, v);
+            vstore<T, VEC>(planes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A);
+            vstore<T, VEC>(planes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, v);
+            if constexpr (MON) {
+                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + (t1 + S)) * n + pix, A2);
+                vstore<T, VEC>(args.mplanes + ((size_t)c * 2 * side + side + (t1 + S)) * n + pix, V2);
             }
         }
-        if (item + 1 < nb) consumer_barrier(ncons);   // Hs is read before the next band rewrites it
+        // Xs is rewritten by the next band only after every thread has crossed the last tau2's
+        // barrier, that is after every read of it (Xo and Vs are read by their owner only)
     }
     if constexpr (MON) {
         // the block's sum of (Sigma' - Sigma)^2 over its consumers, in a fixed order
         __shared__ double s_red[8];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsq += __shfl_down_sync(0xffffffffu, dsq, o);
-        consumer_barrier(ncons);                 // the last band's reads of Hs are done
         if (lane == 0) s_red[tid >> 5] = dsq;
         consumer_barrier(ncons);
         if (tid == 0) {
@@ -450,7 +504,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
 }
 
 template <typename T, typename WT, int K, int VEC, typename ST = T>
-__global__ void __launch_bounds__(288, 2) latent_tma_kernel(LatentArgs<T, WT> args) {
+__global__ void __maxnreg__(112) latent_tma_kernel(LatentArgs<T, WT> args) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     latent_tma_body<T, WT, K, VEC, ST>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
 }
@@ -467,7 +521,7 @@ __global__ void __launch_bounds__(288, 1) latent_tma_monitor_kernel(LatentArgs<T
 // by the segment table; every problem's launch shape fits the common block size and shared
 // memory size of the launch.  zero_in applies to every problem (see LatentArgs).
 template <typename T, typename WT, int K, int VEC, typename ST = T>
-__global__ void __launch_bounds__(288, 2)
+__global__ void __maxnreg__(112)
 latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
                         int zero_in) {
     extern __shared__ __align__(128) unsigned char smem_tma[];

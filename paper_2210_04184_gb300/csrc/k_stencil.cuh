@@ -106,16 +106,16 @@ struct SquareTaps {
     T t[B * B];
 };
 
+// Block (bx, by, c): the 32 x 32 tile at columns 32 bx, rows 32 by of band c.
 template <typename T, int MODE, int B>
-__global__ void __launch_bounds__(256) stencil_sq_kernel(StencilArgs<T> a, SquareTaps<T, B> taps) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void stencil_sq_body(const StencilArgs<T>& a, const SquareTaps<T, B>& taps, int bx, int by,
+                                                int c, unsigned char* smem_raw) {
     constexpr int QY = ST_TY / ST_BY;
     constexpr int NR = B + QY - 1;
     constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, R = B / 2;
     const int H = a.H, W = a.W;
-    const int c = blockIdx.z;
     T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TW]
-    const int x0 = blockIdx.x * ST_TX, y0 = blockIdx.y * ST_TY;
+    const int x0 = bx * ST_TX, y0 = by * ST_TY;
     const T* __restrict__ inc = a.in + (size_t)c * H * W;
     for (int rr = threadIdx.y; rr < TH; rr += ST_BY) {
         const T* row = inc + (size_t)wrapc(y0 - R + rr, H) * W;
@@ -141,6 +141,25 @@ __global__ void __launch_bounds__(256) stencil_sq_kernel(StencilArgs<T> a, Squar
         }
     }
     stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
+}
+
+template <typename T, int MODE, int B>
+__global__ void __launch_bounds__(256) stencil_sq_kernel(StencilArgs<T> a, SquareTaps<T, B> taps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stencil_sq_body<T, MODE, B>(a, taps, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+// Batched square-blur stencil: every problem of a batch shares the blur, so the taps travel in
+// the argument space as in stencil_sq_kernel.
+template <typename T, int MODE, int B>
+__global__ void __launch_bounds__(256)
+stencil_sq_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
+                        SquareTaps<T, B> taps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const StencilArgs<T> a = args[prob];
+    stencil_sq_body<T, MODE, B>(a, taps, bx, by, bz, smem_raw);
 }
 
 // C = G + U2 + R without a blur: the right-hand side of the variant that keeps S B in the X

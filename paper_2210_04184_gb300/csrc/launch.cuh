@@ -55,8 +55,8 @@ template <typename T, int MODE>
 void stencil_launch(const StencilArgs<T>& a, int bh, const double* taps_host, dim3 grid, size_t smem,
                     cudaStream_t s);
 template <typename T, int MODE>
-void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, unsigned blocks,
-                          size_t smem, cudaStream_t s);
+void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* taps_host,
+                          unsigned blocks, size_t smem, cudaStream_t s);
 // Dynamic shared-memory cap of the stencil kernels for blur height bh and of the wide pixel kernel.
 template <typename T>
 cudaError_t pixel_stencil_set_smem(int bh, int bytes);
@@ -107,10 +107,10 @@ cudaError_t latent_bwd_set_smem(int K, int bytes);
                                               cudaStream_t);                                                  \
     extern template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, dim3, size_t,        \
                                               cudaStream_t);                                                  \
-    extern template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int, unsigned,  \
-                                                    size_t, cudaStream_t);                                    \
-    extern template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int, unsigned,  \
-                                                    size_t, cudaStream_t);                                    \
+    extern template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int,           \
+                                                    const double*, unsigned, size_t, cudaStream_t);           \
+    extern template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int,           \
+                                                    const double*, unsigned, size_t, cudaStream_t);           \
     extern template cudaError_t pixel_stencil_set_smem<T>(int, int);                                          \
     extern template cudaError_t stencil_batch_set_smem<T>(int, int);                                          \
     extern template void pixel_bwd_launch<T>(const PixelBwdArgs<T>&, unsigned, cudaStream_t);

@@ -42,8 +42,17 @@ void stencil_launch(const StencilArgs<T>& a, int bh, const double* taps_host, di
 }
 
 template <typename T, int MODE>
-void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, unsigned blocks,
-                          size_t smem, cudaStream_t s) {
+void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* taps_host,
+                          unsigned blocks, size_t smem, cudaStream_t s) {
+    if (taps_host) {
+        with_bh(bh, [&](auto b) {
+            constexpr int B = decltype(b)::value;
+            SquareTaps<T, B> tp;
+            for (int i = 0; i < B * B; ++i) tp.t[i] = (T)taps_host[i];
+            stencil_sq_batch_kernel<T, MODE, B><<<blocks, dim3(ST_TX, ST_BY), smem, s>>>(args, seg, nseg, tp);
+        });
+        return;
+    }
     with_bh(bh, [&](auto b) {
         stencil_batch_kernel<T, MODE, decltype(b)::value><<<blocks, dim3(ST_TX, ST_BY), smem, s>>>(args, seg, nseg);
     });
@@ -71,6 +80,8 @@ cudaError_t stencil_batch_set_smem(int bh, int bytes) {
         constexpr int B = decltype(b)::value;
         e = cudaFuncSetAttribute(stencil_batch_kernel<T, 0, B>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 1, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_batch_kernel<T, 0, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_batch_kernel<T, 1, B>, A, bytes);
     });
     return e;
 }
@@ -81,10 +92,10 @@ cudaError_t stencil_batch_set_smem(int bh, int bytes) {
                                         cudaStream_t);                                                          \
     template void stencil_launch<T, 0>(const StencilArgs<T>&, int, const double*, dim3, size_t, cudaStream_t);  \
     template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, dim3, size_t, cudaStream_t);  \
-    template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int, unsigned, size_t,  \
-                                             cudaStream_t);                                                     \
-    template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int, unsigned, size_t,  \
-                                             cudaStream_t);                                                     \
+    template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
+                                             unsigned, size_t, cudaStream_t);                                   \
+    template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
+                                             unsigned, size_t, cudaStream_t);                                   \
     template cudaError_t pixel_stencil_set_smem<T>(int, int);                                                   \
     template cudaError_t stencil_batch_set_smem<T>(int, int);
 

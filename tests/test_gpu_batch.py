@@ -146,3 +146,23 @@ def test_batch64_full_size_sampled():
     Xg = Xs[i].double().cpu().numpy()
     assert np.linalg.norm(Xg - nlpr.to_lhw(Xo)) / np.linalg.norm(Xo) <= 1e-5
     batch.close()
+
+
+def test_batch_with_different_blur_taps():
+    # problems with the same blur size but different taps (sigma 1.0 and 1.6): the batch falls back
+    # to the stencil that reads each problem's taps, and every problem equals its single solve
+    ps = [synth.make_problem(H=h, W=w, L_l=9, L_h=3, L_s=5, d=4, blur_size=5, blur_sigma=sg, K=1, S=2,
+                             lam1=1.0, lam2=1e-2, rho=5e-2, h=0.3, seed=300 + i)
+          for i, (h, w, sg) in enumerate([(40, 40, 1.0), (48, 64, 1.6), (32, 24, 1.0)])]
+    fs, yl, yh = _contexts(ps, "f32", "f32")
+    single = []
+    for f, a, b in zip(fs, yl, yh):
+        X, _ = f.solve(a, b, 9)
+        f.sync()
+        single.append(X.clone())
+    batch = FusionBatch(fs)
+    Xs, _ = batch.solve(yl, yh, 9)
+    batch.sync()
+    for X, Xb in zip(single, Xs):
+        assert torch.equal(X, Xb)
+    batch.close()

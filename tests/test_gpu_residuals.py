@@ -89,7 +89,7 @@ def test_residuals_fp64(iters, half):
 @pytest.mark.parametrize("case", ["base", "ratio2_identity", "odd_bands_k0"])
 def test_residuals_fp32(case):
     kw = {"base": {}, "ratio2_identity": dict(d=2, L_l=4, L_s=4, E_identity=True, K=1, S=2, H=40, W=40),
-          "odd_bands_k0": dict(L_s=5, K=0, S=2, W=56)}[case]
+          "odd_bands_k0": dict(L_s=5, K=0, S=2, W=40)}[case]
     p = small(**kw)
     om = nlpr.round_bf16(nlpr.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h))
     for iters in (2, 9):
