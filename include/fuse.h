@@ -115,13 +115,19 @@ enum {
                                     deviation <= 1e-6) and H, W with 2H+1 complex values per
                                     column fitting shared memory; not with the reverse pass or a
                                     batch (FUSE_EUNSUPPORTED).  Switching clears the ADMM state. */
-    FUSE_OPT_RESIDUALS = 15      /* 1: every fuse_solve with iters >= 1 runs its last iteration as a
+    FUSE_OPT_RESIDUALS = 15,     /* 1: every fuse_solve with iters >= 1 runs its last iteration as a
                                     monitored one (directly launched, about 1.5 times the work of
                                     an iteration) whose ADMM residual norms fuse_residuals returns;
                                     0 (default): off.  Needs the bulk-copy latent pass, the state in
                                     the iterate type and the paper's splitting (FUSE_EUNSUPPORTED
                                     otherwise).  The first switch to 1 allocates 4 images and 2
                                     adjoint-plane arrays of workspace. */
+    FUSE_OPT_SEPARABLE_BLUR = 16 /* 1 (default): a square blur whose taps factor as
+                                    b(u, v) = cu(u) cv(v) (to 1e-13 of the largest tap, checked at
+                                    fuse_init; a sampled Gaussian does) is applied as a horizontal
+                                    and a vertical pass (2B multiply-adds per output instead of
+                                    B^2; the same operator up to rounding); 0: always the 2D
+                                    stencil.  A batch follows its first context. */
 };
 
 /* Kernel groups for fuse_profile. */

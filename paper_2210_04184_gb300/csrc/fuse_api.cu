@@ -150,8 +150,10 @@ struct fuse_ctx {
     std::vector<double> hM1, hF, hER;
     // spectral condition numbers of A (eq. inv), E E^T + rho I and F^{-1} (fuse_conditioning)
     double cond[3] = {0.0, 0.0, 0.0};
-    // host copies of the blur taps (b for B^T, flipped b for B) for the square-blur stencil
-    std::vector<double> htapsT, htapsB;
+    // host copies of the blur taps (b for B^T, flipped b for B) for the square-blur stencil, and
+    // their factors cu (bh values) then cv when the taps are separable (empty otherwise)
+    std::vector<double> htapsT, htapsB, hsepT, hsepB;
+    int sep_blur = 1;           // FUSE_OPT_SEPARABLE_BLUR
     // latent state read / written by the next latent launch (NULL = Sig, in place); set only
     // around directly launched iterations of the taped forward, never while capturing
     void *lat_in = nullptr, *lat_out = nullptr;
@@ -271,6 +273,24 @@ void sym_eig_range(std::vector<double> A, int n, double* lo, double* hi) {
         *lo = std::min(*lo, A[(size_t)i * n + i]);
         *hi = std::max(*hi, A[(size_t)i * n + i]);
     }
+}
+
+// Factors of a separable square blur: taps(u, v) = cu[u] cv[v] up to rounding (1e-13 of the
+// largest tap), returned as cu[0..b) then cv[0..b); empty when the taps are not of rank one.
+std::vector<double> separable_factors(const std::vector<double>& t, int b) {
+    int am = 0, bm = 0;
+    double mx = 0.0;
+    for (int u = 0; u < b; ++u)
+        for (int v = 0; v < b; ++v)
+            if (std::fabs(t[(size_t)u * b + v]) > mx) { mx = std::fabs(t[(size_t)u * b + v]); am = u; bm = v; }
+    if (mx == 0.0) return {};
+    std::vector<double> f(2 * (size_t)b);
+    for (int u = 0; u < b; ++u) f[u] = t[(size_t)u * b + bm];
+    for (int v = 0; v < b; ++v) f[b + v] = t[(size_t)am * b + v] / t[(size_t)am * b + bm];
+    for (int u = 0; u < b; ++u)
+        for (int v = 0; v < b; ++v)
+            if (std::fabs(t[(size_t)u * b + v] - f[u] * f[b + v]) > 1e-13 * mx) return {};
+    return f;
 }
 
 bool invert(std::vector<double>& A, int n) {
@@ -419,8 +439,10 @@ bool latent_tma_shape(fuse_ctx* c) {
     const int ncons = ((tpr * Ty + 31) / 32) * 32;
     if (ncons + 32 > 288) return false;
     const size_t ssz = c->sfmt ? 2 : c->esz;     // bytes of one stored state element
-    // ring, two H tiles, the X tiles Xs and Xo and the V tile (see latent_tma_body), mbarriers
-    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz + 5 * (size_t)Ty * c->W * c->esz +
+    // ring, two H tiles and Xs at the padded pitch W + W/8, the tiles Xo and Vs (see
+    // latent_tma_body), mbarriers
+    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz +
+                        (3 * (size_t)Ty * (c->W + c->W / 8) + 2 * (size_t)Ty * c->W) * c->esz + 16 +
                         2 * (size_t)c->lat_stages * 8;
     if (smem > (size_t)kMaxSmem || c->lat_stages < 1) return false;
     c->lt_Ty = Ty;
@@ -494,9 +516,14 @@ struct Impl {
     template <int MODE>
     static void stencil_launch(fuse_ctx* c, cudaStream_t s, const StencilArgs<T>& a) {
         dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
-        const double* ht = nullptr;
-        if (c->bh == c->bw) ht = a.taps == (const T*)c->tapsB ? c->htapsB.data() : c->htapsT.data();
-        fuse::stencil_launch<T, MODE>(a, c->bh, ht, grid, c->st_smem, s);
+        const double *ht = nullptr, *sep = nullptr;
+        if (c->bh == c->bw) {
+            const bool isB = a.taps == (const T*)c->tapsB;
+            ht = isB ? c->htapsB.data() : c->htapsT.data();
+            const std::vector<double>& f = isB ? c->hsepB : c->hsepT;
+            if (c->sep_blur && !f.empty()) sep = f.data();
+        }
+        fuse::stencil_launch<T, MODE>(a, c->bh, sep, ht, grid, c->st_smem, s);
     }
 
     // MODE 0: out = B in (taps = flipped b); MODE 1: C = B^T U1 + U2 + R (taps = b).
@@ -562,7 +589,7 @@ struct Impl {
         a.mplanes = (T*)c->mPm;
         a.mpart = c->mon_part;
         c->mon_lat = (size_t)grid.x * grid.y * grid.z;
-        const size_t smem = c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * sizeof(T);     // two more tiles
+        const size_t smem = c->lt_smem + 2 * (size_t)c->lt_Ty * (c->W + c->W / 8) * sizeof(T);   // two more tiles
         latent_monitor_launch<T, WT>(a, c->K, grid, (unsigned)(c->lt_ncons + 32), smem, s);
     }
 
@@ -780,7 +807,7 @@ fuse_status monitored_iteration(fuse_ctx* c, bool zero_in) {
     if (c->lat_impl != 1 || c->sfmt != 0 || c->xmode != 0)
         return fail(c, FUSE_EUNSUPPORTED, "the residual monitor needs the bulk-copy latent pass, the state in the "
                                           "iterate type and the paper's splitting");
-    if (c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * c->esz > (size_t)kMaxSmem)
+    if (c->lt_smem + 2 * (size_t)c->lt_Ty * (c->W + c->W / 8) * c->esz > (size_t)kMaxSmem)
         return fail(c, FUSE_EUNSUPPORTED, "the monitoring latent pass does not fit shared memory");
     const size_t img = c->n * c->Ls * c->esz;
     cudaStream_t s = c->stream;
@@ -1093,7 +1120,8 @@ struct BatchImpl {
             fuse_ctx* c = b->ctx[i];
             la[i] = Impl<T>::template lat_args<WT>(c, Ty[i], b->lat_ncons, b->lat_stages, b->lat_bpb);
             const size_t ssz = b->sfmt ? 2 : esz;
-            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz + 5 * (size_t)Ty[i] * c->W * esz +
+            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz +
+                              (3 * (size_t)Ty[i] * (c->W + c->W / 8) + 2 * (size_t)Ty[i] * c->W) * esz + 16 +
                               2 * (size_t)b->lat_stages * 8;
             if (sm > b->lat_smem) b->lat_smem = sm;
         }
@@ -1182,13 +1210,16 @@ struct BatchImpl {
         // square blurs shared by every problem: taps in the argument space (from problem 0)
         const fuse_ctx* c0 = b->ctx[0];
         const bool sq = b->bh == b->bw && b->same_taps;
+        const bool sep = sq && c0->sep_blur && !c0->hsepT.empty();
         stencil_batch_launch<T, 1>((const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg, b->bh,
-                                   sq ? c0->htapsT.data() : nullptr, (unsigned)b->st_blocks, b->st_smem, s);
+                                   sep ? c0->hsepT.data() : nullptr, sq ? c0->htapsT.data() : nullptr,
+                                   (unsigned)b->st_blocks, b->st_smem, s);
         fft_batch_kernel<T, 0><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
         fft_batch_kernel<T, 1><<<b->fc_blocks, 256, b->fc_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fc_seg, b->fc_nseg);
         fft_batch_kernel<T, 2><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
         stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
-                                   sq ? c0->htapsB.data() : nullptr, (unsigned)b->st_blocks, b->st_smem, s);
+                                   sep ? c0->hsepB.data() : nullptr, sq ? c0->htapsB.data() : nullptr,
+                                   (unsigned)b->st_blocks, b->st_smem, s);
         pixel_batch_launch<T>((const PixelArgs<T>*)b->d_px, b->d_px_seg, b->px_nseg, b->Ls, (unsigned)b->px_blocks,
                               b->px_smem, s);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1468,6 +1499,10 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     if (!invert(M1, Ls) || !invert(Fm, Ls)) return bail(FUSE_EINVAL);
     c->htapsT = tT;
     c->htapsB = tB;
+    if (bh == bw) {
+        c->hsepT = separable_factors(tT, bh);
+        c->hsepB = separable_factors(tB, bh);
+    }
     c->hM1 = M1;
     c->hF = Fm;
     c->hER = ER;
@@ -1785,6 +1820,11 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             drop_graphs(c);
             return FUSE_OK;
         }
+        case FUSE_OPT_SEPARABLE_BLUR:
+            if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "separable blur is 0 or 1");
+            c->sep_blur = (int)value;
+            drop_graphs(c);
+            return FUSE_OK;
         case FUSE_OPT_RESIDUALS: {
             if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "residual monitor is 0 or 1");
             if (value == 1 && (c->xmode != 0 || c->sfmt != 0 || c->lat_impl != 1))
@@ -1940,6 +1980,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_GRAD_WEIGHTS: *value = c->grad_weights; return FUSE_OK;
         case FUSE_OPT_X_UPDATE: *value = c->xmode; return FUSE_OK;
         case FUSE_OPT_RESIDUALS: *value = c->monitor; return FUSE_OK;
+        case FUSE_OPT_SEPARABLE_BLUR: *value = c->sep_blur; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }

@@ -162,6 +162,87 @@ stencil_sq_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* 
     stencil_sq_body<T, MODE, B>(a, taps, bx, by, bz, smem_raw);
 }
 
+// Separable square blurs, b(u, v) = cu(u) cv(v) (a sampled Gaussian, for example): the B x B
+// stencil as a horizontal pass over the haloed tile, hs(r, x) = sum_v cv(v) tile(r, x + v) (rows
+// with the vertical halo, four consecutive columns per work item), then a vertical pass with QY
+// outputs per thread, out = sum_u cu(u) hs(y + u, x): 2B multiply-adds per output instead of B^2
+// (plus the halo rows of the first pass).  Shared memory: the tile at an odd pitch (TW | 1, so the
+// four-column items of a warp hit distinct banks), then hs at pitch ST_TX + 1.
+template <typename T, int B>
+struct SepTaps {
+    T cu[B], cv[B];
+};
+
+template <typename T, int B>
+constexpr size_t stencil_sep_smem() {
+    return ((size_t)(ST_TY + B - 1) * ((ST_TX + B - 1) | 1) + (size_t)(ST_TY + B - 1) * (ST_TX + 1)) * sizeof(T);
+}
+
+template <typename T, int MODE, int B>
+__device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const SepTaps<T, B>& tp, int bx, int by,
+                                                 int c, unsigned char* smem_raw) {
+    constexpr int QY = ST_TY / ST_BY;
+    constexpr int R = B / 2;
+    constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, TP = TW | 1, HP = ST_TX + 1;
+    constexpr int CG = ST_TX / 4;                     // four-column groups per row
+    const int H = a.H, W = a.W;
+    T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TP]
+    T* hs = tile + TH * TP;                           // [TH][HP]
+    const int x0 = bx * ST_TX, y0 = by * ST_TY;
+    const T* __restrict__ inc = a.in + (size_t)c * H * W;
+    for (int rr = threadIdx.y; rr < TH; rr += ST_BY) {
+        const T* row = inc + (size_t)wrapc(y0 - R + rr, H) * W;
+        for (int cc = threadIdx.x; cc < TW; cc += ST_TX) tile[rr * TP + cc] = row[wrapc(x0 - R + cc, W)];
+    }
+    __syncthreads();
+    const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    for (int it = tid; it < TH * CG; it += ST_TX * ST_BY) {
+        const int r = it / CG, x = (it - r * CG) * 4;
+        T w[4 + B - 1];
+#pragma unroll
+        for (int k = 0; k < 4 + B - 1; ++k) w[k] = tile[r * TP + x + k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T acc = T(0);
+#pragma unroll
+            for (int v = 0; v < B; ++v) acc += tp.cv[v] * w[q + v];
+            hs[r * HP + x + q] = acc;
+        }
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    const int ly0 = threadIdx.y * QY;
+    T col[QY + B - 1];
+#pragma unroll
+    for (int k = 0; k < QY + B - 1; ++k) col[k] = hs[(ly0 + k) * HP + threadIdx.x];
+    T acc[QY];
+#pragma unroll
+    for (int q = 0; q < QY; ++q) {
+        acc[q] = T(0);
+#pragma unroll
+        for (int u = 0; u < B; ++u) acc[q] += tp.cu[u] * col[q + u];
+    }
+    stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
+}
+
+template <typename T, int MODE, int B>
+__global__ void __launch_bounds__(256) stencil_sep_kernel(StencilArgs<T> a, SepTaps<T, B> taps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stencil_sep_body<T, MODE, B>(a, taps, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+}
+
+template <typename T, int MODE, int B>
+__global__ void __launch_bounds__(256)
+stencil_sep_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
+                         SepTaps<T, B> taps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int prob, bx, by, bz;
+    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
+    const StencilArgs<T> a = args[prob];
+    stencil_sep_body<T, MODE, B>(a, taps, bx, by, bz, smem_raw);
+}
+
 // C = G + U2 + R without a blur: the right-hand side of the variant that keeps S B in the X
 // system, where the data term G = B^T S^T Y_l E^T / rho is fixed for the whole solve and
 // precomputed once (in = G).  Same tiles and epilogue as the stencils.

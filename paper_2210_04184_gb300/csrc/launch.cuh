@@ -48,15 +48,17 @@ void pixel_launch(const PixelArgs<T>& a, unsigned blocks, unsigned threads, size
 template <typename T>
 void pixel_batch_launch(const PixelArgs<T>* args, const Segment* seg, int nseg, int Ls, unsigned blocks,
                         size_t smem, cudaStream_t s);
-// Blur stencil (MODE 0: B in; MODE 1: right-hand side).  taps_host: the bh x bw taps in FP64 when
-// bh == bw (the square kernel takes them as arguments), else NULL (generic kernel, taps read
-// from a.taps).
+// Blur stencil (MODE 0: B in; MODE 1: right-hand side).  sep_host: for a separable square blur,
+// its factors in FP64, cu[bh] then cv[bh] (taps(u, v) = cu[u] cv[v]; separable kernel), else NULL;
+// taps_host: the bh x bw taps in FP64 when bh == bw (the square kernel takes them as arguments),
+// else NULL (generic kernel, taps read from a.taps).  smem: the 2D kernels' dynamic shared memory
+// (the separable kernel sizes its own).
 template <typename T, int MODE>
-void stencil_launch(const StencilArgs<T>& a, int bh, const double* taps_host, dim3 grid, size_t smem,
-                    cudaStream_t s);
+void stencil_launch(const StencilArgs<T>& a, int bh, const double* sep_host, const double* taps_host, dim3 grid,
+                    size_t smem, cudaStream_t s);
 template <typename T, int MODE>
-void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* taps_host,
-                          unsigned blocks, size_t smem, cudaStream_t s);
+void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* sep_host,
+                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s);
 // Dynamic shared-memory cap of the stencil kernels for blur height bh and of the wide pixel kernel.
 template <typename T>
 cudaError_t pixel_stencil_set_smem(int bh, int bytes);
@@ -103,14 +105,16 @@ cudaError_t latent_bwd_set_smem(int K, int bytes);
     extern template void pixel_launch<T>(const PixelArgs<T>&, unsigned, unsigned, size_t, cudaStream_t);     \
     extern template void pixel_batch_launch<T>(const PixelArgs<T>*, const Segment*, int, int, unsigned, size_t, \
                                                cudaStream_t);                                                 \
-    extern template void stencil_launch<T, 0>(const StencilArgs<T>&, int, const double*, dim3, size_t,        \
-                                              cudaStream_t);                                                  \
-    extern template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, dim3, size_t,        \
-                                              cudaStream_t);                                                  \
+    extern template void stencil_launch<T, 0>(const StencilArgs<T>&, int, const double*, const double*, dim3,  \
+                                              size_t, cudaStream_t);                                          \
+    extern template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, const double*, dim3,  \
+                                              size_t, cudaStream_t);                                          \
     extern template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int,           \
-                                                    const double*, unsigned, size_t, cudaStream_t);           \
+                                                    const double*, const double*, unsigned, size_t,           \
+                                                    cudaStream_t);                                            \
     extern template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int,           \
-                                                    const double*, unsigned, size_t, cudaStream_t);           \
+                                                    const double*, const double*, unsigned, size_t,           \
+                                                    cudaStream_t);                                            \
     extern template cudaError_t pixel_stencil_set_smem<T>(int, int);                                          \
     extern template cudaError_t stencil_batch_set_smem<T>(int, int);                                          \
     extern template void pixel_bwd_launch<T>(const PixelBwdArgs<T>&, unsigned, cudaStream_t);

@@ -25,8 +25,27 @@ void pixel_batch_launch(const PixelArgs<T>* args, const Segment* seg, int nseg, 
     });
 }
 
+template <typename T, int B>
+SepTaps<T, B> sep_taps(const double* sep_host) {
+    SepTaps<T, B> tp;
+    for (int i = 0; i < B; ++i) {
+        tp.cu[i] = (T)sep_host[i];
+        tp.cv[i] = (T)sep_host[B + i];
+    }
+    return tp;
+}
+
 template <typename T, int MODE>
-void stencil_launch(const StencilArgs<T>& a, int bh, const double* taps_host, dim3 grid, size_t smem, cudaStream_t s) {
+void stencil_launch(const StencilArgs<T>& a, int bh, const double* sep_host, const double* taps_host, dim3 grid,
+                    size_t smem, cudaStream_t s) {
+    if (sep_host) {
+        with_bh(bh, [&](auto b) {
+            constexpr int B = decltype(b)::value;
+            stencil_sep_kernel<T, MODE, B><<<grid, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B>(), s>>>(
+                a, sep_taps<T, B>(sep_host));
+        });
+        return;
+    }
     if (taps_host) {
         with_bh(bh, [&](auto b) {
             constexpr int B = decltype(b)::value;
@@ -42,8 +61,16 @@ void stencil_launch(const StencilArgs<T>& a, int bh, const double* taps_host, di
 }
 
 template <typename T, int MODE>
-void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* taps_host,
-                          unsigned blocks, size_t smem, cudaStream_t s) {
+void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* sep_host,
+                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s) {
+    if (sep_host) {
+        with_bh(bh, [&](auto b) {
+            constexpr int B = decltype(b)::value;
+            stencil_sep_batch_kernel<T, MODE, B><<<blocks, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B>(), s>>>(
+                args, seg, nseg, sep_taps<T, B>(sep_host));
+        });
+        return;
+    }
     if (taps_host) {
         with_bh(bh, [&](auto b) {
             constexpr int B = decltype(b)::value;
@@ -90,12 +117,14 @@ cudaError_t stencil_batch_set_smem(int bh, int bytes) {
     template void pixel_launch<T>(const PixelArgs<T>&, unsigned, unsigned, size_t, cudaStream_t);               \
     template void pixel_batch_launch<T>(const PixelArgs<T>*, const Segment*, int, int, unsigned, size_t,        \
                                         cudaStream_t);                                                          \
-    template void stencil_launch<T, 0>(const StencilArgs<T>&, int, const double*, dim3, size_t, cudaStream_t);  \
-    template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, dim3, size_t, cudaStream_t);  \
+    template void stencil_launch<T, 0>(const StencilArgs<T>&, int, const double*, const double*, dim3, size_t,   \
+                                       cudaStream_t);                                                           \
+    template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, const double*, dim3, size_t,   \
+                                       cudaStream_t);                                                           \
     template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
-                                             unsigned, size_t, cudaStream_t);                                   \
+                                             const double*, unsigned, size_t, cudaStream_t);                    \
     template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
-                                             unsigned, size_t, cudaStream_t);                                   \
+                                             const double*, unsigned, size_t, cudaStream_t);                    \
     template cudaError_t pixel_stencil_set_smem<T>(int, int);                                                   \
     template cudaError_t stencil_batch_set_smem<T>(int, int);
 

@@ -346,3 +346,29 @@ def test_identity_subspace_at_93_bands():
     Xo, _, _ = nlpr.admm(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S, p.lam1, p.lam2,
                          p.rho, om, 4, fast=True, inplace=True)
     assert rel(g["X"], nlpr.to_lhw(Xo)) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_non_separable_square_blur(dtype):
+    # random 5x5 taps (rank 5): the 2D square-blur stencil, against the oracle's direct convolution
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4)
+    rng = np.random.default_rng(77)
+    p.blur = rng.random((5, 5))
+    p.blur /= p.blur.sum()
+    wd = "f64" if dtype == "f64" else "f32"
+    g = gpu_solve(p, 10, dtype=dtype, wdtype=wd)
+    Xo, _, _ = oracle_solve(p, 10)
+    assert rel(g["X"], Xo) <= (1e-11 if dtype == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("bsize,sigma", [(9, 1.7), (5, 1.0), (11, 2.0), (3, 0.8)])
+def test_separable_blur_equals_2d_stencil(bsize, sigma):
+    # a Gaussian blur factors as cu(u) cv(v): the separable passes and the 2D stencil apply the same
+    # operator up to rounding (FP64, 12 iterations); the separable path also matches the oracle
+    from paper_2210_04184_gb300.fuse import FUSE_OPT_SEPARABLE_BLUR
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=bsize, blur_sigma=sigma)
+    a = gpu_solve(p, 12, dtype="f64", wdtype="f64")["X"]
+    b = gpu_solve(p, 12, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_SEPARABLE_BLUR, 0)])["X"]
+    assert rel(a, b) <= 1e-13
+    Xo, _, _ = oracle_solve(p, 12)
+    assert rel(a, Xo) <= 1e-11
