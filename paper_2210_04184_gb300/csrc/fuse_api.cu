@@ -439,10 +439,8 @@ bool latent_tma_shape(fuse_ctx* c) {
     const int ncons = ((tpr * Ty + 31) / 32) * 32;
     if (ncons + 32 > 288) return false;
     const size_t ssz = c->sfmt ? 2 : c->esz;     // bytes of one stored state element
-    // ring, two H tiles and Xs at the padded pitch W + W/8, the tiles Xo and Vs (see
-    // latent_tma_body), mbarriers
-    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz +
-                        (3 * (size_t)Ty * (c->W + c->W / 8) + 2 * (size_t)Ty * c->W) * c->esz + 16 +
+    // ring, the tiles Xo, Vs, two H tiles and Xs (see latent_tma_body), mbarriers
+    const size_t smem = (size_t)c->lat_stages * Ty * c->W * ssz + 5 * (size_t)Ty * c->W * c->esz +
                         2 * (size_t)c->lat_stages * 8;
     if (smem > (size_t)kMaxSmem || c->lat_stages < 1) return false;
     c->lt_Ty = Ty;
@@ -589,7 +587,7 @@ struct Impl {
         a.mplanes = (T*)c->mPm;
         a.mpart = c->mon_part;
         c->mon_lat = (size_t)grid.x * grid.y * grid.z;
-        const size_t smem = c->lt_smem + 2 * (size_t)c->lt_Ty * (c->W + c->W / 8) * sizeof(T);   // two more tiles
+        const size_t smem = c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * sizeof(T);     // two more tiles
         latent_monitor_launch<T, WT>(a, c->K, grid, (unsigned)(c->lt_ncons + 32), smem, s);
     }
 
@@ -807,7 +805,7 @@ fuse_status monitored_iteration(fuse_ctx* c, bool zero_in) {
     if (c->lat_impl != 1 || c->sfmt != 0 || c->xmode != 0)
         return fail(c, FUSE_EUNSUPPORTED, "the residual monitor needs the bulk-copy latent pass, the state in the "
                                           "iterate type and the paper's splitting");
-    if (c->lt_smem + 2 * (size_t)c->lt_Ty * (c->W + c->W / 8) * c->esz > (size_t)kMaxSmem)
+    if (c->lt_smem + 2 * (size_t)c->lt_Ty * c->W * c->esz > (size_t)kMaxSmem)
         return fail(c, FUSE_EUNSUPPORTED, "the monitoring latent pass does not fit shared memory");
     const size_t img = c->n * c->Ls * c->esz;
     cudaStream_t s = c->stream;
@@ -1036,7 +1034,7 @@ struct fuse_batch {
     // launch shapes shared by all problems
     int lat_target = 256, lat_stages = 6, lat_ncons = 0, lat_bpb = 2;
     size_t lat_smem = 0, st_smem = 0, fr_smem = 0, fc_smem = 0, px_smem = 0;
-    int fr_rpb = 4, fc_cw = 8;
+    int fc_cw = 8;              // FFT column pass: columns per block (row passes: rows per block per problem)
     // device tables: [args of every problem] and segments per kernel
     void* d_lat = nullptr; Segment* d_lat_seg = nullptr; int lat_nseg = 0, lat_blocks = 0;
     void* d_st1 = nullptr; void* d_st0 = nullptr; Segment* d_st_seg = nullptr; int st_nseg = 0, st_blocks = 0;
@@ -1120,8 +1118,7 @@ struct BatchImpl {
             fuse_ctx* c = b->ctx[i];
             la[i] = Impl<T>::template lat_args<WT>(c, Ty[i], b->lat_ncons, b->lat_stages, b->lat_bpb);
             const size_t ssz = b->sfmt ? 2 : esz;
-            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz +
-                              (3 * (size_t)Ty[i] * (c->W + c->W / 8) + 2 * (size_t)Ty[i] * c->W) * esz + 16 +
+            const size_t sm = (size_t)b->lat_stages * Ty[i] * c->W * ssz + 5 * (size_t)Ty[i] * c->W * esz +
                               2 * (size_t)b->lat_stages * 8;
             if (sm > b->lat_smem) b->lat_smem = sm;
         }
@@ -1163,10 +1160,14 @@ struct BatchImpl {
         b->fr_smem = b->fc_smem = 0;
         for (int i = 0; i < n; ++i) {
             fuse_ctx* c = b->ctx[i];
-            fa[i] = Impl<T>::fft_args(c, b->fr_rpb, b->fc_cw);
-            add_segment(sr, i, (c->H + b->fr_rpb - 1) / b->fr_rpb, c->npair, 1, 0, &nr);
+            // rows per block of this problem: about W/4 threads per row (at least 32), as many rows
+            // as fit in the 256 threads
+            const int tpr = std::min(256, std::max(32, c->W / 4));
+            const int rpb = std::max(1, 256 / tpr);
+            fa[i] = Impl<T>::fft_args(c, rpb, b->fc_cw);
+            add_segment(sr, i, (c->H + rpb - 1) / rpb, c->npair, 1, 0, &nr);
             add_segment(sc, i, (c->W + b->fc_cw - 1) / b->fc_cw, c->npair, 1, 0, &ncl);
-            const size_t r = 2 * (size_t)b->fr_rpb * c->W * csz;
+            const size_t r = 2 * (size_t)rpb * c->W * csz;
             const size_t cc = (size_t)b->fc_cw * (2 * c->H + 1) * csz;
             if (r > b->fr_smem) b->fr_smem = r;
             if (cc > b->fc_smem) b->fc_smem = cc;

@@ -200,10 +200,9 @@ struct WRow {
 // for every tau2; per tau2 each consumer adds its H_tau to A in registers and publishes it in one
 // of two shared tiles (alternating), and after one named barrier (the producer never waits on it)
 // adds the shifted H_tau(m + (0, tau2)) of its row to its entries of the V tile (Vs).
-// Shared memory: ring [D][Ty][W] (storage type), then two H tiles and Xs at the padded pitch
-// PW = W + W/8 (element x of a row at x + x/8: the lanes of a warp, VEC = 8 columns apart, then
-// fall in distinct banks), Xo and Vs [Ty][W], and with MON two more padded tiles of the
-// monitoring sums (all of T), then the 2D mbarriers.
+// Shared memory: ring [D][Ty][W] (storage type), then the tiles Xo, Vs, two H tiles, Xs and with
+// MON two tiles of the monitoring sums, each [Ty][W] of T (W % 8 == 0 keeps every tile a
+// multiple of 32 bytes, so the 16-byte vector accesses stay aligned), then the 2D mbarriers.
 // MON (monitoring instance, the last iteration of a solve whose residuals are wanted) also forms
 // the adjoint sums of Q' + Sigma = v + Sigma' + Sigma (into args.mplanes) and the block's sum of
 // (Sigma' - Sigma)^2 (into args.mpart): the latent parts of the ADMM dual and primal residuals
@@ -226,18 +225,13 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int side = 2 * S + 1;
     const int tile = Ty * W;
     ST* ring = reinterpret_cast<ST*>(smem_tma);               // [D][Ty][W] of the storage type
-    const int PW = W + W / 8;                                 // padded pitch
-    const int ptile = Ty * PW;
-    T* Hb = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [2][Ty][PW]
-    T* Xs = Hb + (size_t)2 * ptile;                           // [Ty][PW]
-    T* Xo = Xs + ptile;                                       // [Ty][W]
+    T* Xo = reinterpret_cast<T*>(ring + (size_t)D * tile);    // [Ty][W]
     T* Vs = Xo + tile;                                        // [Ty][W]
-    T* Mb = Vs + tile;                                        // MON only: [2][Ty][PW]
-    constexpr int NPT = MON ? 5 : 3;                          // padded tiles
-    // the padded tiles leave the end of the tile area 4-byte aligned only: the mbarriers start at
-    // the next 16-byte boundary (the launch reserves 16 bytes for this)
-    const uintptr_t bar_addr = reinterpret_cast<uintptr_t>(Hb + (size_t)NPT * ptile + (size_t)2 * tile);
-    uint64_t* full = reinterpret_cast<uint64_t*>((bar_addr + 15) & ~(uintptr_t)15);
+    T* Hb = Vs + tile;                                        // [2][Ty][W]
+    T* Xs = Hb + (size_t)2 * tile;                            // [Ty][W]
+    T* Mb = Xs + tile;                                        // MON only: [2][Ty][W]
+    constexpr int NT = MON ? 7 : 5;
+    uint64_t* full = reinterpret_cast<uint64_t*>(Xo + (size_t)NT * tile);
     uint64_t* empty = full + D;
     __shared__ volatile int s_abort;
 
@@ -321,9 +315,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             vload<T, VEC>(Xc + pix, xr);
             vstore<T, VEC>(xo, xr);
             vload<T, VEC>(Xc + xsrow + x0, xr);
-            T* xs = Xs + (size_t)r * PW + x0 + x0 / 8;
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) xs[j + j / 8] = xr[j];
+            vstore<T, VEC>(Xs + (size_t)r * W + x0, xr);
 #pragma unroll
             for (int j = 0; j < VEC; ++j) xr[j] = T(0);
             vstore<T, VEC>(vs, xr);
@@ -347,8 +339,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             for (int j = 0; j < VEC; ++j) {
                 Hacc[j] = T(0);
                 if constexpr (MON) Macc[j] = T(0);
-                const int xx = wrap1(x0 + j - t2, W);
-                delta[j] = active ? delta[j] - Xs[(size_t)r * PW + xx + xx / 8] : T(0);
+                delta[j] = active ? delta[j] - Xs[(size_t)r * W + wrap1(x0 + j - t2, W)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
             const WT* om_next = jt + 1 < nt2 ? omega + (size_t)tm.w_index(t1, tm.t2_of(t1, jt + 1)) * n : om;
@@ -458,17 +449,16 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 }
             }
             // A += H_tau; publish H_tau so the row can form V(m) += H_tau(m + (0, tau2))
-            T* ht = Hb + (size_t)hb * ptile + (size_t)r * PW;
-            T* mt = Mb + (size_t)hb * ptile + (size_t)r * PW;
+            T* ht = Hb + (size_t)hb * tile + (size_t)r * W;
+            T* mt = Mb + (size_t)hb * tile + (size_t)r * W;
             if (owner) {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    const int xx = x0 + j;
                     A[j] += Hacc[j];
-                    ht[xx + xx / 8] = Hacc[j];
+                    ht[x0 + j] = Hacc[j];
                     if constexpr (MON) {
                         A2[j] += Macc[j];
-                        mt[xx + xx / 8] = Macc[j];
+                        mt[x0 + j] = Macc[j];
                     }
                 }
             }
@@ -479,9 +469,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 vload<T, VEC>(vs, v);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    const int xx = wrap1(x0 + j + t2, W);
-                    v[j] += ht[xx + xx / 8];
-                    if constexpr (MON) V2[j] += mt[xx + xx / 8];
+                    v[j] += ht[wrap1(x0 + j + t2, W)];
+                    if constexpr (MON) V2[j] += mt[wrap1(x0 + j + t2, W)];
                 }
                 vstore<T, VEC>(vs, v);
             }
