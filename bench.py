@@ -60,6 +60,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch64")
     ap.add_argument("--problems", type=int, default=64, help="problems of the batch workload")
+    ap.add_argument("--sizes", default=None,
+                    help="keep only the batch's problems of these sizes (comma-separated), for analysis")
     ap.add_argument("--batch-shape", default=None,
                     help="latent launch shape of the batch as THREADS,STAGES,BANDS (skips the batch tuner)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the single-problem secondary line")
@@ -443,6 +445,9 @@ def run_batch(a, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     ps = synth.batch_workload(a.problems, seed=synth.SEED_BASE + 4 + 7919 * rank)
+    if a.sizes:
+        keep = {int(v) for v in a.sizes.split(",")}
+        ps = [p for p in ps if p.H in keep]
     iters = a.iters or ps[0].iters
     for p in ps:
         p.iters = iters

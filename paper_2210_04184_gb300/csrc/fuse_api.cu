@@ -1034,7 +1034,7 @@ struct fuse_batch {
     // launch shapes shared by all problems
     int lat_target = 256, lat_stages = 6, lat_ncons = 0, lat_bpb = 2;
     size_t lat_smem = 0, st_smem = 0, fr_smem = 0, fc_smem = 0, px_smem = 0;
-    int fc_cw = 8;              // FFT column pass: columns per block (row passes: rows per block per problem)
+    int fr_rpb = 4, fc_cw = 8;
     // device tables: [args of every problem] and segments per kernel
     void* d_lat = nullptr; Segment* d_lat_seg = nullptr; int lat_nseg = 0, lat_blocks = 0;
     void* d_st1 = nullptr; void* d_st0 = nullptr; Segment* d_st_seg = nullptr; int st_nseg = 0, st_blocks = 0;
@@ -1160,10 +1160,7 @@ struct BatchImpl {
         b->fr_smem = b->fc_smem = 0;
         for (int i = 0; i < n; ++i) {
             fuse_ctx* c = b->ctx[i];
-            // rows per block of this problem: about W/4 threads per row (at least 32), as many rows
-            // as fit in the 256 threads
-            const int tpr = std::min(256, std::max(32, c->W / 4));
-            const int rpb = std::max(1, 256 / tpr);
+            const int rpb = b->fr_rpb;
             fa[i] = Impl<T>::fft_args(c, rpb, b->fc_cw);
             add_segment(sr, i, (c->H + rpb - 1) / rpb, c->npair, 1, 0, &nr);
             add_segment(sc, i, (c->W + b->fc_cw - 1) / b->fc_cw, c->npair, 1, 0, &ncl);

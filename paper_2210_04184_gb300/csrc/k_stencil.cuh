@@ -15,6 +15,27 @@ namespace fuse {
 
 constexpr int ST_TX = 32, ST_TY = 32, ST_BY = 8;
 
+// Loads the th x tw input tile whose top-left element is (y0 - rh, x0 - rw) of the H x W plane
+// `in`, with circular indices, into tile[rr * pitch + cc].  When every index of the tile lies in
+// [-n, 2n) (the usual case: the tile and its halo are smaller than the image) the wrap is one
+// compare and select; otherwise (tiny images) the general modulo.  The test is uniform per block.
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* __restrict__ in, int H, int W, int y0, int x0, int rh, int rw,
+                                          int th, int tw, T* tile, int pitch) {
+    const bool near = y0 - rh >= -H && y0 - rh + th <= 2 * H && x0 - rw >= -W && x0 - rw + tw <= 2 * W;
+    if (near) {
+        for (int rr = threadIdx.y; rr < th; rr += ST_BY) {
+            const T* row = in + (size_t)wrap1(y0 - rh + rr, H) * W;
+            for (int cc = threadIdx.x; cc < tw; cc += ST_TX) tile[rr * pitch + cc] = row[wrap1(x0 - rw + cc, W)];
+        }
+    } else {
+        for (int rr = threadIdx.y; rr < th; rr += ST_BY) {
+            const T* row = in + (size_t)wrapn(y0 - rh + rr, H) * W;
+            for (int cc = threadIdx.x; cc < tw; cc += ST_TX) tile[rr * pitch + cc] = row[wrapn(x0 - rw + cc, W)];
+        }
+    }
+}
+
 template <typename T>
 struct StencilArgs {
     const T* in;
@@ -72,10 +93,7 @@ __device__ __forceinline__ void stencil_body(const StencilArgs<T>& a, int bx, in
     const T* __restrict__ inc = a.in + (size_t)c * n;
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
     const int nthr = ST_TX * ST_BY;
-    for (int rr = threadIdx.y; rr < th; rr += ST_BY) {
-        const T* row = inc + (size_t)wrapc(y0 - rh + rr, H) * W;
-        for (int cc = threadIdx.x; cc < tw; cc += ST_TX) tile[rr * tw + cc] = row[wrapc(x0 - rw + cc, W)];
-    }
+    load_tile<T>(inc, H, W, y0, x0, rh, rw, th, tw, tile, tw);
     for (int idx = tid; idx < BH * bw; idx += nthr) tp[idx] = a.taps[idx];
     __syncthreads();
     const int x = x0 + threadIdx.x;
@@ -117,10 +135,7 @@ __device__ __forceinline__ void stencil_sq_body(const StencilArgs<T>& a, const S
     T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TW]
     const int x0 = bx * ST_TX, y0 = by * ST_TY;
     const T* __restrict__ inc = a.in + (size_t)c * H * W;
-    for (int rr = threadIdx.y; rr < TH; rr += ST_BY) {
-        const T* row = inc + (size_t)wrapc(y0 - R + rr, H) * W;
-        for (int cc = threadIdx.x; cc < TW; cc += ST_TX) tile[rr * TW + cc] = row[wrapc(x0 - R + cc, W)];
-    }
+    load_tile<T>(inc, H, W, y0, x0, R, R, TH, TW, tile, TW);
     __syncthreads();
     const int x = x0 + threadIdx.x;
     if (x >= W) return;
@@ -190,10 +205,7 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
     T* hs = tile + TH * TP;                           // [TH][HP]
     const int x0 = bx * ST_TX, y0 = by * ST_TY;
     const T* __restrict__ inc = a.in + (size_t)c * H * W;
-    for (int rr = threadIdx.y; rr < TH; rr += ST_BY) {
-        const T* row = inc + (size_t)wrapc(y0 - R + rr, H) * W;
-        for (int cc = threadIdx.x; cc < TW; cc += ST_TX) tile[rr * TP + cc] = row[wrapc(x0 - R + cc, W)];
-    }
+    load_tile<T>(inc, H, W, y0, x0, R, R, TH, TW, tile, TP);
     __syncthreads();
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
     for (int it = tid; it < TH * CG; it += ST_TX * ST_BY) {

@@ -150,16 +150,20 @@ def test_batch64_full_size_sampled():
 
 def test_batch_with_different_blur_taps():
     # problems with the same blur size but different taps (sigma 1.0 and 1.6): the batch falls back
-    # to the stencil that reads each problem's taps, and every problem equals its single solve
+    # to the 2D stencil that reads each problem's taps, and every problem equals its single solve
+    # with the 2D stencil (a single Gaussian blur otherwise takes the separable passes: the same
+    # operator with another rounding)
     ps = [synth.make_problem(H=h, W=w, L_l=9, L_h=3, L_s=5, d=4, blur_size=5, blur_sigma=sg, K=1, S=2,
                              lam1=1.0, lam2=1e-2, rho=5e-2, h=0.3, seed=300 + i)
           for i, (h, w, sg) in enumerate([(40, 40, 1.0), (48, 64, 1.6), (32, 24, 1.0)])]
     fs, yl, yh = _contexts(ps, "f32", "f32")
     single = []
     for f, a, b in zip(fs, yl, yh):
+        f.set_option(fuse.FUSE_OPT_SEPARABLE_BLUR, 0)
         X, _ = f.solve(a, b, 9)
         f.sync()
         single.append(X.clone())
+        f.set_option(fuse.FUSE_OPT_SEPARABLE_BLUR, 1)
     batch = FusionBatch(fs)
     Xs, _ = batch.solve(yl, yh, 9)
     batch.sync()
