@@ -126,8 +126,9 @@ enum {
                                     b(u, v) = cu(u) cv(v) (to 1e-13 of the largest tap, checked at
                                     fuse_init; a sampled Gaussian does) is applied as a horizontal
                                     and a vertical pass (2B multiply-adds per output instead of
-                                    B^2; the same operator up to rounding); 0: always the 2D
-                                    stencil.  A batch follows its first context. */
+                                    B^2; the same operator up to rounding; W % 4 == 0, else the
+                                    2D stencil); 0: always the 2D stencil.  A batch follows its
+                                    first context. */
 };
 
 /* Kernel groups for fuse_profile. */
@@ -267,8 +268,8 @@ fuse_status fuse_get_option(fuse_ctx* ctx, int option, long long* value);
 
 /* Launch-shape tuner: with the context's weights and the given inputs (as in fuse_solve), times
  * `iters` iterations for each candidate shape of the latent pass (consumer threads 128/192/256,
- * ring slots 4/6/8, bands per block 1/2) and of the FFT passes (rows per block 1..8, columns per
- * block 2..16) and keeps the fastest.  Results do not depend on the shapes (bit-identical).
+ * ring slots 4/6/8/12/16/24, bands per block 1/2; shapes that do not fit are skipped) and of the
+ * FFT passes (rows per block 1..8, columns per block 2..16) and keeps the fastest.  Results do not depend on the shapes (bit-identical).
  * Leaves the context without state: the next fuse_solve starts from zero.  Synchronous. */
 fuse_status fuse_autotune(fuse_ctx* ctx, const void* Yl_dev, const void* Yh_dev, int iters);
 
@@ -414,7 +415,8 @@ fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value);
 /* Current value of a batch option (the options of fuse_batch_set_option).  Errors: FUSE_EINVAL. */
 fuse_status fuse_batch_get_option(fuse_batch* b, int option, long long* value);
 
-/* Launch-shape tuner of a batch (latent pass: consumer threads, ring slots, bands per block),
+/* Launch-shape tuner of a batch (latent pass: consumer threads 128/160/192/256, ring slots
+ * 6/8/12/16, bands per block 1/2/4; shapes that do not fit are skipped),
  * timing `iters` batched iterations per candidate; inputs as in fuse_batch_solve.  Synchronous. */
 fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters);
 

@@ -42,8 +42,11 @@ __global__ void wait_selftest_kernel(int* err, unsigned limit, int code) {
 namespace {
 
 constexpr int kMaxSmem = 200 * 1024;
-// blocks of the grid-stride reduction kernels of the residual monitor (fixed: deterministic sums)
-constexpr int kMonBlocks = 4 * 152;
+// blocks of the grid-stride reduction kernels of the residual monitor (a fixed count, so the sums
+// are formed in the same order on every device)
+constexpr int kMonBlocks = 608;
+// SM count assumed where no device is queried (fuse_workspace_bytes: the sizes do not depend on it)
+constexpr int kDefaultSMs = 152;
 
 struct Event2 { cudaEvent_t a, b; };
 
@@ -92,7 +95,7 @@ struct fuse_ctx {
     size_t esz = 4, wsz = 4;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    int device = 0;
+    int device = 0, nsm = kDefaultSMs;      // device and its SM count (launch-shape heuristics)
     // launch shapes
     int vec = 4, lat_Ty = 1, lat_threads = 0;
     size_t lat_smem = 0;
@@ -327,8 +330,10 @@ struct Shapes {
     size_t lat_smem, w_smem, fr_smem, fc_smem, st_smem, px_smem, mix_smem_max;
 };
 
+// Validates the problem and picks the default launch shapes for a device with `nsm` SMs.
 fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, int ratio, fuse_dtype dtype,
-                           fuse_dtype wdtype, int bh, int bw, Shapes* sh, FFTPlan* pH, FFTPlan* pW) {
+                           fuse_dtype wdtype, int bh, int bw, Shapes* sh, FFTPlan* pH, FFTPlan* pW,
+                           int nsm = kDefaultSMs) {
     if (!g) return fail(c, FUSE_EINVAL, "geometry is NULL");
     if (g->H < 1 || g->W < 1 || g->L_l < 1 || g->L_h < 1 || g->L_s < 1 || g->L_guide < 1)
         return fail(c, FUSE_EINVAL, "sizes must be positive");
@@ -369,7 +374,7 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     while (sh->fr_rpb > 1 && 2 * (size_t)sh->fr_rpb * g->W * csz > 64 * 1024) sh->fr_rpb--;
     // small images: fewer rows per block until the pass has about two blocks per SM
     const int npair_ = (g->L_s + 1) / 2;
-    while (sh->fr_rpb > 1 && (long long)((g->H + sh->fr_rpb - 1) / sh->fr_rpb) * npair_ < 304) sh->fr_rpb /= 2;
+    while (sh->fr_rpb > 1 && (long long)((g->H + sh->fr_rpb - 1) / sh->fr_rpb) * npair_ < 2 * nsm) sh->fr_rpb /= 2;
     sh->fr_smem = 2 * (size_t)sh->fr_rpb * g->W * csz;
     if (sh->fr_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "W too large for the FFT");
     // fft columns
@@ -377,7 +382,7 @@ fuse_status check_geometry(fuse_ctx* c, const fuse_geometry* g, int K, int S, in
     while (sh->fc_cw > 1 && (size_t)sh->fc_cw * (2 * g->H + 1) * csz > kMaxSmem) sh->fc_cw /= 2;
     // narrower blocks until the pass has about four blocks per SM (one wave at four resident
     // blocks: a column block holds 256 threads and tens of KB of shared memory)
-    while (sh->fc_cw > 2 && (long long)((g->W + sh->fc_cw - 1) / sh->fc_cw) * npair_ < 4 * 152) sh->fc_cw /= 2;
+    while (sh->fc_cw > 2 && (long long)((g->W + sh->fc_cw - 1) / sh->fc_cw) * npair_ < 4 * nsm) sh->fc_cw /= 2;
     sh->fc_smem = (size_t)sh->fc_cw * (2 * g->H + 1) * csz;
     if (sh->fc_smem > kMaxSmem) return fail(c, FUSE_EUNSUPPORTED, "H too large for the FFT");
     int tc = g->H / 4;
@@ -519,7 +524,7 @@ struct Impl {
             const bool isB = a.taps == (const T*)c->tapsB;
             ht = isB ? c->htapsB.data() : c->htapsT.data();
             const std::vector<double>& f = isB ? c->hsepB : c->hsepT;
-            if (c->sep_blur && !f.empty()) sep = f.data();
+            if (c->sep_blur && !f.empty() && c->W % 4 == 0) sep = f.data();     // four-column vectors
         }
         fuse::stencil_launch<T, MODE>(a, c->bh, sep, ht, grid, c->st_smem, s);
     }
@@ -961,7 +966,7 @@ fuse_status sb_prepare(fuse_ctx* c) {
     if (m > w) m = w;
     while (m > 1 && (size_t)m * d * (2 * H + 1) * csz > kMaxSmem) m /= 2;
     // fewer base columns per block until the pass has about four blocks per SM
-    while (m > 1 && (long long)((w + m - 1) / m) * c->npair < 4 * 152) m /= 2;
+    while (m > 1 && (long long)((w + m - 1) / m) * c->npair < 4 * c->nsm) m /= 2;
     if ((size_t)m * d * (2 * H + 1) * csz > kMaxSmem || m * d > 256)
         return fail(c, FUSE_EUNSUPPORTED, "the alias-class column pass does not fit shared memory");
     int tpc = H / 4 < 1 ? 1 : H / 4;
@@ -1262,6 +1267,25 @@ void batch_release(fuse_batch* b) {
     b->allocs.clear();
 }
 
+// Sets the batch's latent launch shape (consumer threads, ring slots, bands per block) and rebuilds
+// its launch tables once; a shape that does not fit leaves the previous one in place (FUSE_EINVAL).
+fuse_status batch_set_shape(fuse_batch* b, int threads, int stages, int bands) {
+    if (threads < 32 || threads > 256 || stages < 2 || stages > 32 || bands < 1 || bands > 64)
+        return bfail(b, FUSE_EINVAL, "latent launch option out of range");
+    const int old_t = b->lat_target, old_d = b->lat_stages, old_b = b->lat_bpb;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    b->lat_target = threads;
+    b->lat_stages = stages;
+    b->lat_bpb = bands;
+    if (batch_build(b) == FUSE_OK) return FUSE_OK;
+    b->sticky = FUSE_OK;
+    b->lat_target = old_t; b->lat_stages = old_d; b->lat_bpb = old_b;
+    batch_release(b);
+    if (batch_build(b) != FUSE_OK) return bfail(b, FUSE_ECUDA, "cannot rebuild the batch tables");
+    return bfail(b, FUSE_EINVAL, "latent launch shape does not fit the batch");
+}
+
 // Batched counterpart of launch_loop: `len` batched iterations replayed from one graph.
 fuse_status batch_launch_loop(fuse_batch* b, int len, bool cold) {
     LoopGraph* lg = b->loops.find(len, cold);
@@ -1364,6 +1388,14 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     fuse_status st = check_geometry(nullptr, g, K, S, ratio, dtype, wdtype, bh, bw, &sh, &pH, &pW);
     if (st != FUSE_OK) return st;
     if (!E && g->L_s != g->L_l) return FUSE_EINVAL;
+    // the launch shapes for this device's SM count
+    int dev = 0, nsm = kDefaultSMs;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+        cudaGetLastError();
+        return FUSE_ECUDA;
+    }
+    if ((st = check_geometry(nullptr, g, K, S, ratio, dtype, wdtype, bh, bw, &sh, &pH, &pW, nsm)) != FUSE_OK) return st;
 
     fuse_ctx* c = new (std::nothrow) fuse_ctx();
     if (!c) return FUSE_ENOMEM;
@@ -1386,6 +1418,7 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     c->fc_cw = sh.fc_cw; c->fc_tpc = sh.fc_tpc; c->fc_smem = sh.fc_smem;
     c->st_smem = sh.st_smem; c->px_smem = sh.px_smem; c->px_threads = sh.px_threads;
     c->planH = pH; c->planW = pW;
+    c->nsm = nsm;
 
     auto bail = [&](fuse_status s) { release(c); delete c; return s; };
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); return bail(FUSE_ECUDA); }
@@ -1918,7 +1951,7 @@ fuse_status fuse_autotune(fuse_ctx* c, const void* Yl, const void* Yh, int iters
     if (c->lat_impl == 1) {
         const int bt = c->lat_target, bs = c->lat_stages, bb = c->lat_bpb;
         int best_t = bt, best_s = bs, best_b = bb;
-        const int threads[] = {128, 192, 256}, stages[] = {4, 6, 8}, bands[] = {1, 2};
+        const int threads[] = {128, 192, 256}, stages[] = {4, 6, 8, 12, 16, 24}, bands[] = {1, 2};
         for (int th : threads)
             for (int sg : stages)
                 for (int bd : bands) {
@@ -2156,29 +2189,11 @@ fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value) {
         case FUSE_OPT_PROFILE: b->profile = value != 0; return FUSE_OK;
         case FUSE_OPT_GRAPH: b->use_graph = value != 0; return FUSE_OK;
         case FUSE_OPT_LATENT_THREADS:
+            return batch_set_shape(b, (int)value, b->lat_stages, b->lat_bpb);
         case FUSE_OPT_LATENT_STAGES:
-        case FUSE_OPT_LATENT_BANDS: {
-            const int old_t = b->lat_target, old_d = b->lat_stages, old_b = b->lat_bpb;
-            if (option == FUSE_OPT_LATENT_THREADS) b->lat_target = (int)value;
-            else if (option == FUSE_OPT_LATENT_STAGES) b->lat_stages = (int)value;
-            else b->lat_bpb = (int)value;
-            if (b->lat_target < 32 || b->lat_target > 256 || b->lat_stages < 2 || b->lat_stages > 32 ||
-                b->lat_bpb < 1 || b->lat_bpb > 64) {
-                b->lat_target = old_t; b->lat_stages = old_d; b->lat_bpb = old_b;
-                return bfail(b, FUSE_EINVAL, "latent launch option out of range");
-            }
-            cudaStreamSynchronize(b->stream);
-            batch_release(b);
-            fuse_status st = batch_build(b);
-            if (st != FUSE_OK) {
-                b->sticky = FUSE_OK;
-                b->lat_target = old_t; b->lat_stages = old_d; b->lat_bpb = old_b;
-                batch_release(b);
-                if (batch_build(b) != FUSE_OK) return bfail(b, FUSE_ECUDA, "cannot rebuild the batch tables");
-                return bfail(b, FUSE_EINVAL, "latent launch option does not fit the batch");
-            }
-            return FUSE_OK;
-        }
+            return batch_set_shape(b, b->lat_target, (int)value, b->lat_bpb);
+        case FUSE_OPT_LATENT_BANDS:
+            return batch_set_shape(b, b->lat_target, b->lat_stages, (int)value);
         default: return bfail(b, FUSE_EINVAL, "unknown batch option");
     }
 }
@@ -2207,14 +2222,12 @@ fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void
         st = bfail(b, FUSE_ECUDA, "cudaEventCreate");
     double best = 1e30;
     int bt = b->lat_target, bs = b->lat_stages, bb = b->lat_bpb;
-    const int threads[] = {128, 256}, stages[] = {4, 6, 8}, bands[] = {1, 2, 4};
+    const int threads[] = {128, 160, 192, 256}, stages[] = {6, 8, 12, 16}, bands[] = {1, 2, 4};
     for (int th : threads)
         for (int sg : stages)
             for (int bd : bands) {
                 if (st != FUSE_OK) break;
-                if (fuse_batch_set_option(b, FUSE_OPT_LATENT_THREADS, th) != FUSE_OK ||
-                    fuse_batch_set_option(b, FUSE_OPT_LATENT_STAGES, sg) != FUSE_OK ||
-                    fuse_batch_set_option(b, FUSE_OPT_LATENT_BANDS, bd) != FUSE_OK) {
+                if (batch_set_shape(b, th, sg, bd) != FUSE_OK) {
                     b->sticky = FUSE_OK;
                     continue;
                 }
@@ -2233,9 +2246,7 @@ fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void
     b->use_graph = g;
     b->profile = pr;
     if (st != FUSE_OK) return st;
-    fuse_batch_set_option(b, FUSE_OPT_LATENT_THREADS, bt);
-    fuse_batch_set_option(b, FUSE_OPT_LATENT_STAGES, bs);
-    return fuse_batch_set_option(b, FUSE_OPT_LATENT_BANDS, bb);
+    return batch_set_shape(b, bt, bs, bb);
 }
 
 fuse_status fuse_batch_profile(fuse_batch* b, int which, double* ms, long long* launches, int reset) {

@@ -73,6 +73,39 @@ __device__ __forceinline__ void stencil_store(const StencilArgs<T>& a, const T (
     }
 }
 
+// Writes four consecutive outputs (row y, columns x..x+3, x % 4 == 0, W % 4 == 0) of band c as
+// 16-byte vectors; MODE 1 adds U2 and the adjoint sum R of the latent planes, each read as a
+// vector of the same four columns (the same terms in the same order as stencil_store).
+template <typename T, int MODE>
+__device__ __forceinline__ void stencil_store4(const StencilArgs<T>& a, const T (&acc)[4], int x, int y, int c) {
+    const int H = a.H, W = a.W, S = a.S, half = a.half;
+    const size_t n = (size_t)H * W;
+    const int side = 2 * S + 1;
+    const size_t pix = (size_t)y * W + x;
+    T val[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) val[q] = acc[q];
+    if constexpr (MODE == 1) {
+        const T* pc = a.planes + (size_t)c * 2 * side * n;
+        T rs[4] = {T(0), T(0), T(0), T(0)};
+        for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
+            T pa[4], pv[4];
+            vload<T, 4>(pc + (size_t)(t1 + S) * n + pix, pa);
+            vload<T, 4>(pc + (size_t)(side + t1 + S) * n + (size_t)wrap1(y + t1, H) * W + x, pv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                rs[q] += pa[q];
+                rs[q] -= pv[q];
+            }
+        }
+        T u2[4];
+        vload<T, 4>(a.U2 + (size_t)c * n + pix, u2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) val[q] += u2[q] + (half ? T(2) * rs[q] : rs[q]);
+    }
+    vstore<T, 4>(a.out + (size_t)c * n + pix, val);
+}
+
 // Each thread computes QY = 4 vertically adjacent outputs; for every tap column v it holds the
 // BH + QY - 1 tile values of its column in registers, so each shared-memory read feeds up to
 // QY multiply-adds.  BH is a compile-time odd size (1..15); bw is a runtime odd size.
@@ -179,10 +212,12 @@ stencil_sq_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* 
 
 // Separable square blurs, b(u, v) = cu(u) cv(v) (a sampled Gaussian, for example): the B x B
 // stencil as a horizontal pass over the haloed tile, hs(r, x) = sum_v cv(v) tile(r, x + v) (rows
-// with the vertical halo, four consecutive columns per work item), then a vertical pass with QY
-// outputs per thread, out = sum_u cu(u) hs(y + u, x): 2B multiply-adds per output instead of B^2
-// (plus the halo rows of the first pass).  Shared memory: the tile at an odd pitch (TW | 1, so the
-// four-column items of a warp hit distinct banks), then hs at pitch ST_TX + 1.
+// with the vertical halo, four consecutive columns per work item), then a vertical pass,
+// out(y, x) = sum_u cu(u) hs(y + u, x), again four consecutive columns per thread, so that the
+// rows of hs, the latent planes, U2 and the output move as 16-byte vectors: B (2 + (B - 1)/32)
+// multiply-adds per output instead of B^2.  Shared memory: the tile at an odd pitch (TW | 1, so
+// the four-column items of a warp hit distinct banks in the first pass), then hs at pitch
+// ST_TX + 4 (rows 16-byte aligned).  Needs W % 4 == 0.
 template <typename T, int B>
 struct SepTaps {
     T cu[B], cv[B];
@@ -190,15 +225,14 @@ struct SepTaps {
 
 template <typename T, int B>
 constexpr size_t stencil_sep_smem() {
-    return ((size_t)(ST_TY + B - 1) * ((ST_TX + B - 1) | 1) + (size_t)(ST_TY + B - 1) * (ST_TX + 1)) * sizeof(T);
+    return ((size_t)(ST_TY + B - 1) * ((ST_TX + B - 1) | 1) + (size_t)(ST_TY + B - 1) * (ST_TX + 4)) * sizeof(T);
 }
 
 template <typename T, int MODE, int B>
 __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const SepTaps<T, B>& tp, int bx, int by,
                                                  int c, unsigned char* smem_raw) {
-    constexpr int QY = ST_TY / ST_BY;
     constexpr int R = B / 2;
-    constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, TP = TW | 1, HP = ST_TX + 1;
+    constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, TP = TW | 1, HP = ST_TX + 4;
     constexpr int CG = ST_TX / 4;                     // four-column groups per row
     const int H = a.H, W = a.W;
     T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TP]
@@ -213,29 +247,28 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
         T w[4 + B - 1];
 #pragma unroll
         for (int k = 0; k < 4 + B - 1; ++k) w[k] = tile[r * TP + x + k];
+        T o[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            T acc = T(0);
+            o[q] = T(0);
 #pragma unroll
-            for (int v = 0; v < B; ++v) acc += tp.cv[v] * w[q + v];
-            hs[r * HP + x + q] = acc;
+            for (int v = 0; v < B; ++v) o[q] += tp.cv[v] * w[q + v];
         }
+        vstore<T, 4>(hs + r * HP + x, o);
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= W) return;
-    const int ly0 = threadIdx.y * QY;
-    T col[QY + B - 1];
+    const int vy = tid / CG, vx = (tid - vy * CG) * 4;
+    const int x = x0 + vx, y = y0 + vy;
+    if (x >= W || y >= H) return;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int k = 0; k < QY + B - 1; ++k) col[k] = hs[(ly0 + k) * HP + threadIdx.x];
-    T acc[QY];
+    for (int u = 0; u < B; ++u) {
+        T h[4];
+        vload<T, 4>(hs + (vy + u) * HP + vx, h);
 #pragma unroll
-    for (int q = 0; q < QY; ++q) {
-        acc[q] = T(0);
-#pragma unroll
-        for (int u = 0; u < B; ++u) acc[q] += tp.cu[u] * col[q + u];
+        for (int q = 0; q < 4; ++q) acc[q] += tp.cu[u] * h[q];
     }
-    stencil_store<T, MODE, QY>(a, acc, x, y0 + ly0, c);
+    stencil_store4<T, MODE>(a, acc, x, y, c);
 }
 
 template <typename T, int MODE, int B>

@@ -263,24 +263,30 @@ def test_unrolled_workload_full_size():
 
 def test_unrolled_workload_mse_loss():
     # the workload's loss: L = 1/2 ||X_K E - Z||^2 against the seeded ground truth Z, given to
-    # the reverse pass as dL/dZ = X_K E - Z
+    # the reverse pass as dL/dZ = X_K E - Z.  FP64 on the GPU takes the oracle's clamp decisions
+    # and matches its reverse pass to 1e-8.  FP32 rounding moves some v across |v| = mu, which flips
+    # that entry's derivative between 0 and 1 (reading 17) and its adjoint by O(1): decision noise on
+    # top of rounding, measured up to 2.3e-3 relative on dL/dY_h at this size; bound 5e-3.
     p, meta = synth.workload("unrolled_256")
     from oracle import cloops
     om32 = cloops.weights(nlpr.to_hwl(p.Yh), p.K, p.S, p.h).astype(np.float32).astype(np.float64)
-    f, yl, yh = context(p, meta["dtype"], meta["wdtype"], om32)
-    X = f.grad_forward(yl, yh, p.iters)
-    E = torch.tensor(p.E, dtype=torch.float32, device="cuda")
-    Zt = torch.tensor(p.Z, dtype=torch.float32, device="cuda")
-    Zbar = (torch.einsum("chw,cl->lhw", X, E) - Zt).contiguous()
-    gl, gh, pr = f.grad_backward(Zbar=Zbar)
     Zh = nlpr.to_hwl(p.Z)
     _, go = ograd.unrolled_grad(nlpr.to_hwl(p.Yl), nlpr.to_hwl(p.Yh), p.blur, p.d, p.R, p.E, p.K, p.S, p.lam1,
                                 p.lam2, p.rho, om32, p.iters, lambda Xo: (nlpr.mat(Xo) @ p.E - nlpr.mat(Zh)).reshape(
                                     p.H, p.W, -1) @ p.E.T)
-    assert rel(gl.double().cpu().numpy(), nlpr.to_lhw(go["Yl"])) <= 2e-3
-    assert rel(gh.double().cpu().numpy(), nlpr.to_lhw(go["Yh"])) <= 2e-3
-    for k in ("lam1", "lam2", "rho"):
-        assert abs(pr[k] - go[k]) <= 2e-3 * abs(go[k]), (k, pr[k], go[k])
+    for dtype, tol in (("f64", 1e-8), ("f32", 5e-3)):
+        td = torch.float64 if dtype == "f64" else torch.float32
+        f, yl, yh = context(p, dtype, "f64" if dtype == "f64" else meta["wdtype"], om32)
+        X = f.grad_forward(yl, yh, p.iters)
+        E = torch.tensor(p.E, dtype=td, device="cuda")
+        Zt = torch.tensor(p.Z, dtype=td, device="cuda")
+        Zbar = (torch.einsum("chw,cl->lhw", X, E) - Zt).contiguous()
+        gl, gh, pr = f.grad_backward(Zbar=Zbar)
+        assert rel(gl.double().cpu().numpy(), nlpr.to_lhw(go["Yl"])) <= tol, dtype
+        assert rel(gh.double().cpu().numpy(), nlpr.to_lhw(go["Yh"])) <= tol, dtype
+        for k in ("lam1", "lam2", "rho"):
+            assert abs(pr[k] - go[k]) <= max(tol, 1e-8) * abs(go[k]), (dtype, k, pr[k], go[k])
+        f.close()
 
 
 # ---- weight and guide gradients (fuse_grad_weights) ----------------------------------------
