@@ -62,6 +62,8 @@ def _args():
     ap.add_argument("--problems", type=int, default=64, help="problems of the batch workload")
     ap.add_argument("--sizes", default=None,
                     help="keep only the batch's problems of these sizes (comma-separated), for analysis")
+    ap.add_argument("--latent-shape", default=None,
+                    help="latent launch shape of a single-problem workload as THREADS,STAGES,BANDS (skips the tuner)")
     ap.add_argument("--batch-shape", default=None,
                     help="latent launch shape of the batch as THREADS,STAGES,BANDS (skips the batch tuner)")
     ap.add_argument("--no-secondary", action="store_true", help="skip the single-problem secondary line")
@@ -688,9 +690,14 @@ def single_problem(a, name, rank, dist, keep=False):
     stream = torch.cuda.current_stream()
     fuse_set_stream(f.ctx, stream.cuda_stream)
     fuse_weights(f.ctx, yh.data_ptr())
-    if a.no_autotune:
+    if a.no_autotune or a.latent_shape:
         from paper_2210_04184_gb300.fuse import (fuse_get_option, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES,
                                                  FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS)
+        if a.latent_shape:
+            th, sg, bd = (int(v) for v in a.latent_shape.split(","))
+            f.set_option(FUSE_OPT_LATENT_THREADS, th)
+            f.set_option(FUSE_OPT_LATENT_STAGES, sg)
+            f.set_option(FUSE_OPT_LATENT_BANDS, bd)
         tuned = {k: fuse_get_option(f.ctx, v) for k, v in
                  (("latent_threads", FUSE_OPT_LATENT_THREADS), ("latent_stages", FUSE_OPT_LATENT_STAGES),
                   ("latent_bands", FUSE_OPT_LATENT_BANDS), ("fft_rows", FUSE_OPT_FFT_ROWS),

@@ -223,9 +223,17 @@ struct SepTaps {
     T cu[B], cv[B];
 };
 
+// Offset (elements) of hs: the tile's size rounded up to a 16-byte multiple, since the rows of hs
+// are read and written as 16-byte vectors.
+template <typename T, int B>
+__host__ __device__ constexpr int stencil_sep_hs_offset() {
+    constexpr int e = (int)(16 / sizeof(T));
+    return (((ST_TY + B - 1) * ((ST_TX + B - 1) | 1)) + e - 1) / e * e;
+}
+
 template <typename T, int B>
 constexpr size_t stencil_sep_smem() {
-    return ((size_t)(ST_TY + B - 1) * ((ST_TX + B - 1) | 1) + (size_t)(ST_TY + B - 1) * (ST_TX + 4)) * sizeof(T);
+    return ((size_t)stencil_sep_hs_offset<T, B>() + (size_t)(ST_TY + B - 1) * (ST_TX + 4)) * sizeof(T);
 }
 
 template <typename T, int MODE, int B>
@@ -236,7 +244,7 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
     constexpr int CG = ST_TX / 4;                     // four-column groups per row
     const int H = a.H, W = a.W;
     T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TP]
-    T* hs = tile + TH * TP;                           // [TH][HP]
+    T* hs = tile + stencil_sep_hs_offset<T, B>();     // [TH][HP], 16-byte aligned
     const int x0 = bx * ST_TX, y0 = by * ST_TY;
     const T* __restrict__ inc = a.in + (size_t)c * H * W;
     load_tile<T>(inc, H, W, y0, x0, R, R, TH, TW, tile, TP);
