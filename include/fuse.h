@@ -122,13 +122,22 @@ enum {
                                     the iterate type and the paper's splitting (FUSE_EUNSUPPORTED
                                     otherwise).  The first switch to 1 allocates 4 images and 2
                                     adjoint-plane arrays of workspace. */
-    FUSE_OPT_SEPARABLE_BLUR = 16 /* 1 (default): a square blur whose taps factor as
+    FUSE_OPT_SEPARABLE_BLUR = 16, /* 1 (default): a square blur whose taps factor as
                                     b(u, v) = cu(u) cv(v) (to 1e-13 of the largest tap, checked at
                                     fuse_init; a sampled Gaussian does) is applied as a horizontal
                                     and a vertical pass (2B multiply-adds per output instead of
                                     B^2; the same operator up to rounding; W % 4 == 0, else the
                                     2D stencil); 0: always the 2D stencil.  A batch follows its
                                     first context. */
+    FUSE_OPT_FFT_IMPL = 17       /* DFT solve of the X system: 1 = register-resident passes (one
+                                    warp per line, exchanges by warp shuffles; default when H and
+                                    W are 32 P with P in {1, 2, 3, 4, 5, 6, 8, 10, 12, 16});
+                                    0 = shared-memory Stockham passes (any H, W factoring into 2,
+                                    3, 5; FUSE_OPT_FFT_ROWS / FFT_COLS shape them).  Both compute
+                                    the same DFT up to rounding.  1 on other sizes:
+                                    FUSE_EUNSUPPORTED.  The variant FUSE_OPT_X_UPDATE = 1 always
+                                    uses the Stockham passes.  In a batch every problem keeps the
+                                    form its context had when the batch was created. */
 };
 
 /* Kernel groups for fuse_profile. */

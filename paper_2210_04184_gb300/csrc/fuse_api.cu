@@ -105,6 +105,10 @@ struct fuse_ctx {
     size_t fr_smem = 0, fc_smem = 0, st_smem = 0, px_smem = 0;
     int px_threads = 128;
     FFTPlan planH{}, planW{};
+    // DFT solve: 1 = register-resident passes (k_wfft.cuh; sides 32 P), 0 = shared-memory
+    // Stockham passes; fT: f in the register form's spectrum order (NULL when not eligible)
+    int fft_impl = 0;
+    void* fT = nullptr;
     // device memory
     void *X = nullptr, *BX = nullptr, *C = nullptr, *Y = nullptr;
     void *Lam1 = nullptr, *U1 = nullptr, *Lam2 = nullptr, *U2 = nullptr;
@@ -478,7 +482,8 @@ struct Impl {
     }
     static FFTArgs<T> fft_args(fuse_ctx* c, int rpb, int cw) {
         return FFTArgs<T>{(const T*)c->C, (cplx<T>*)c->Y, (T*)c->X, (const T*)c->fpf, c->H, c->W, c->Ls,
-                          c->planW, c->planH, (const cplx<T>*)c->twW, (const cplx<T>*)c->twH, rpb, cw};
+                          c->planW, c->planH, (const cplx<T>*)c->twW, (const cplx<T>*)c->twH, rpb, cw,
+                          c->fft_impl == 1 ? (const T*)c->fT : nullptr};
     }
     static PixelArgs<T> px_args(fuse_ctx* c) {
         return PixelArgs<T>{(const T*)c->X, (const T*)c->BX, (T*)c->Lam1, (T*)c->U1, (T*)c->Lam2, (T*)c->U2,
@@ -501,6 +506,7 @@ struct Impl {
         CK(c, cudaFuncSetAttribute(fft_rows_inv_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_cols_kernel<T>, A, kMaxSmem));
         CK(c, cudaFuncSetAttribute(fft_cols_alias_kernel<T>, A, kMaxSmem));
+        CK(c, wfft_set_smem<T>(kMaxSmem));
         CK(c, pixel_stencil_set_smem<T>(c->bh, kMaxSmem));
         CK(c, cudaFuncSetAttribute(band_mix_kernel<T>, A, kMaxSmem));
         return FUSE_OK;
@@ -629,23 +635,22 @@ struct Impl {
             CKL(c, "stencil_kernel (right-hand side)");
         }
         const FFTArgs<T> fa = fft_args(c, c->fr_rpb, c->fc_cw);
-        dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
-        fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
-        CKL(c, "fft_rows_fwd_kernel");
         if (c->xmode == 1) {
+            dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
+            fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+            CKL(c, "fft_rows_fwd_kernel");
             const FFTAliasArgs<T> aa{(cplx<T>*)c->Y, c->H, c->W, c->d, c->fa_m, c->planH, (const cplx<T>*)c->twH,
                                      (const T*)c->sbq, (const cplx<T>*)c->sbp, (const T*)c->sbk};
             const int w = c->W / c->d;
             dim3 agrid((unsigned)((w + c->fa_m - 1) / c->fa_m), (unsigned)c->npair);
             fft_cols_alias_kernel<T><<<agrid, c->fa_m * c->d * c->fa_tpc, c->fa_smem, s>>>(aa);
             CKL(c, "fft_cols_alias_kernel");
+            fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+            CKL(c, "fft_rows_inv_kernel");
         } else {
-            dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
-            fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
-            CKL(c, "fft_cols_kernel");
+            const fuse_status st = dft_solve(c, s, fa);
+            if (st != FUSE_OK) return st;
         }
-        fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
-        CKL(c, "fft_rows_inv_kernel");
         if (c->xmode != 1) {
             stencil<0>(c, s, c->X, c->BX, c->tapsB);
             CKL(c, "stencil_kernel (B X)");
@@ -675,6 +680,30 @@ struct Impl {
         }
         CKL(c, "latent kernel");
         if (monitor) return monitor_sums(c, s);
+        return FUSE_OK;
+    }
+
+    // out = A^{-1} in (eq. inv) with the plain factor f: three DFT passes over fa (input fa.C,
+    // output fa.X), in the register-resident form when the context selected it.
+    static fuse_status dft_solve(fuse_ctx* c, cudaStream_t s, const FFTArgs<T>& fa) {
+        if (c->fft_impl == 1) {
+            const size_t smem = wfft_cols_smem<T>(c->H);
+            wfft_pass_launch<T>(fa, 0, c->npair, 0, s);
+            CKL(c, "wfft_rows_fwd_kernel");
+            wfft_pass_launch<T>(fa, 1, c->npair, smem, s);
+            CKL(c, "wfft_cols_kernel");
+            wfft_pass_launch<T>(fa, 2, c->npair, 0, s);
+            CKL(c, "wfft_rows_inv_kernel");
+            return FUSE_OK;
+        }
+        dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
+        fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+        CKL(c, "fft_rows_fwd_kernel");
+        dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
+        fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
+        CKL(c, "fft_cols_kernel");
+        fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
+        CKL(c, "fft_rows_inv_kernel");
         return FUSE_OK;
     }
 
@@ -1158,7 +1187,9 @@ struct BatchImpl {
         if ((st = bupload(b, &b->d_st0, s0)) != FUSE_OK) return st;
         if ((st = bupload(b, (void**)&b->d_st_seg, seg)) != FUSE_OK) return st;
 
-        // FFT passes: 256 threads, rpb rows (tpr = 256 / rpb) or CW columns per block
+        // FFT passes: 256 threads; each problem in its context's form (register-resident: 8 rows
+        // or 8 columns per block, one warp each; Stockham: rpb rows, tpr = 256 / rpb, or CW
+        // columns per block)
         std::vector<FFTArgs<T>> fa(n);
         std::vector<Segment> sr, sc;
         int nr = 0, ncl = 0;
@@ -1167,6 +1198,13 @@ struct BatchImpl {
             fuse_ctx* c = b->ctx[i];
             const int rpb = b->fr_rpb;
             fa[i] = Impl<T>::fft_args(c, rpb, b->fc_cw);
+            if (fa[i].fT) {
+                add_segment(sr, i, (c->H + 7) / 8, c->npair, 1, 0, &nr);
+                add_segment(sc, i, (c->W + kWfftCols - 1) / kWfftCols, c->npair, 1, 0, &ncl);
+                const size_t cc = wfft_cols_smem<T>(c->H);
+                if (cc > b->fc_smem) b->fc_smem = cc;
+                continue;
+            }
             add_segment(sr, i, (c->H + rpb - 1) / rpb, c->npair, 1, 0, &nr);
             add_segment(sc, i, (c->W + b->fc_cw - 1) / b->fc_cw, c->npair, 1, 0, &ncl);
             const size_t r = 2 * (size_t)rpb * c->W * csz;
@@ -1198,12 +1236,9 @@ struct BatchImpl {
         if ((st = bupload(b, (void**)&b->d_px_seg, seg)) != FUSE_OK) return st;
 
         // attributes
-        const auto A = cudaFuncAttributeMaxDynamicSharedMemorySize;
         BCK(b, (latent_batch_set_smem<T, WT>(b->K, kMaxSmem)));
         BCK(b, stencil_batch_set_smem<T>(b->bh, kMaxSmem));
-        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 0>, A, kMaxSmem));
-        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 1>, A, kMaxSmem));
-        BCK(b, cudaFuncSetAttribute(fft_batch_kernel<T, 2>, A, kMaxSmem));
+        BCK(b, wfft_set_smem<T>(kMaxSmem));
         return FUSE_OK;
     }
 
@@ -1217,9 +1252,10 @@ struct BatchImpl {
         stencil_batch_launch<T, 1>((const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg, b->bh,
                                    sep ? c0->hsepT.data() : nullptr, sq ? c0->htapsT.data() : nullptr,
                                    (unsigned)b->st_blocks, b->st_smem, s);
-        fft_batch_kernel<T, 0><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
-        fft_batch_kernel<T, 1><<<b->fc_blocks, 256, b->fc_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fc_seg, b->fc_nseg);
-        fft_batch_kernel<T, 2><<<b->fr_blocks, 256, b->fr_smem, s>>>((const FFTArgs<T>*)b->d_fft, b->d_fr_seg, b->fr_nseg);
+        const FFTArgs<T>* fa = (const FFTArgs<T>*)b->d_fft;
+        fft_batch_launch<T>(fa, b->d_fr_seg, b->fr_nseg, 0, (unsigned)b->fr_blocks, b->fr_smem, s);
+        fft_batch_launch<T>(fa, b->d_fc_seg, b->fc_nseg, 1, (unsigned)b->fc_blocks, b->fc_smem, s);
+        fft_batch_launch<T>(fa, b->d_fr_seg, b->fr_nseg, 2, (unsigned)b->fr_blocks, b->fr_smem, s);
         stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
                                    sep ? c0->hsepB.data() : nullptr, sq ? c0->htapsB.data() : nullptr,
                                    (unsigned)b->st_blocks, b->st_smem, s);
@@ -1569,6 +1605,22 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
     if ((st = upload_any(c, &c->tapsT, tT)) != FUSE_OK) return bail(st);
     if ((st = upload_any(c, &c->tapsB, tB)) != FUSE_OK) return bail(st);
     if ((st = upload_any(c, &c->fpf, fh)) != FUSE_OK) return bail(st);
+    if (wfft_length_ok(H) && wfft_length_ok(W)) {
+        // f in the register-resident form's spectrum order: fT[q][r] = f(u(r), v(q)) for row
+        // position r and column position q, u(r) = r / 32 + (H / 32) rev5(r mod 32), v likewise
+        auto freq = [](int pos, int P) {
+            int r = 0;
+            for (int b = 0; b < 5; ++b) r |= ((pos >> b) & 1) << (4 - b);
+            return pos / 32 + P * r;
+        };
+        std::vector<double> ft(c->n);
+        for (int q = 0; q < W; ++q) {
+            const int v = freq(q, W / 32);
+            for (int r = 0; r < H; ++r) ft[(size_t)q * H + r] = fh[(size_t)freq(r, H / 32) * W + v];
+        }
+        if ((st = upload_any(c, &c->fT, ft)) != FUSE_OK) return bail(st);
+        c->fft_impl = 1;
+    }
     if ((st = upload_any(c, &c->M1, M1)) != FUSE_OK) return bail(st);
     if ((st = upload_any(c, &c->F, Fm)) != FUSE_OK) return bail(st);
     if ((st = upload_any(c, &c->Et, Et)) != FUSE_OK) return bail(st);
@@ -1856,6 +1908,14 @@ fuse_status fuse_set_option(fuse_ctx* c, int option, long long value) {
             c->sep_blur = (int)value;
             drop_graphs(c);
             return FUSE_OK;
+        case FUSE_OPT_FFT_IMPL:
+            if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "FFT form is 0 or 1");
+            if (value == 1 && !c->fT)
+                return fail(c, FUSE_EUNSUPPORTED, "the register-resident FFT needs H and W = 32 P, P in "
+                                                  "{1, 2, 3, 4, 5, 6, 8, 10, 12, 16}");
+            c->fft_impl = (int)value;
+            drop_graphs(c);
+            return FUSE_OK;
         case FUSE_OPT_RESIDUALS: {
             if (value != 0 && value != 1) return fail(c, FUSE_EINVAL, "residual monitor is 0 or 1");
             if (value == 1 && (c->xmode != 0 || c->sfmt != 0 || c->lat_impl != 1))
@@ -1963,8 +2023,9 @@ fuse_status fuse_autotune(fuse_ctx* c, const void* Yl, const void* Yh, int iters
         c->lat_target = best_t; c->lat_stages = best_s; c->lat_bpb = best_b;
         latent_tma_shape(c);
     }
-    // 2. FFT passes: rows per block, then columns per block
-    {
+    // 2. FFT passes: rows per block, then columns per block (the Stockham passes; the register-
+    // resident passes have one shape, and the S B-in-X variant always runs Stockham rows)
+    if (c->fft_impl != 1 || c->xmode == 1) {
         best = 1e30;
         const int old_r = c->fr_rpb;
         int best_r = old_r;
@@ -2012,6 +2073,7 @@ fuse_status fuse_get_option(fuse_ctx* c, int option, long long* value) {
         case FUSE_OPT_X_UPDATE: *value = c->xmode; return FUSE_OK;
         case FUSE_OPT_RESIDUALS: *value = c->monitor; return FUSE_OK;
         case FUSE_OPT_SEPARABLE_BLUR: *value = c->sep_blur; return FUSE_OK;
+        case FUSE_OPT_FFT_IMPL: *value = c->fft_impl; return FUSE_OK;
         default: return FUSE_EINVAL;
     }
 }

@@ -232,15 +232,10 @@ struct GradImpl {
     // out = A^{-1} in (eq. inv), the forward's three FFT launches on other buffers.
     static fuse_status solve_A(fuse_ctx* c, cudaStream_t s, const void* in, void* out) {
         const FFTArgs<T> fa{(const T*)in, (cplx<T>*)c->Y, (T*)out, (const T*)c->fpf, c->H, c->W, c->Ls,
-                            c->planW, c->planH, (const cplx<T>*)c->twW, (const cplx<T>*)c->twH, c->fr_rpb, c->fc_cw};
-        dim3 rgrid((unsigned)((c->H + c->fr_rpb - 1) / c->fr_rpb), (unsigned)c->npair);
-        fft_rows_fwd_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
-        CKL(c, "fft_rows_fwd_kernel (reverse pass)");
-        dim3 cgrid((unsigned)((c->W + c->fc_cw - 1) / c->fc_cw), (unsigned)c->npair);
-        fft_cols_kernel<T><<<cgrid, c->fc_cw * c->fc_tpc, c->fc_smem, s>>>(fa);
-        CKL(c, "fft_cols_kernel (reverse pass)");
-        fft_rows_inv_kernel<T><<<rgrid, c->fr_tpr * c->fr_rpb, c->fr_smem, s>>>(fa);
-        CKL(c, "fft_rows_inv_kernel (reverse pass)");
+                            c->planW, c->planH, (const cplx<T>*)c->twW, (const cplx<T>*)c->twH, c->fr_rpb, c->fc_cw,
+                            c->fft_impl == 1 ? (const T*)c->fT : nullptr};
+        const fuse_status st = Impl<T>::dft_solve(c, s, fa);
+        if (st != FUSE_OK) return st;
         c->launches_all += 3;
         return FUSE_OK;
     }

@@ -116,6 +116,7 @@ struct FFTArgs {
     const cplx<T>* twH;
     int rpb;             // rows per block (row passes)
     int CW;              // columns per block (column pass)
+    const T* fT;         // register-resident form (k_wfft.cuh): f in the spectra's order, [W][H]
 };
 
 // Rows forward, block (bx, p): rows [bx rpb, bx rpb + rpb) of band pair p;
@@ -319,19 +320,6 @@ __global__ void __launch_bounds__(256) fft_cols_alias_kernel(FFTAliasArgs<T> a) 
             const int b = cc / m, j = cc - b * m;
             if (x0 + j < w) Yp[(size_t)row * W + x0 + j + b * w] = sm[(size_t)cc * pitch + off2 + row];
         }
-}
-
-// Batched forms (one launch over many problems, see Segment).
-template <typename T, int PASS>
-__global__ void __launch_bounds__(256)
-fft_batch_kernel(const FFTArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int prob, bx, by, bz;
-    segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
-    const FFTArgs<T> a = args[prob];
-    if constexpr (PASS == 0) fft_rows_fwd_body<T>(a, bx, by, smem_raw);
-    else if constexpr (PASS == 1) fft_cols_body<T>(a, bx, by, smem_raw);
-    else fft_rows_inv_body<T>(a, bx, by, smem_raw);
 }
 
 }  // namespace fuse

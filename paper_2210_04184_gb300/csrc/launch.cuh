@@ -1,6 +1,6 @@
 // Host-side launchers of the kernel families with many template instantiations.  Each family
 // is instantiated in its own translation unit (launch_latent.cu, launch_pixel.cu,
-// launch_grad.cu), so the library's device code compiles in parallel; the launch sequence in
+// launch_grad.cu, launch_fft.cu), so the library's device code compiles in parallel; the launch sequence in
 // fuse_api.cu calls these functions.  Every launcher issues one kernel launch on stream `s`
 // and returns without checking it (the caller reads cudaGetLastError).
 // Instantiated for T = float with WT = float or __nv_bfloat16, and T = double with WT = double.
@@ -13,6 +13,7 @@
 #include "k_latent.cuh"
 #include "k_pixel.cuh"
 #include "k_stencil.cuh"
+#include "k_wfft.cuh"
 
 namespace fuse {
 
@@ -64,6 +65,21 @@ template <typename T>
 cudaError_t pixel_stencil_set_smem(int bh, int bytes);
 template <typename T>
 cudaError_t stencil_batch_set_smem(int bh, int bytes);
+
+// ---- register-resident DFT solve (k_wfft.cuh) ----
+// One pass (0: rows forward, 1: columns with f, 2: rows inverse) over npair band pairs of one
+// problem whose sides are wfft_length_ok; smem: the column pass's wfft_cols_smem<T>(H).
+template <typename T>
+void wfft_pass_launch(const FFTArgs<T>& a, int pass, int npair, size_t smem, cudaStream_t s);
+// One pass over the segment table of a batch, each problem in the form its FFTArgs select
+// (fT set: register-resident, ceil(H / 8) row blocks or ceil(W / 8) column blocks per pair;
+// NULL: Stockham, the problem's rpb / CW shape); smem: the largest any block of the pass needs.
+template <typename T>
+void fft_batch_launch(const FFTArgs<T>* args, const Segment* seg, int nseg, int pass, unsigned blocks, size_t smem,
+                      cudaStream_t s);
+// Dynamic shared-memory cap of the register-form column kernels and the batched kernels.
+template <typename T>
+cudaError_t wfft_set_smem(int bytes);
 
 // ---- reverse pass (k_grad.cuh) ----
 template <typename T, typename WT>
@@ -117,7 +133,11 @@ cudaError_t latent_bwd_set_smem(int K, int bytes);
                                                     cudaStream_t);                                            \
     extern template cudaError_t pixel_stencil_set_smem<T>(int, int);                                          \
     extern template cudaError_t stencil_batch_set_smem<T>(int, int);                                          \
-    extern template void pixel_bwd_launch<T>(const PixelBwdArgs<T>&, unsigned, cudaStream_t);
+    extern template void pixel_bwd_launch<T>(const PixelBwdArgs<T>&, unsigned, cudaStream_t);                \
+    extern template void wfft_pass_launch<T>(const FFTArgs<T>&, int, int, size_t, cudaStream_t);             \
+    extern template void fft_batch_launch<T>(const FFTArgs<T>*, const Segment*, int, int, unsigned, size_t,   \
+                                             cudaStream_t);                                                  \
+    extern template cudaError_t wfft_set_smem<T>(int);
 
 #ifndef FUSE_LAUNCH_DEFINITIONS
 FUSE_LAUNCH_EXTERN_T_WT(float, float)

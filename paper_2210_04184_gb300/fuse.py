@@ -24,7 +24,7 @@ FUSE_OPT_PROFILE, FUSE_OPT_GRAPH = 1, 2
 FUSE_OPT_LATENT_IMPL, FUSE_OPT_LATENT_THREADS, FUSE_OPT_LATENT_STAGES, FUSE_OPT_WAIT_LIMIT = 3, 4, 5, 6
 FUSE_OPT_HALF_WINDOW, FUSE_OPT_LATENT_BANDS, FUSE_OPT_FFT_ROWS, FUSE_OPT_FFT_COLS = 7, 8, 9, 10
 FUSE_OPT_GRAD_SEGMENT, FUSE_OPT_GRAD_WEIGHTS, FUSE_OPT_STATE_FORMAT = 11, 12, 13
-FUSE_OPT_X_UPDATE, FUSE_OPT_RESIDUALS, FUSE_OPT_SEPARABLE_BLUR = 14, 15, 16
+FUSE_OPT_X_UPDATE, FUSE_OPT_RESIDUALS, FUSE_OPT_SEPARABLE_BLUR, FUSE_OPT_FFT_IMPL = 14, 15, 16, 17
 FUSE_K_ALL, FUSE_K_LATENT = 0, 1
 
 DTYPES = {"f32": FUSE_F32, "f64": FUSE_F64, "bf16": FUSE_BF16}
@@ -478,6 +478,9 @@ class Fusion:
 
     def set_option(self, option, value):
         fuse_set_option(self.ctx, option, value)
+
+    def get_option(self, option):
+        return fuse_get_option(self.ctx, option)
 
     def sync(self):
         fuse_sync(self.ctx)
