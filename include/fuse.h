@@ -425,7 +425,7 @@ fuse_status fuse_batch_set_option(fuse_batch* b, int option, long long value);
 fuse_status fuse_batch_get_option(fuse_batch* b, int option, long long* value);
 
 /* Launch-shape tuner of a batch (latent pass: consumer threads 128/160/192/256, ring slots
- * 6/8/12/16, bands per block 1/2/4; shapes that do not fit are skipped),
+ * 6/8/12/16, bands per block 1/2/4/8; shapes that do not fit are skipped),
  * timing `iters` batched iterations per candidate; inputs as in fuse_batch_solve.  Synchronous. */
 fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void* const* Yh, int iters);
 

@@ -85,6 +85,27 @@ struct LoopCache {
 
 struct GradWork;
 
+// Second capture stream of a captured iteration loop: B X and the pixel updates of an iteration
+// need only X, like the latent pass, so in a captured loop they run on this stream beside the
+// latent pass (fork after the inverse DFT); the next iteration's right-hand side, which reads
+// their U1 and U2, waits for them (join).
+struct SideBranch {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool create() {
+        return cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+    }
+    void destroy() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+        s = nullptr;
+        fork = join = nullptr;
+    }
+};
+
 struct fuse_ctx {
     // problem
     int H = 0, W = 0, Ll = 0, Lh = 0, Ls = 0, Lg = 0, K = 0, S = 0, d = 1, bh = 1, bw = 1;
@@ -95,6 +116,7 @@ struct fuse_ctx {
     size_t esz = 4, wsz = 4;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    SideBranch side;
     int device = 0, nsm = kDefaultSMs;      // device and its SM count (launch-shape heuristics)
     // launch shapes
     int vec = 4, lat_Ty = 1, lat_threads = 0;
@@ -625,7 +647,11 @@ struct Impl {
     // One ADMM iteration (Sec. IV): C, X update, P1/P2/duals, latent pass.  With xmode 1 (S B
     // kept in the X system): C = G + U2 + R with the fixed data term G in U1, the column pass
     // solves the alias classes, and there is no B X and no P1.  zero_in: see latent().
-    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed, bool zero_in = false, bool monitor = false) {
+    // side (captured loops): B X and the pixel pass run on c->side.s beside the latent pass;
+    // join_prev: wait for the previous iteration's side branch before the right-hand side.
+    static fuse_status iterate(fuse_ctx* c, cudaStream_t s, bool timed, bool zero_in = false, bool monitor = false,
+                               bool side = false, bool join_prev = false) {
+        if (side && join_prev) CK(c, cudaStreamWaitEvent(s, c->side.join, 0));
         if (c->xmode == 1) {
             dim3 grid((unsigned)((c->W + ST_TX - 1) / ST_TX), (unsigned)((c->H + ST_TY - 1) / ST_TY), (unsigned)c->Ls);
             rhs_sum_kernel<T><<<grid, dim3(ST_TX, ST_BY), 0, s>>>(st_args(c, c->U1, c->C, nullptr));
@@ -651,12 +677,19 @@ struct Impl {
             const fuse_status st = dft_solve(c, s, fa);
             if (st != FUSE_OK) return st;
         }
+        cudaStream_t sp = s;
+        if (side) {
+            CK(c, cudaEventRecord(c->side.fork, s));
+            CK(c, cudaStreamWaitEvent(c->side.s, c->side.fork, 0));
+            sp = c->side.s;
+        }
         if (c->xmode != 1) {
-            stencil<0>(c, s, c->X, c->BX, c->tapsB);
+            stencil<0>(c, sp, c->X, c->BX, c->tapsB);
             CKL(c, "stencil_kernel (B X)");
         }
-        pixel(c, s);
+        pixel(c, sp);
         CKL(c, "pixel_kernel");
+        if (side) CK(c, cudaEventRecord(c->side.join, c->side.s));
         if (timed) {
             if (c->ev_used == c->ev.size()) {
                 Event2 e{};
@@ -803,9 +836,13 @@ fuse_status launch_loop(fuse_ctx* c, int len, bool cold) {
         const bool f64 = c->dtype == FUSE_F64;
         CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         fuse_status st = FUSE_OK;
-        for (int t = 0; t < len && st == FUSE_OK; ++t)
-            st = f64 ? Impl<double>::iterate(c, c->cap_stream, false, cold && t == 0)
-                     : Impl<float>::iterate(c, c->cap_stream, false, cold && t == 0);
+        int forked = 0;
+        for (int t = 0; t < len && st == FUSE_OK; ++t, ++forked)
+            st = f64 ? Impl<double>::iterate(c, c->cap_stream, false, cold && t == 0, false, true, t > 0)
+                     : Impl<float>::iterate(c, c->cap_stream, false, cold && t == 0, false, true, t > 0);
+        // the side branch of the last iteration joins the loop's stream before the capture ends
+        if (forked && cudaStreamWaitEvent(c->cap_stream, c->side.join, 0) != cudaSuccess && st == FUSE_OK)
+            st = fail(c, FUSE_ECUDA, "cudaStreamWaitEvent");
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
         if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -965,6 +1002,7 @@ void release(fuse_ctx* c) {
     for (void* p : c->allocs)
         if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->side.destroy();
     c->allocs.clear();
 }
 
@@ -1061,6 +1099,7 @@ fuse_status sb_prepare(fuse_ctx* c) {
 struct fuse_batch {
     std::vector<fuse_ctx*> ctx;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
+    SideBranch side;
     int device = 0;
     fuse_dtype dtype = FUSE_F32, wdtype = FUSE_F32;
     int K = 0, S = 0, Ls = 0, bh = 1, bw = 1, half = 1, sfmt = 0;
@@ -1244,7 +1283,11 @@ struct BatchImpl {
 
     // One batched ADMM iteration: 7 launches cover every problem.  zero_in: the latent state of
     // every problem is zero on entry (first iteration of the solve) and is not read.
-    static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false) {
+    // side, join_prev: as for a single problem (B X and the pixel pass beside the latent pass in
+    // captured loops).
+    static fuse_status iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false, bool side = false,
+                               bool join_prev = false) {
+        if (side && join_prev) BCK(b, cudaStreamWaitEvent(s, b->side.join, 0));
         // square blurs shared by every problem: taps in the argument space (from problem 0)
         const fuse_ctx* c0 = b->ctx[0];
         const bool sq = b->bh == b->bw && b->same_taps;
@@ -1256,11 +1299,18 @@ struct BatchImpl {
         fft_batch_launch<T>(fa, b->d_fr_seg, b->fr_nseg, 0, (unsigned)b->fr_blocks, b->fr_smem, s);
         fft_batch_launch<T>(fa, b->d_fc_seg, b->fc_nseg, 1, (unsigned)b->fc_blocks, b->fc_smem, s);
         fft_batch_launch<T>(fa, b->d_fr_seg, b->fr_nseg, 2, (unsigned)b->fr_blocks, b->fr_smem, s);
+        cudaStream_t sp = s;
+        if (side) {
+            BCK(b, cudaEventRecord(b->side.fork, s));
+            BCK(b, cudaStreamWaitEvent(b->side.s, b->side.fork, 0));
+            sp = b->side.s;
+        }
         stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
                                    sep ? c0->hsepB.data() : nullptr, sq ? c0->htapsB.data() : nullptr,
-                                   (unsigned)b->st_blocks, b->st_smem, s);
+                                   (unsigned)b->st_blocks, b->st_smem, sp);
         pixel_batch_launch<T>((const PixelArgs<T>*)b->d_px, b->d_px_seg, b->px_nseg, b->Ls, (unsigned)b->px_blocks,
-                              b->px_smem, s);
+                              b->px_smem, sp);
+        if (side) BCK(b, cudaEventRecord(b->side.join, b->side.s));
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timed) {
             if (b->ev_used == b->ev.size()) {
@@ -1289,10 +1339,12 @@ fuse_status batch_build(fuse_batch* b) {
     return BatchImpl<float, float>::build(b);
 }
 
-fuse_status batch_iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false) {
-    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::iterate(b, s, timed, zero_in);
-    if (b->wdtype == FUSE_BF16) return BatchImpl<float, __nv_bfloat16>::iterate(b, s, timed, zero_in);
-    return BatchImpl<float, float>::iterate(b, s, timed, zero_in);
+fuse_status batch_iterate(fuse_batch* b, cudaStream_t s, bool timed, bool zero_in = false, bool side = false,
+                          bool join_prev = false) {
+    if (b->dtype == FUSE_F64) return BatchImpl<double, double>::iterate(b, s, timed, zero_in, side, join_prev);
+    if (b->wdtype == FUSE_BF16)
+        return BatchImpl<float, __nv_bfloat16>::iterate(b, s, timed, zero_in, side, join_prev);
+    return BatchImpl<float, float>::iterate(b, s, timed, zero_in, side, join_prev);
 }
 
 void batch_release(fuse_batch* b) {
@@ -1328,7 +1380,12 @@ fuse_status batch_launch_loop(fuse_batch* b, int len, bool cold) {
     if (!lg) {
         BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
         fuse_status st = FUSE_OK;
-        for (int t = 0; t < len && st == FUSE_OK; ++t) st = batch_iterate(b, b->cap_stream, false, cold && t == 0);
+        int forked = 0;
+        for (int t = 0; t < len && st == FUSE_OK; ++t, ++forked)
+            st = batch_iterate(b, b->cap_stream, false, cold && t == 0, true, t > 0);
+        // the side branch of the last iteration joins the loop's stream before the capture ends
+        if (forked && cudaStreamWaitEvent(b->cap_stream, b->side.join, 0) != cudaSuccess && st == FUSE_OK)
+            st = bfail(b, FUSE_ECUDA, "cudaStreamWaitEvent");
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
         if (st != FUSE_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -1458,7 +1515,7 @@ fuse_status fuse_init(fuse_ctx** out, const fuse_geometry* g, const double* blur
 
     auto bail = [&](fuse_status s) { release(c); delete c; return s; };
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); return bail(FUSE_ECUDA); }
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess || !c->side.create()) {
         cudaGetLastError();
         return bail(FUSE_ECUDA);
     }
@@ -2140,8 +2197,10 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
         if (c->htapsT != c0->htapsT) b->same_taps = false;
     b->fc_cw = c0->dtype == FUSE_F64 ? 4 : 8;
     if (cudaSetDevice(b->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess || !b->side.create()) {
         cudaGetLastError();
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        b->side.destroy();
         delete b;
         return FUSE_ECUDA;
     }
@@ -2150,6 +2209,7 @@ fuse_status fuse_batch_create(fuse_batch** out, fuse_ctx* const* ctxs, int n, vo
     if (st != FUSE_OK) {
         batch_release(b);
         cudaStreamDestroy(b->cap_stream);
+        b->side.destroy();
         delete b;
         return st;
     }
@@ -2284,7 +2344,7 @@ fuse_status fuse_batch_autotune(fuse_batch* b, const void* const* Yl, const void
         st = bfail(b, FUSE_ECUDA, "cudaEventCreate");
     double best = 1e30;
     int bt = b->lat_target, bs = b->lat_stages, bb = b->lat_bpb;
-    const int threads[] = {128, 160, 192, 256}, stages[] = {6, 8, 12, 16}, bands[] = {1, 2, 4};
+    const int threads[] = {128, 160, 192, 256}, stages[] = {6, 8, 12, 16}, bands[] = {1, 2, 4, 8};
     for (int th : threads)
         for (int sg : stages)
             for (int bd : bands) {
@@ -2354,6 +2414,7 @@ fuse_status fuse_batch_destroy(fuse_batch* b) {
     cudaStreamSynchronize(b->stream);
     batch_release(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    b->side.destroy();
     delete b;
     return FUSE_OK;
 }

@@ -36,6 +36,40 @@ __device__ __forceinline__ void load_tile(const T* __restrict__ in, int H, int W
     }
 }
 
+// load_tile for a tile shape fixed at compile time (TH x TW, block ST_TX x ST_BY): every load of a
+// thread is issued before any of its shared-memory stores, so a thread has all of its
+// ceil(TH / ST_BY) * ceil(TW / ST_TX) loads in flight at once.
+template <typename T, int TH, int TW>
+__device__ __forceinline__ void load_tile_ct(const T* __restrict__ in, int H, int W, int y0, int x0, int rh, int rw,
+                                             T* tile, int pitch) {
+    constexpr int NR = (TH + ST_BY - 1) / ST_BY, NC = (TW + ST_TX - 1) / ST_TX;
+    const bool near = y0 - rh >= -H && y0 - rh + TH <= 2 * H && x0 - rw >= -W && x0 - rw + TW <= 2 * W;
+    T v[NR][NC];
+    int col[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int cc = threadIdx.x + j * ST_TX;
+        col[j] = near ? wrap1(x0 - rw + cc, W) : wrapn(x0 - rw + cc, W);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int rr = threadIdx.y + i * ST_BY;
+        const T* row = in + (size_t)(near ? wrap1(y0 - rh + rr, H) : wrapn(y0 - rh + rr, H)) * W;
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+            if (rr < TH && threadIdx.x + j * ST_TX < TW) v[i][j] = row[col[j]];
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int rr = threadIdx.y + i * ST_BY;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int cc = threadIdx.x + j * ST_TX;
+            if (rr < TH && cc < TW) tile[rr * pitch + cc] = v[i][j];
+        }
+    }
+}
+
 template <typename T>
 struct StencilArgs {
     const T* in;
@@ -73,19 +107,20 @@ __device__ __forceinline__ void stencil_store(const StencilArgs<T>& a, const T (
     }
 }
 
-// Writes four consecutive outputs (row y, columns x..x+3, x % 4 == 0, W % 4 == 0) of band c as
-// 16-byte vectors; MODE 1 adds U2 and the adjoint sum R of the latent planes, each read as a
-// vector of the same four columns (the same terms in the same order as stencil_store).
+// The part of four consecutive outputs (row y, columns x..x+3, x % 4 == 0, W % 4 == 0) of band c
+// that does not depend on the blur: MODE 1 adds U2 and the adjoint sum R of the latent planes,
+// each read as a vector of the same four columns (the same terms in the same order as
+// stencil_store); MODE 0 adds nothing.  Read before the blur's tile, so these loads and the
+// tile's are in flight together.
 template <typename T, int MODE>
-__device__ __forceinline__ void stencil_store4(const StencilArgs<T>& a, const T (&acc)[4], int x, int y, int c) {
-    const int H = a.H, W = a.W, S = a.S, half = a.half;
-    const size_t n = (size_t)H * W;
-    const int side = 2 * S + 1;
-    const size_t pix = (size_t)y * W + x;
-    T val[4];
+__device__ __forceinline__ void stencil_pre4(const StencilArgs<T>& a, int x, int y, int c, T (&pre)[4]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) val[q] = acc[q];
+    for (int q = 0; q < 4; ++q) pre[q] = T(0);
     if constexpr (MODE == 1) {
+        const int H = a.H, W = a.W, S = a.S, half = a.half;
+        const size_t n = (size_t)H * W;
+        const int side = 2 * S + 1;
+        const size_t pix = (size_t)y * W + x;
         const T* pc = a.planes + (size_t)c * 2 * side * n;
         T rs[4] = {T(0), T(0), T(0), T(0)};
         for (int t1 = half ? 0 : -S; t1 <= S; ++t1) {
@@ -101,9 +136,19 @@ __device__ __forceinline__ void stencil_store4(const StencilArgs<T>& a, const T 
         T u2[4];
         vload<T, 4>(a.U2 + (size_t)c * n + pix, u2);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) val[q] += u2[q] + (half ? T(2) * rs[q] : rs[q]);
+        for (int q = 0; q < 4; ++q) pre[q] = u2[q] + (half ? T(2) * rs[q] : rs[q]);
     }
-    vstore<T, 4>(a.out + (size_t)c * n + pix, val);
+}
+
+// Writes the four outputs acc + pre as one 16-byte vector (pre from stencil_pre4; MODE 0: acc).
+template <typename T, int MODE>
+__device__ __forceinline__ void stencil_store4(const StencilArgs<T>& a, const T (&acc)[4], const T (&pre)[4], int x,
+                                               int y, int c) {
+    const size_t pix = (size_t)y * a.W + x;
+    T val[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) val[q] = MODE == 1 ? acc[q] + pre[q] : acc[q];
+    vstore<T, 4>(a.out + (size_t)c * a.H * a.W + pix, val);
 }
 
 // Each thread computes QY = 4 vertically adjacent outputs; for every tap column v it holds the
@@ -246,10 +291,15 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
     T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TP]
     T* hs = tile + stencil_sep_hs_offset<T, B>();     // [TH][HP], 16-byte aligned
     const int x0 = bx * ST_TX, y0 = by * ST_TY;
-    const T* __restrict__ inc = a.in + (size_t)c * H * W;
-    load_tile<T>(inc, H, W, y0, x0, R, R, TH, TW, tile, TP);
-    __syncthreads();
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
+    const int vy = tid / CG, vx = (tid - vy * CG) * 4;
+    const int x = x0 + vx, y = y0 + vy;
+    const bool out = x < W && y < H;
+    T pre[4];
+    if (out) stencil_pre4<T, MODE>(a, x, y, c, pre);
+    const T* __restrict__ inc = a.in + (size_t)c * H * W;
+    load_tile_ct<T, TH, TW>(inc, H, W, y0, x0, R, R, tile, TP);
+    __syncthreads();
     for (int it = tid; it < TH * CG; it += ST_TX * ST_BY) {
         const int r = it / CG, x = (it - r * CG) * 4;
         T w[4 + B - 1];
@@ -265,9 +315,7 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
         vstore<T, 4>(hs + r * HP + x, o);
     }
     __syncthreads();
-    const int vy = tid / CG, vx = (tid - vy * CG) * 4;
-    const int x = x0 + vx, y = y0 + vy;
-    if (x >= W || y >= H) return;
+    if (!out) return;
     T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int u = 0; u < B; ++u) {
@@ -276,7 +324,7 @@ __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const 
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += tp.cu[u] * h[q];
     }
-    stencil_store4<T, MODE>(a, acc, x, y, c);
+    stencil_store4<T, MODE>(a, acc, pre, x, y, c);
 }
 
 template <typename T, int MODE, int B>

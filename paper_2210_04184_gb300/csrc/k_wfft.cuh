@@ -290,6 +290,15 @@ __device__ __forceinline__ void wfft_cols(const FFTArgs<T>& a, int bx, int p, un
     }
 }
 
+// Occupancy of the FP32 passes: three 256-thread blocks per SM for the column pass (at most 80
+// registers a thread) where its body fits in them (P <= 12), four for the row passes (64); FP64
+// and larger P: the compiler's allocation.  The batched kernels take the P <= 12 bounds for every
+// block (a 512 side then spills a few registers in the column pass).
+template <typename T, int P>
+constexpr int wfft_cols_min_blocks() { return sizeof(T) == 4 && P <= 12 ? 3 : 1; }
+template <typename T, int PASS>
+constexpr int fft_batch_min_blocks() { return sizeof(T) != 4 ? 1 : PASS == 1 ? 3 : 4; }
+
 template <typename T>
 __host__ __device__ constexpr size_t wfft_cols_smem(int H) {
     return (size_t)H * (kWfftCols + 1) * sizeof(cplx<T>);
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(256) wfft_rows_fwd_kernel(FFTArgs<T> a) {
     if (y < a.H) wfft_row_fwd<T, P>(a, y, blockIdx.y, threadIdx.x & 31);
 }
 template <typename T, int P>
-__global__ void __launch_bounds__(256) wfft_cols_kernel(FFTArgs<T> a) {
+__global__ void __launch_bounds__(256, (wfft_cols_min_blocks<T, P>())) wfft_cols_kernel(FFTArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     wfft_cols<T, P>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
@@ -321,12 +330,12 @@ __global__ void __launch_bounds__(256) wfft_rows_inv_kernel(FFTArgs<T> a) {
 #define FUSE_WFFT_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(16)
 
 template <typename T, int PASS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (fft_batch_min_blocks<T, PASS>()))
 fft_batch_kernel(const FFTArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int prob, bx, by, bz;
     segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
-    const FFTArgs<T> a = args[prob];
+    const FFTArgs<T>& a = args[prob];        // read in place (a copy would live in local memory)
     if (a.fT == nullptr) {
         if constexpr (PASS == 0) fft_rows_fwd_body<T>(a, bx, by, smem_raw);
         else if constexpr (PASS == 1) fft_cols_body<T>(a, bx, by, smem_raw);
