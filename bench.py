@@ -583,7 +583,17 @@ def run_batch(a, rank, world, local_rank):
     del yl, yh, Zs
     torch.cuda.empty_cache()
     if not a.no_secondary and world == 1:
-        out["hsms_256"] = single_problem(a, "hsms_256", 0, None)
+        sec, (f1, p1, m1, yl1, yh1, Z1) = single_problem(a, "hsms_256", 0, None, keep=True)
+        if not a.no_fixed:
+            # the opt-in 16-bit latent state on the same workload, its error against the FP64 form
+            Z64 = None
+            if not a.no_fp64:
+                sec["fp64_compare"], Z64 = fp64_compare(p1, m1, f1, yl1, yh1, Z1)
+            sec["fixed_point_state"] = fixed_point_bench(a, p1, m1, yl1, yh1, Z64)
+        f1.close()
+        del yl1, yh1, Z1
+        torch.cuda.empty_cache()
+        out["hsms_256"] = sec
     if not a.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(ps[0], crop=min(p.H for p in ps))
     print(json.dumps(out), flush=True)

@@ -504,8 +504,15 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     }
 }
 
+// Register cap: 112 with the state in the iterate type (2 blocks of 288 threads, or 3 of 192, fit
+// the 64K registers); 96 with the 16-bit state, which is latency-bound rather than DRAM-bound and
+// gains from resident warps (measured at hsms_256: 0.80 ms per launch at 96, 0.92 at 112 and at
+// 80, where it spills).
+template <typename ST>
+constexpr int latent_max_regs() { return sizeof(ST) == 2 ? 96 : 112; }
+
 template <typename T, typename WT, int K, int VEC, typename ST = T>
-__global__ void __maxnreg__(112) latent_tma_kernel(LatentArgs<T, WT> args) {
+__global__ void __maxnreg__(latent_max_regs<ST>()) latent_tma_kernel(LatentArgs<T, WT> args) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
     latent_tma_body<T, WT, K, VEC, ST>(args, blockIdx.x, blockIdx.y, blockIdx.z, smem_tma);
 }
@@ -522,7 +529,7 @@ __global__ void __launch_bounds__(288, 1) latent_tma_monitor_kernel(LatentArgs<T
 // by the segment table; every problem's launch shape fits the common block size and shared
 // memory size of the launch.  zero_in applies to every problem (see LatentArgs).
 template <typename T, typename WT, int K, int VEC, typename ST = T>
-__global__ void __maxnreg__(112)
+__global__ void __maxnreg__(latent_max_regs<ST>())
 latent_tma_batch_kernel(const LatentArgs<T, WT>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
                         int zero_in) {
     extern __shared__ __align__(128) unsigned char smem_tma[];
