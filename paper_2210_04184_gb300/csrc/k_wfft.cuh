@@ -251,16 +251,23 @@ __device__ __forceinline__ void wfft_row_inv(const FFTArgs<T>& a, int y, int p, 
 template <typename T, int P>
 __device__ __forceinline__ void wfft_cols(const FFTArgs<T>& a, int bx, int p, unsigned char* smem_raw) {
     constexpr int CW = kWfftCols, PITCH = kWfftCols + 1;
+    // H = 32 P rows of CW columns over the block's 256 threads: P values per thread, all loaded
+    // before the first shared store
+    constexpr int NL = 32 * P * CW / 256;
+    static_assert(NL * 256 == 32 * P * CW, "256 threads cover the tile");
     cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
     const int H = a.H, W = a.W;
     const size_t n = (size_t)H * W;
     const int q0 = bx * CW;
     cplx<T>* Yp = a.Y + (size_t)p * n;
-    for (int idx = threadIdx.x; idx < H * CW; idx += blockDim.x) {
-        const int row = idx / CW, cc = idx - row * CW;
-        const int q = q0 + cc;
-        tile[row * PITCH + cc] = q < W ? ldc(Yp + (size_t)row * W + q) : cplx<T>{T(0), T(0)};
-    }
+    const int cc = threadIdx.x % CW, r0 = threadIdx.x / CW;
+    const bool inq = q0 + cc < W;
+    cplx<T> ld[NL];
+#pragma unroll
+    for (int i = 0; i < NL; ++i)
+        ld[i] = inq ? ldc(Yp + (size_t)(r0 + i * (256 / CW)) * W + q0 + cc) : cplx<T>{T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < NL; ++i) tile[(r0 + i * (256 / CW)) * PITCH + cc] = ld[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
     const int q = q0 + c;
@@ -283,10 +290,12 @@ __device__ __forceinline__ void wfft_cols(const FFTArgs<T>& a, int bx, int p, un
         for (int j = 0; j < P; ++j) tile[(lane + 32 * j) * PITCH + c] = v[j];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < H * CW; idx += blockDim.x) {
-        const int row = idx / CW, cc = idx - row * CW;
-        const int q = q0 + cc;
-        if (q < W) stc(Yp + (size_t)row * W + q, tile[row * PITCH + cc]);
+    if (inq) {
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int row = r0 + i * (256 / CW);
+            stc(Yp + (size_t)row * W + q0 + cc, tile[row * PITCH + cc]);
+        }
     }
 }
 
