@@ -1111,6 +1111,8 @@ struct fuse_batch {
     // device tables: [args of every problem] and segments per kernel
     void* d_lat = nullptr; Segment* d_lat_seg = nullptr; int lat_nseg = 0, lat_blocks = 0;
     void* d_st1 = nullptr; void* d_st0 = nullptr; Segment* d_st_seg = nullptr; int st_nseg = 0, st_blocks = 0;
+    // separable B X: blocks of stencil_sep_bands bands (band groups in z)
+    Segment* d_sep0_seg = nullptr; int sep0_nseg = 0, sep0_blocks = 0;
     void* d_fft = nullptr; Segment* d_fr_seg = nullptr; Segment* d_fc_seg = nullptr;
     int fr_nseg = 0, fr_blocks = 0, fc_nseg = 0, fc_blocks = 0;
     void* d_px = nullptr; Segment* d_px_seg = nullptr; int px_nseg = 0, px_blocks = 0;
@@ -1225,6 +1227,19 @@ struct BatchImpl {
         if ((st = bupload(b, &b->d_st1, s1)) != FUSE_OK) return st;
         if ((st = bupload(b, &b->d_st0, s0)) != FUSE_OK) return st;
         if ((st = bupload(b, (void**)&b->d_st_seg, seg)) != FUSE_OK) return st;
+        {
+            constexpr int NB = stencil_sep_bands<T, 0>();
+            std::vector<Segment> sg;
+            int nx = 0;
+            for (int i = 0; i < n; ++i) {
+                fuse_ctx* c = b->ctx[i];
+                add_segment(sg, i, (c->W + ST_TX - 1) / ST_TX, (c->H + ST_TY - 1) / ST_TY, (b->Ls + NB - 1) / NB, 0,
+                            &nx);
+            }
+            b->sep0_nseg = (int)sg.size();
+            b->sep0_blocks = nx;
+            if ((st = bupload(b, (void**)&b->d_sep0_seg, sg)) != FUSE_OK) return st;
+        }
 
         // FFT passes: 256 threads; each problem in its context's form (register-resident: 8 rows
         // or 8 columns per block, one warp each; Stockham: rpb rows, tpr = 256 / rpb, or CW
@@ -1294,7 +1309,7 @@ struct BatchImpl {
         const bool sep = sq && c0->sep_blur && !c0->hsepT.empty();
         stencil_batch_launch<T, 1>((const StencilArgs<T>*)b->d_st1, b->d_st_seg, b->st_nseg, b->bh,
                                    sep ? c0->hsepT.data() : nullptr, sq ? c0->htapsT.data() : nullptr,
-                                   (unsigned)b->st_blocks, b->st_smem, s);
+                                   (unsigned)b->st_blocks, b->st_smem, s, b->Ls);
         const FFTArgs<T>* fa = (const FFTArgs<T>*)b->d_fft;
         fft_batch_launch<T>(fa, b->d_fr_seg, b->fr_nseg, 0, (unsigned)b->fr_blocks, b->fr_smem, s);
         fft_batch_launch<T>(fa, b->d_fc_seg, b->fc_nseg, 1, (unsigned)b->fc_blocks, b->fc_smem, s);
@@ -1305,9 +1320,10 @@ struct BatchImpl {
             BCK(b, cudaStreamWaitEvent(b->side.s, b->side.fork, 0));
             sp = b->side.s;
         }
-        stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, b->d_st_seg, b->st_nseg, b->bh,
-                                   sep ? c0->hsepB.data() : nullptr, sq ? c0->htapsB.data() : nullptr,
-                                   (unsigned)b->st_blocks, b->st_smem, sp);
+        stencil_batch_launch<T, 0>((const StencilArgs<T>*)b->d_st0, sep ? b->d_sep0_seg : b->d_st_seg,
+                                   sep ? b->sep0_nseg : b->st_nseg, b->bh, sep ? c0->hsepB.data() : nullptr,
+                                   sq ? c0->htapsB.data() : nullptr,
+                                   (unsigned)(sep ? b->sep0_blocks : b->st_blocks), b->st_smem, sp, b->Ls);
         pixel_batch_launch<T>((const PixelArgs<T>*)b->d_px, b->d_px_seg, b->px_nseg, b->Ls, (unsigned)b->px_blocks,
                               b->px_smem, sp);
         if (side) BCK(b, cudaEventRecord(b->side.join, b->side.s));

@@ -36,40 +36,6 @@ __device__ __forceinline__ void load_tile(const T* __restrict__ in, int H, int W
     }
 }
 
-// load_tile for a tile shape fixed at compile time (TH x TW, block ST_TX x ST_BY): every load of a
-// thread is issued before any of its shared-memory stores, so a thread has all of its
-// ceil(TH / ST_BY) * ceil(TW / ST_TX) loads in flight at once.
-template <typename T, int TH, int TW>
-__device__ __forceinline__ void load_tile_ct(const T* __restrict__ in, int H, int W, int y0, int x0, int rh, int rw,
-                                             T* tile, int pitch) {
-    constexpr int NR = (TH + ST_BY - 1) / ST_BY, NC = (TW + ST_TX - 1) / ST_TX;
-    const bool near = y0 - rh >= -H && y0 - rh + TH <= 2 * H && x0 - rw >= -W && x0 - rw + TW <= 2 * W;
-    T v[NR][NC];
-    int col[NC];
-#pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        const int cc = threadIdx.x + j * ST_TX;
-        col[j] = near ? wrap1(x0 - rw + cc, W) : wrapn(x0 - rw + cc, W);
-    }
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const int rr = threadIdx.y + i * ST_BY;
-        const T* row = in + (size_t)(near ? wrap1(y0 - rh + rr, H) : wrapn(y0 - rh + rr, H)) * W;
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-            if (rr < TH && threadIdx.x + j * ST_TX < TW) v[i][j] = row[col[j]];
-    }
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const int rr = threadIdx.y + i * ST_BY;
-#pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            const int cc = threadIdx.x + j * ST_TX;
-            if (rr < TH && cc < TW) tile[rr * pitch + cc] = v[i][j];
-        }
-    }
-}
-
 template <typename T>
 struct StencilArgs {
     const T* in;
@@ -276,72 +242,145 @@ __host__ __device__ constexpr int stencil_sep_hs_offset() {
     return (((ST_TY + B - 1) * ((ST_TX + B - 1) | 1)) + e - 1) / e * e;
 }
 
+// Bands per block of the separable kernel: B X (MODE 0) moves little per band, so a block takes
+// several bands and issues all of their tile loads before its first shared store; the right-hand
+// side (MODE 1) already has its plane loads in flight and keeps one band.
+template <typename T, int MODE>
+__host__ __device__ constexpr int stencil_sep_bands() { return MODE == 0 ? (sizeof(T) == 4 ? 4 : 2) : 1; }
+
+// Shared memory of one band: the haloed tile, then (16-byte aligned) the horizontal pass's rows.
 template <typename T, int B>
-constexpr size_t stencil_sep_smem() {
-    return ((size_t)stencil_sep_hs_offset<T, B>() + (size_t)(ST_TY + B - 1) * (ST_TX + 4)) * sizeof(T);
+__host__ __device__ constexpr int stencil_sep_band_elems() {
+    constexpr int e = (int)(16 / sizeof(T));
+    return (stencil_sep_hs_offset<T, B>() + (ST_TY + B - 1) * (ST_TX + 4) + e - 1) / e * e;
 }
 
+template <typename T, int B, int NB = 1>
+constexpr size_t stencil_sep_smem() {
+    return (size_t)NB * stencil_sep_band_elems<T, B>() * sizeof(T);
+}
+
+// The TH x TW tiles whose top-left element is (y0 - rh, x0 - rw), with circular indices, of bands
+// c0 .. c0 + NB - 1 (those below nbands) of the planes at `in` (plane stride H W), into
+// tile0 + b * stride (row pitch `pitch`); block ST_TX x ST_BY, shape fixed at compile time, so
+// every load of a thread is issued before any of its shared-memory stores.  The wrap is one
+// compare and select when the tile lies within one period of the plane, else the modulo.
+template <typename T, int TH, int TW, int NB>
+__device__ __forceinline__ void load_tiles_ct(const T* __restrict__ in, int H, int W, int c0, int nbands, int y0,
+                                              int x0, int rh, int rw, T* tile0, int stride, int pitch) {
+    constexpr int NR = (TH + ST_BY - 1) / ST_BY, NC = (TW + ST_TX - 1) / ST_TX;
+    const bool near = y0 - rh >= -H && y0 - rh + TH <= 2 * H && x0 - rw >= -W && x0 - rw + TW <= 2 * W;
+    const size_t n = (size_t)H * W;
+    T v[NB][NR][NC];
+    int col[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int cc = threadIdx.x + j * ST_TX;
+        col[j] = near ? wrap1(x0 - rw + cc, W) : wrapn(x0 - rw + cc, W);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int rr = threadIdx.y + i * ST_BY;
+        const size_t row = (size_t)(near ? wrap1(y0 - rh + rr, H) : wrapn(y0 - rh + rr, H)) * W;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int j = 0; j < NC; ++j)
+                if (c0 + b < nbands && rr < TH && threadIdx.x + j * ST_TX < TW)
+                    v[b][i][j] = in[(size_t)(c0 + b) * n + row + col[j]];
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int rr = threadIdx.y + i * ST_BY;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                const int cc = threadIdx.x + j * ST_TX;
+                if (c0 + b < nbands && rr < TH && cc < TW) tile0[b * stride + rr * pitch + cc] = v[b][i][j];
+            }
+        }
+}
+
+// Block (bx, by, cz): the 32 x 32 outputs at columns 32 bx, rows 32 by of the bands
+// cz NB .. cz NB + NB - 1 below nbands.  Per band a horizontal pass over its haloed tile (four
+// consecutive columns per work item) into its own shared rows, then the vertical pass with four
+// outputs per thread.
 template <typename T, int MODE, int B>
 __device__ __forceinline__ void stencil_sep_body(const StencilArgs<T>& a, const SepTaps<T, B>& tp, int bx, int by,
-                                                 int c, unsigned char* smem_raw) {
+                                                 int cz, int nbands, unsigned char* smem_raw) {
+    constexpr int NB = stencil_sep_bands<T, MODE>();
     constexpr int R = B / 2;
     constexpr int TH = ST_TY + B - 1, TW = ST_TX + B - 1, TP = TW | 1, HP = ST_TX + 4;
     constexpr int CG = ST_TX / 4;                     // four-column groups per row
+    constexpr int BS = stencil_sep_band_elems<T, B>();
     const int H = a.H, W = a.W;
-    T* tile = reinterpret_cast<T*>(smem_raw);         // [TH][TP]
-    T* hs = tile + stencil_sep_hs_offset<T, B>();     // [TH][HP], 16-byte aligned
+    T* tile0 = reinterpret_cast<T*>(smem_raw);        // band b: tile [TH][TP] at b BS, then hs [TH][HP]
     const int x0 = bx * ST_TX, y0 = by * ST_TY;
+    const int c0 = cz * NB;
     const int tid = threadIdx.y * ST_TX + threadIdx.x;
     const int vy = tid / CG, vx = (tid - vy * CG) * 4;
     const int x = x0 + vx, y = y0 + vy;
     const bool out = x < W && y < H;
-    T pre[4];
-    if (out) stencil_pre4<T, MODE>(a, x, y, c, pre);
-    const T* __restrict__ inc = a.in + (size_t)c * H * W;
-    load_tile_ct<T, TH, TW>(inc, H, W, y0, x0, R, R, tile, TP);
+    T pre[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        if (out && c0 + b < nbands) stencil_pre4<T, MODE>(a, x, y, c0 + b, pre[b]);
+    load_tiles_ct<T, TH, TW, NB>(a.in, H, W, c0, nbands, y0, x0, R, R, tile0, BS, TP);
     __syncthreads();
-    for (int it = tid; it < TH * CG; it += ST_TX * ST_BY) {
-        const int r = it / CG, x = (it - r * CG) * 4;
-        T w[4 + B - 1];
 #pragma unroll
-        for (int k = 0; k < 4 + B - 1; ++k) w[k] = tile[r * TP + x + k];
-        T o[4];
+    for (int b = 0; b < NB; ++b) {
+        if (c0 + b >= nbands) break;
+        const T* tile = tile0 + b * BS;
+        T* hs = tile0 + b * BS + stencil_sep_hs_offset<T, B>();    // 16-byte aligned
+        for (int it = tid; it < TH * CG; it += ST_TX * ST_BY) {
+            const int r = it / CG, xx = (it - r * CG) * 4;
+            T w[4 + B - 1];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            o[q] = T(0);
+            for (int k = 0; k < 4 + B - 1; ++k) w[k] = tile[r * TP + xx + k];
+            T o[4];
 #pragma unroll
-            for (int v = 0; v < B; ++v) o[q] += tp.cv[v] * w[q + v];
+            for (int q = 0; q < 4; ++q) {
+                o[q] = T(0);
+#pragma unroll
+                for (int v = 0; v < B; ++v) o[q] += tp.cv[v] * w[q + v];
+            }
+            vstore<T, 4>(hs + r * HP + xx, o);
         }
-        vstore<T, 4>(hs + r * HP + x, o);
     }
     __syncthreads();
     if (!out) return;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int u = 0; u < B; ++u) {
-        T h[4];
-        vload<T, 4>(hs + (vy + u) * HP + vx, h);
+    for (int b = 0; b < NB; ++b) {
+        if (c0 + b >= nbands) break;
+        const T* hs = tile0 + b * BS + stencil_sep_hs_offset<T, B>();
+        T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += tp.cu[u] * h[q];
+        for (int u = 0; u < B; ++u) {
+            T h[4];
+            vload<T, 4>(hs + (vy + u) * HP + vx, h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] += tp.cu[u] * h[q];
+        }
+        stencil_store4<T, MODE>(a, acc, pre[b], x, y, c0 + b);
     }
-    stencil_store4<T, MODE>(a, acc, pre, x, y, c);
 }
 
 template <typename T, int MODE, int B>
-__global__ void __launch_bounds__(256) stencil_sep_kernel(StencilArgs<T> a, SepTaps<T, B> taps) {
+__global__ void __launch_bounds__(256) stencil_sep_kernel(StencilArgs<T> a, SepTaps<T, B> taps, int nbands) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stencil_sep_body<T, MODE, B>(a, taps, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    stencil_sep_body<T, MODE, B>(a, taps, blockIdx.x, blockIdx.y, blockIdx.z, nbands, smem_raw);
 }
 
 template <typename T, int MODE, int B>
 __global__ void __launch_bounds__(256)
 stencil_sep_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* __restrict__ seg, int nseg,
-                         SepTaps<T, B> taps) {
+                         SepTaps<T, B> taps, int nbands) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int prob, bx, by, bz;
     segment_of_block(seg, nseg, blockIdx.x, &prob, &bx, &by, &bz);
     const StencilArgs<T> a = args[prob];
-    stencil_sep_body<T, MODE, B>(a, taps, bx, by, bz, smem_raw);
+    stencil_sep_body<T, MODE, B>(a, taps, bx, by, bz, nbands, smem_raw);
 }
 
 // C = G + U2 + R without a blur: the right-hand side of the variant that keeps S B in the X

@@ -57,9 +57,11 @@ void pixel_batch_launch(const PixelArgs<T>* args, const Segment* seg, int nseg, 
 template <typename T, int MODE>
 void stencil_launch(const StencilArgs<T>& a, int bh, const double* sep_host, const double* taps_host, dim3 grid,
                     size_t smem, cudaStream_t s);
+// nbands: the bands of every problem (the separable kernel takes stencil_sep_bands per block; its
+// segment table counts band groups, the other kernels' count bands).
 template <typename T, int MODE>
 void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* sep_host,
-                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s);
+                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s, int nbands);
 // Dynamic shared-memory cap of the stencil kernels for blur height bh and of the wide pixel kernel.
 template <typename T>
 cudaError_t pixel_stencil_set_smem(int bh, int bytes);
@@ -127,10 +129,10 @@ cudaError_t latent_bwd_set_smem(int K, int bytes);
                                               size_t, cudaStream_t);                                          \
     extern template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int,           \
                                                     const double*, const double*, unsigned, size_t,           \
-                                                    cudaStream_t);                                            \
+                                                    cudaStream_t, int);                                            \
     extern template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int,           \
                                                     const double*, const double*, unsigned, size_t,           \
-                                                    cudaStream_t);                                            \
+                                                    cudaStream_t, int);                                            \
     extern template cudaError_t pixel_stencil_set_smem<T>(int, int);                                          \
     extern template cudaError_t stencil_batch_set_smem<T>(int, int);                                          \
     extern template void pixel_bwd_launch<T>(const PixelBwdArgs<T>&, unsigned, cudaStream_t);                \

@@ -39,10 +39,14 @@ template <typename T, int MODE>
 void stencil_launch(const StencilArgs<T>& a, int bh, const double* sep_host, const double* taps_host, dim3 grid,
                     size_t smem, cudaStream_t s) {
     if (sep_host) {
+        // grid.z counts bands; the separable kernel takes stencil_sep_bands of them per block
+        constexpr int NB = stencil_sep_bands<T, MODE>();
+        const int nbands = (int)grid.z;
+        const dim3 g(grid.x, grid.y, (unsigned)((nbands + NB - 1) / NB));
         with_bh(bh, [&](auto b) {
             constexpr int B = decltype(b)::value;
-            stencil_sep_kernel<T, MODE, B><<<grid, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B>(), s>>>(
-                a, sep_taps<T, B>(sep_host));
+            stencil_sep_kernel<T, MODE, B><<<g, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B, NB>(), s>>>(
+                a, sep_taps<T, B>(sep_host), nbands);
         });
         return;
     }
@@ -62,12 +66,13 @@ void stencil_launch(const StencilArgs<T>& a, int bh, const double* sep_host, con
 
 template <typename T, int MODE>
 void stencil_batch_launch(const StencilArgs<T>* args, const Segment* seg, int nseg, int bh, const double* sep_host,
-                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s) {
+                          const double* taps_host, unsigned blocks, size_t smem, cudaStream_t s, int nbands) {
     if (sep_host) {
+        constexpr int NB = stencil_sep_bands<T, MODE>();
         with_bh(bh, [&](auto b) {
             constexpr int B = decltype(b)::value;
-            stencil_sep_batch_kernel<T, MODE, B><<<blocks, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B>(), s>>>(
-                args, seg, nseg, sep_taps<T, B>(sep_host));
+            stencil_sep_batch_kernel<T, MODE, B><<<blocks, dim3(ST_TX, ST_BY), stencil_sep_smem<T, B, NB>(), s>>>(
+                args, seg, nseg, sep_taps<T, B>(sep_host), nbands);
         });
         return;
     }
@@ -95,6 +100,8 @@ cudaError_t pixel_stencil_set_smem(int bh, int bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_kernel<T, 1, B>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 0, B>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_kernel<T, 1, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sep_kernel<T, 0, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sep_kernel<T, 1, B>, A, bytes);
     });
     return e;
 }
@@ -109,6 +116,8 @@ cudaError_t stencil_batch_set_smem(int bh, int bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_batch_kernel<T, 1, B>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_batch_kernel<T, 0, B>, A, bytes);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sq_batch_kernel<T, 1, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sep_batch_kernel<T, 0, B>, A, bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(stencil_sep_batch_kernel<T, 1, B>, A, bytes);
     });
     return e;
 }
@@ -122,9 +131,9 @@ cudaError_t stencil_batch_set_smem(int bh, int bytes) {
     template void stencil_launch<T, 1>(const StencilArgs<T>&, int, const double*, const double*, dim3, size_t,   \
                                        cudaStream_t);                                                           \
     template void stencil_batch_launch<T, 0>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
-                                             const double*, unsigned, size_t, cudaStream_t);                    \
+                                             const double*, unsigned, size_t, cudaStream_t, int);               \
     template void stencil_batch_launch<T, 1>(const StencilArgs<T>*, const Segment*, int, int, const double*,     \
-                                             const double*, unsigned, size_t, cudaStream_t);                    \
+                                             const double*, unsigned, size_t, cudaStream_t, int);               \
     template cudaError_t pixel_stencil_set_smem<T>(int, int);                                                   \
     template cudaError_t stencil_batch_set_smem<T>(int, int);
 
