@@ -6,8 +6,8 @@
 //         (half-window mode: tau1 >= 0 only and R doubled, see k_latent.cuh)
 //         the right-hand side C = B^T(P1 + Lambda1) + P2 + Lambda2 + sum D^T(Q + Sigma)
 //         (Sec. IV-A, after eq. x_linear_system_main), with R from the latent pass planes.
-// Tiles of 32 x 32 pixels of one band; the halo is loaded with circular wrap.  Blur sizes are
-// odd and at most 15 x 15.
+// Tiles of 32 x 32 pixels of one band (the separable B X kernel: of several bands per block); the
+// halo is loaded with circular wrap.  Blur sizes are odd and at most 15 x 15.
 #pragma once
 #include "common.cuh"
 
@@ -226,9 +226,9 @@ stencil_sq_batch_kernel(const StencilArgs<T>* __restrict__ args, const Segment* 
 // with the vertical halo, four consecutive columns per work item), then a vertical pass,
 // out(y, x) = sum_u cu(u) hs(y + u, x), again four consecutive columns per thread, so that the
 // rows of hs, the latent planes, U2 and the output move as 16-byte vectors: B (2 + (B - 1)/32)
-// multiply-adds per output instead of B^2.  Shared memory: the tile at an odd pitch (TW | 1, so
-// the four-column items of a warp hit distinct banks in the first pass), then hs at pitch
-// ST_TX + 4 (rows 16-byte aligned).  Needs W % 4 == 0.
+// multiply-adds per output instead of B^2.  Shared memory per band: the tile at an odd pitch
+// (TW | 1, so the four-column items of a warp hit distinct banks in the first pass), then hs at
+// pitch ST_TX + 4 (rows 16-byte aligned).  Needs W % 4 == 0.
 template <typename T, int B>
 struct SepTaps {
     T cu[B], cv[B];
