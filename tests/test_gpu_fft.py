@@ -67,3 +67,28 @@ def test_fft_form_option():
     assert other.get_option(FUSE_OPT_FFT_IMPL) == 0       # 40 = 32 P has no integer P
     with pytest.raises(FuseError):
         other.set_option(FUSE_OPT_FFT_IMPL, 1)
+
+
+def test_switching_the_form_recaptures_the_loop():
+    # a solve, a switch of the DFT form on the same context, another solve: each equals a fresh
+    # context of that form bit for bit (the captured iteration loop is dropped on the switch)
+    p = small(H=96, W=64, L_l=5, L_h=2, L_s=3, K=1, S=1, blur_size=5)
+    yl = torch.tensor(p.Yl, dtype=torch.float32, device="cuda")
+    yh = torch.tensor(p.Yh, dtype=torch.float32, device="cuda")
+
+    def solve(f):
+        X, _ = f.solve(yl, yh, 4)
+        f.sync()
+        return X.clone()
+
+    f = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+    f.weights(yh)
+    a1 = solve(f)
+    f.set_option(FUSE_OPT_FFT_IMPL, 0)
+    a0 = solve(f)
+    for form, got in ((1, a1), (0, a0)):
+        g = Fusion.from_problem(p, dtype="f32", wdtype="f32")
+        g.set_option(FUSE_OPT_FFT_IMPL, form)
+        g.weights(yh)
+        assert torch.equal(solve(g), got)
+    assert not torch.equal(a0, a1)          # the two forms round differently

@@ -361,12 +361,13 @@ def test_non_separable_square_blur(dtype):
     assert rel(g["X"], Xo) <= (1e-11 if dtype == "f64" else 1e-5)
 
 
-@pytest.mark.parametrize("bsize,sigma", [(9, 1.7), (5, 1.0), (11, 2.0), (3, 0.8)])
-def test_separable_blur_equals_2d_stencil(bsize, sigma):
+@pytest.mark.parametrize("bsize,sigma,Ls", [(9, 1.7, 4), (5, 1.0, 4), (11, 2.0, 4), (3, 0.8, 4), (9, 1.7, 5)])
+def test_separable_blur_equals_2d_stencil(bsize, sigma, Ls):
     # a Gaussian blur factors as cu(u) cv(v): the separable passes and the 2D stencil apply the same
-    # operator up to rounding (FP64, 12 iterations); the separable path also matches the oracle
+    # operator up to rounding (FP64, 12 iterations); the separable path also matches the oracle.
+    # L_s = 5 leaves the last block of the several-bands-per-block B X kernel one band.
     from paper_2210_04184_gb300.fuse import FUSE_OPT_SEPARABLE_BLUR
-    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=4, blur_size=bsize, blur_sigma=sigma)
+    p = small(K=2, S=3, H=48, W=64, L_l=8, L_h=3, L_s=Ls, blur_size=bsize, blur_sigma=sigma)
     a = gpu_solve(p, 12, dtype="f64", wdtype="f64")["X"]
     b = gpu_solve(p, 12, dtype="f64", wdtype="f64", opts=[(FUSE_OPT_SEPARABLE_BLUR, 0)])["X"]
     assert rel(a, b) <= 1e-13
