@@ -294,9 +294,10 @@ fuse_status fuse_profile(fuse_ctx* ctx, int which, double* ms, long long* launch
 
 /* The regulariser value phi(X) = sum_i sum_{tau in W} omega_{i tau} ||P_{i tau}(X)||_1 written
  * to phi_dev[0] (device, one double), without allocating anything.  The paper has no
- * counterpart: this entry point exists for callers that may not allocate device memory
- * (for example while their stream is being captured into a CUDA graph, or inside a host
- * application that owns a fixed GPU memory budget) and so cannot create a fuse_ctx.
+ * counterpart: this entry point exists for callers that may not allocate device memory and
+ * so cannot create a fuse_ctx: a host application that owns a fixed GPU memory budget and
+ * hands out every byte itself, or a loop with a latency bound that cannot afford cudaMalloc's
+ * implicit device synchronisation.
  *   X_dev      [L_s][H][W] of dtype (FUSE_F32 or FUSE_F64), device
  *   omega_dev  [|W|][H][W] of wdtype (FUSE_F32/FUSE_BF16 with FUSE_F32, FUSE_F64 with FUSE_F64),
  *              as produced by fuse_weights / read by fuse_get_weights

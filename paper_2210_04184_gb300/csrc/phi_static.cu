@@ -1,12 +1,12 @@
 // fuse_phi_static: the regulariser value phi(X) of eq. reg1 without any allocation.
 //
-// Who needs it: code that must not call cudaMalloc, for example a caller recording work
-// into another component's CUDA graph (device allocation is not allowed while a stream is
-// being captured), or a host application that gives the GPU a fixed memory budget and owns
-// every allocation itself.  Such a caller cannot create a fuse_ctx (fuse_init allocates), so
-// this entry point takes plain device pointers and keeps its only scratch - the per-block
-// partial sums - in a file-scope device array of fixed size, resident on every GPU that loads
-// the library until the process exits.
+// Who needs it: code that must not call cudaMalloc, for example a host application that
+// gives the GPU a fixed memory budget and owns every allocation itself, or a loop with a
+// latency bound that cannot afford the device synchronisation cudaMalloc may imply.  Such a
+// caller cannot create a fuse_ctx (fuse_init allocates), so this entry point takes plain
+// device pointers and keeps its only scratch - the per-block partial sums - in a file-scope
+// device array of fixed size, resident on every GPU that loads the library until the process
+// exits.
 #include "fuse.h"
 
 #include <cuda_runtime.h>
@@ -25,8 +25,7 @@ static __device__ __align__(256) double g_phi_scratch[kPhiStaticPartials];
 
 // Per-device address of g_phi_scratch (host code only sees a host-side stand-in for the
 // symbol, so the device address is looked up with that device current).  A successful lookup is
-// kept; a failed one is not, so a later call (for example one made outside a stream capture)
-// tries again.
+// kept; a failed one is not, so a later call tries again.
 double* g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 

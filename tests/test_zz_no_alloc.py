@@ -1,8 +1,9 @@
 """fuse_phi_static: the regulariser value without any device allocation, for callers that may
-not allocate (e.g. while their stream is captured into a CUDA graph, or under a host-owned GPU
-memory budget).  Checked through the C-ABI against fuse_objective's regulariser term on two
-calls in a row (the second call finds the previous call's partial sums in the shared array), and
-against the FP64 oracle's phi (eq. reg1) evaluated on the same X and weights copied to the host."""
+not allocate (under a host-owned GPU memory budget, or where cudaMalloc's implicit device
+synchronisation is not affordable).  Checked through the C-ABI against fuse_objective's
+regulariser term on two calls in a row (the second call finds the previous call's partial sums
+in the shared array), and against the FP64 oracle's phi (eq. reg1) evaluated on the same X and
+weights copied to the host."""
 import numpy as np
 import pytest
 
