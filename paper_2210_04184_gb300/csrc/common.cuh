@@ -48,6 +48,33 @@ __device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
 
+// The symmetric clamp clamp(u, -m, m) of the soft threshold, for a bound m >= 0 prepared once
+// per weight and applied to many entries.  FP32: fmaxf then fminf.  FP64: GB300 runs FP64
+// arithmetic, minimum and maximum included, at a small fraction of its FP32 rate, so the clamp
+// is taken on the IEEE-754 bit patterns with integer operations instead: for non-negative
+// doubles the order of the values is the order of their bit patterns read as unsigned integers,
+// so |u| <= m exactly when the magnitude bits of u are at most those of m, and then the result
+// is u, else m with the sign of u.  Same value as fmin(fmax(u, -m), m) for every u that is not
+// NaN and every m >= 0 (the bound's sign bit is cleared, so m = -0 acts as +0).
+template <typename T> struct SymBound;
+template <> struct SymBound<float> {
+    float m;
+    __device__ __forceinline__ static SymBound of(float b) { return {b}; }
+    __device__ __forceinline__ float clamp(float u) const { return fminf(fmaxf(u, -m), m); }
+};
+template <> struct SymBound<double> {
+    unsigned long long mb;                        // magnitude bits of the bound
+    __device__ __forceinline__ static SymBound of(double b) {
+        return {(unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull};
+    }
+    __device__ __forceinline__ double clamp(double u) const {
+        const unsigned long long ub = (unsigned long long)__double_as_longlong(u);
+        return (ub & 0x7fffffffffffffffull) <= mb
+                   ? u
+                   : __longlong_as_double((long long)(mb | (ub & 0x8000000000000000ull)));
+    }
+};
+
 // Streaming (evict-first) 16-byte load/store of the latent state.
 __device__ __forceinline__ vecT<float, 4> ld_stream(const vecT<float, 4>* p) {
     float4 v = __ldcs(reinterpret_cast<const float4*>(p));

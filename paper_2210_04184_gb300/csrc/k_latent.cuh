@@ -81,10 +81,10 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* Si
             for (int k1 = -K; k1 <= K; ++k1) {
                 // mu for the output pixels i = m + k, k2 in [-K, K]: columns x0-K .. x0+VEC-1+K
                 const int yw = wrap1(y + k1, H);
-                T mu[VEC + 2 * K];
+                SymBound<T> mu[VEC + 2 * K];
 #pragma unroll
                 for (int j = 0; j < VEC + 2 * K; ++j)
-                    mu[j] = coef * (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W));
+                    mu[j] = SymBound<T>::of(coef * (T)wload(om + (size_t)yw * W + wrap1(x0 - K + j, W)));
                 // issue the 2K+1 loads of this patch row before any store
                 vecT<T, VEC> s[PS];
 #pragma unroll
@@ -94,8 +94,7 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* Si
 #pragma unroll
                     for (int j = 0; j < VEC; ++j) {
                         const T u = s[k2].v[j] - delta[j];         // -v
-                        const T m = mu[j + k2];
-                        const T s2 = tmin(tmax(u, -m), m);         // Sigma' = -clamp(v)
+                        const T s2 = mu[j + k2].clamp(u);          // Sigma' = -clamp(v)
                         Hacc[j] += T(2) * s2 - u;                  // G = v + 2 Sigma'
                         s[k2].v[j] = s2;
                     }
@@ -347,9 +346,9 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
 #pragma unroll
             for (int k1 = 0; k1 < PS; ++k1) {
                 if constexpr (std::is_same<ST, T>::value) {
-                    T mu[VEC + 2 * K];
+                    SymBound<T> mu[VEC + 2 * K];
 #pragma unroll
-                    for (int j = 0; j < VEC + 2 * K; ++j) mu[j] = active ? coef * (T)wr.get(j) : T(0);
+                    for (int j = 0; j < VEC + 2 * K; ++j) mu[j] = SymBound<T>::of(active ? coef * (T)wr.get(j) : T(0));
                     // the next weight row: row k1 + 1, or the first row of the next tau2
                     if (active) {
                         if (k1 + 1 < PS) wr.load(om + (size_t)wrap1(y + k1 + 1 - K, H) * W, x0, W);
@@ -372,8 +371,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
 #pragma unroll
                             for (int j = 0; j < VEC; ++j) {
                                 const T u = sv[j] - delta[j];
-                                const T m = mu[j + k2];
-                                const T s2 = tmin(tmax(u, -m), m);
+                                const T s2 = mu[j + k2].clamp(u);
                                 Hacc[j] += T(2) * s2 - u;
                                 if constexpr (MON) {
                                     Macc[j] += s2 + sv[j] - u;              // Q' + Sigma
