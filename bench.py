@@ -584,11 +584,11 @@ def run_batch(a, rank, world, local_rank):
     torch.cuda.empty_cache()
     if not a.no_secondary and world == 1:
         sec, (f1, p1, m1, yl1, yh1, Z1) = single_problem(a, "hsms_256", 0, None, keep=True)
+        Z64 = None
+        if not a.no_fp64:
+            sec["fp64_compare"], Z64 = fp64_compare(p1, m1, f1, yl1, yh1, Z1)
         if not a.no_fixed:
             # the opt-in 16-bit latent state on the same workload, its error against the FP64 form
-            Z64 = None
-            if not a.no_fp64:
-                sec["fp64_compare"], Z64 = fp64_compare(p1, m1, f1, yl1, yh1, Z1)
             sec["fixed_point_state"] = fixed_point_bench(a, p1, m1, yl1, yh1, Z64)
         f1.close()
         del yl1, yh1, Z1
