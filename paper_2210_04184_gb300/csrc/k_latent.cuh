@@ -146,6 +146,17 @@ latent_kernel(const T* __restrict__ X, const WT* __restrict__ omega, const T* Si
 
 namespace fuse {
 
+// Position, in a row interleaved by VEC (element x at (x mod VEC) tpr + x / VEC, tpr = W / VEC), of
+// the element x0 + q (circular in the row) for the thread with x0 = VEC tcol: word
+// (q mod VEC) tpr + (tcol + floor(q / VEC)) mod tpr, since W and x0 are multiples of VEC.  One
+// wrap suffices: |floor(q / VEC)| <= tpr for the shifts used here (|q| <= S + VEC - 1, W >= 2S + 1).
+template <int VEC>
+__device__ __forceinline__ int ishift(int tcol, int q, int tpr) {
+    static_assert((VEC & (VEC - 1)) == 0, "VEC is a power of two");
+    constexpr int LV = VEC == 8 ? 3 : VEC == 4 ? 2 : VEC == 2 ? 1 : 0;
+    return (q & (VEC - 1)) * tpr + wrap1(tcol + (q >> LV), tpr);
+}
+
 template <typename T, typename WT>
 struct LatentArgs {
     const T* X;
@@ -199,6 +210,10 @@ struct WRow {
 // for every tau2; per tau2 each consumer adds its H_tau to A in registers and publishes it in one
 // of two shared tiles (alternating), and after one named barrier (the producer never waits on it)
 // adds the shifted H_tau(m + (0, tau2)) of its row to its entries of the V tile (Vs).
+// The shifted tiles (Xs and the H tiles, read at x0 + j -+ tau2 by the thread owning x0 .. x0 +
+// VEC - 1) hold each row interleaved: element x of a row at (x mod VEC) tpr + x / VEC, tpr = W /
+// VEC, so for a fixed j the threads of a row access consecutive words (the natural layout puts
+// them VEC words apart, a VEC-way bank conflict on every such access).
 // Shared memory: ring [D][Ty][W] (storage type), then the tiles Xo, Vs, two H tiles, Xs and with
 // MON two tiles of the monitoring sums, each [Ty][W] of T (W % 8 == 0 keeps every tile a
 // multiple of 32 bytes, so the 16-byte vector accesses stay aligned), then the 2D mbarriers.
@@ -295,6 +310,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
     const int x0 = (tid - r * tpr) * VEC;
     const int y = y0 + r;
     const bool owner = tid < tpr * Ty;
+    const int tcol = x0 / VEC;                           // the thread's word in each interleaved row
     const bool active = owner && r < rows;
     const size_t pix = (size_t)y * W + x0;
     const size_t kstride = (size_t)Ls * n;
@@ -314,7 +330,8 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             vload<T, VEC>(Xc + pix, xr);
             vstore<T, VEC>(xo, xr);
             vload<T, VEC>(Xc + xsrow + x0, xr);
-            vstore<T, VEC>(Xs + (size_t)r * W + x0, xr);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) Xs[(size_t)r * W + j * tpr + tcol] = xr[j];
 #pragma unroll
             for (int j = 0; j < VEC; ++j) xr[j] = T(0);
             vstore<T, VEC>(vs, xr);
@@ -338,7 +355,7 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
             for (int j = 0; j < VEC; ++j) {
                 Hacc[j] = T(0);
                 if constexpr (MON) Macc[j] = T(0);
-                delta[j] = active ? delta[j] - Xs[(size_t)r * W + wrap1(x0 + j - t2, W)] : T(0);
+                delta[j] = active ? delta[j] - Xs[(size_t)r * W + ishift<VEC>(tcol, j - t2, tpr)] : T(0);
             }
             const WT* om = omega + (size_t)tm.w_index(t1, t2) * n;
             const WT* om_next = jt + 1 < nt2 ? omega + (size_t)tm.w_index(t1, tm.t2_of(t1, jt + 1)) * n : om;
@@ -453,10 +470,10 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
                     A[j] += Hacc[j];
-                    ht[x0 + j] = Hacc[j];
+                    ht[j * tpr + tcol] = Hacc[j];
                     if constexpr (MON) {
                         A2[j] += Macc[j];
-                        mt[x0 + j] = Macc[j];
+                        mt[j * tpr + tcol] = Macc[j];
                     }
                 }
             }
@@ -467,8 +484,9 @@ __device__ __forceinline__ void latent_tma_body(const LatentArgs<T, WT>& args, i
                 vload<T, VEC>(vs, v);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    v[j] += ht[wrap1(x0 + j + t2, W)];
-                    if constexpr (MON) V2[j] += mt[wrap1(x0 + j + t2, W)];
+                    const int e = ishift<VEC>(tcol, j + t2, tpr);
+                    v[j] += ht[e];
+                    if constexpr (MON) V2[j] += mt[e];
                 }
                 vstore<T, VEC>(vs, v);
             }
