@@ -44,9 +44,9 @@ NOMINAL_HBM_GBS = 7900.0
 # the kernel has changed since the counters were taken).
 LATENT_TRAFFIC = {
     # latent_tma_kernel, hsms_128 (FP32 state, BF16 weights, K = 2, S = 3, L_s = 20)
-    "hsms": {"bytes_per_pixel": (788.640512e6 + 735.602944e6) / (128 * 128), "sources": "b2c7bb3ded49df13"},
+    "hsms": {"bytes_per_pixel": (788.716800e6 + 736.075008e6) / (128 * 128), "sources": "bd69776d19227011"},
     # latent_tma_batch_kernel, the batch workload's first 8 problems (K = 1, S = 3, L_s = 8)
-    "batch": {"bytes_per_pixel": (4.697224e9 + 4.728260e9) / 667648, "sources": "b2c7bb3ded49df13"},
+    "batch": {"bytes_per_pixel": (4.697702656e9 + 4.726860800e9) / 667648, "sources": "bd69776d19227011"},
 }
 LATENT_SOURCES = ("k_latent.cuh", "tma.cuh", "common.cuh", "launch_latent.cu")
 UNIT = "Mpx*band*iter/s"
