@@ -1,5 +1,6 @@
 """bench.py's host-side formulas: the algorithmic bytes of a latent launch counted element by
-element on small shapes, and the weak-scaling value."""
+element on small shapes, the weak-scaling value, and the stored DRAM traffic of the latent
+captures (reported only for the sources it was taken on)."""
 import pathlib
 import sys
 
@@ -43,3 +44,26 @@ def test_benchmark_latent_bytes():
 def test_job_value_and_single_rank_max():
     assert bench.job_value(10.0, 4, 2.0) == 20.0
     assert bench.max_over_ranks(3.5, None) == 3.5
+
+
+def test_stored_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    # the stored DRAM traffic scales with the pixel count while the latent sources match the
+    # digest recorded with the capture, and is withheld (None) once they differ
+    t = bench.LATENT_TRAFFIC["batch"]
+    monkeypatch.setattr(bench, "_sources_digest", lambda: t["sources"])
+    a = bench.latent_traffic("batch", 1000)
+    assert a == pytest.approx(t["bytes_per_pixel"] * 1000)
+    assert bench.latent_traffic("batch", 2000) == pytest.approx(2 * a)
+    monkeypatch.setattr(bench, "_sources_digest", lambda: "0" * 16)
+    assert bench.latent_traffic("batch", 1000) is None
+    assert bench.latent_traffic("no such kernel", 1000) is None
+
+
+def test_stored_traffic_is_close_to_the_algorithmic_bytes():
+    # each capture moved close to the algorithmic bytes of its workload (no wasted re-reads)
+    p, _ = synth.workload("hsms_256")
+    alg = bench.latent_bytes(p, 4, 2) / (p.H * p.W)
+    assert 0.9 <= bench.LATENT_TRAFFIC["hsms"]["bytes_per_pixel"] / alg <= 1.05
+    ps = synth.batch_workload(8)
+    alg8 = sum(bench.latent_bytes(q, 4, 2) for q in ps) / sum(q.H * q.W for q in ps)
+    assert 0.95 <= bench.LATENT_TRAFFIC["batch"]["bytes_per_pixel"] / alg8 <= 1.05
